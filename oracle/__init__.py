@@ -1,0 +1,144 @@
+"""Stream VByte oracle (test infrastructure only).
+
+A plain scalar C statement of the codec in ``svb_ref.c`` (arXiv 1709.08990,
+Sec. 3-4 for the format, Sec. 1, 2 and 5 for differential coding), wrapped
+here with ctypes over numpy arrays.  Only the test suite, the smoke check
+and the bench's CPU-baseline leg may import this package.  The product
+library neither links nor calls it, and it shares no code with the CUDA
+path.
+
+Every function here is pinned by the ``-m "not gpu"`` tests: the paper's
+worked byte examples (Fig. 1, Fig. 3), its prefix-sum example (Sec. 2), the
+length boundaries (Sec. 3), the size formula (Sec. 4), brute force over all
+length patterns for n <= 12, and an independently written Python definition.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "svb_ref.c")
+LIB = os.path.join(HERE, "libsvb_ref.so")
+
+ERROR = (1 << 64) - 1  # SVB_REF_ERROR, (size_t)-1
+
+
+def build_cmd(src: str = SRC, out: str = LIB) -> list[str]:
+    """gcc command that builds the oracle's shared library."""
+    return ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", out, src]
+
+
+def build() -> None:
+    """Compile the oracle if its library is missing or older than its source."""
+    if os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
+        return
+    subprocess.run(build_cmd(), check=True)
+
+
+class Codec:
+    """The oracle's entry points, bound to one build of ``svb_ref.c``."""
+
+    def __init__(self, path: str = LIB):
+        L = ctypes.CDLL(path)
+        sz, u32, vp = ctypes.c_size_t, ctypes.c_uint32, ctypes.c_void_p
+        L.svb_ref_byte_length.argtypes = [u32]
+        L.svb_ref_byte_length.restype = ctypes.c_uint
+        L.svb_ref_control_bytes.argtypes = [sz]
+        L.svb_ref_control_bytes.restype = sz
+        L.svb_ref_max_compressed_size.argtypes = [sz]
+        L.svb_ref_max_compressed_size.restype = sz
+        L.svb_ref_encode.argtypes = [vp, sz, vp]
+        L.svb_ref_encode.restype = sz
+        L.svb_ref_delta_encode.argtypes = [vp, sz, vp, u32]
+        L.svb_ref_delta_encode.restype = sz
+        L.svb_ref_decode.argtypes = [vp, sz, sz, vp]
+        L.svb_ref_decode.restype = sz
+        L.svb_ref_delta_decode.argtypes = [vp, sz, sz, vp, u32]
+        L.svb_ref_delta_decode.restype = sz
+        L.svb_ref_data_bytes.argtypes = [vp, sz]
+        L.svb_ref_data_bytes.restype = sz
+        self.lib = L
+        self.path = path
+
+    def byte_length(self, x: int) -> int:
+        return self.lib.svb_ref_byte_length(x)
+
+    def control_bytes(self, n: int) -> int:
+        return self.lib.svb_ref_control_bytes(n)
+
+    def max_compressed_size(self, n: int) -> int:
+        return self.lib.svb_ref_max_compressed_size(n)
+
+    def encode(self, x, prev: int = 0, delta: bool = False) -> np.ndarray:
+        """Compressed stream (uint8) of the uint32 array ``x``."""
+        x = np.ascontiguousarray(x, dtype=np.uint32)
+        n = x.size
+        out = np.zeros(max(1, self.max_compressed_size(n)), dtype=np.uint8)
+        if delta:
+            k = self.lib.svb_ref_delta_encode(x.ctypes.data, n, out.ctypes.data,
+                                              prev & 0xFFFFFFFF)
+        else:
+            k = self.lib.svb_ref_encode(x.ctypes.data, n, out.ctypes.data)
+        if k == ERROR:
+            raise MemoryError("oracle encode failed")
+        return out[:k].copy()
+
+    def decode(self, stream, n: int, prev: int = 0, delta: bool = False,
+               in_len: int | None = None):
+        """(decoded uint32 array, bytes consumed).  Bytes consumed is ERROR
+        when the stream is shorter than its control bytes require."""
+        stream = np.ascontiguousarray(stream, dtype=np.uint8)
+        if in_len is None:
+            in_len = stream.size
+        assert in_len <= stream.size
+        buf = stream if stream.size else np.zeros(1, dtype=np.uint8)
+        out = np.zeros(max(1, n), dtype=np.uint32)
+        if delta:
+            k = self.lib.svb_ref_delta_decode(buf.ctypes.data, in_len, n,
+                                              out.ctypes.data, prev & 0xFFFFFFFF)
+        else:
+            k = self.lib.svb_ref_decode(buf.ctypes.data, in_len, n, out.ctypes.data)
+        return out[:n], k
+
+    def data_bytes(self, ctrl, n: int) -> int:
+        ctrl = np.ascontiguousarray(ctrl, dtype=np.uint8)
+        return self.lib.svb_ref_data_bytes(ctrl.ctypes.data, n)
+
+
+_default: Codec | None = None
+
+
+def codec() -> Codec:
+    global _default
+    if _default is None:
+        build()
+        _default = Codec(LIB)
+    return _default
+
+
+def encode(x, prev: int = 0, delta: bool = False) -> np.ndarray:
+    return codec().encode(x, prev, delta)
+
+
+def decode(stream, n: int, prev: int = 0, delta: bool = False, in_len: int | None = None):
+    return codec().decode(stream, n, prev, delta, in_len)
+
+
+def byte_length(x: int) -> int:
+    return codec().byte_length(x)
+
+
+def control_bytes(n: int) -> int:
+    return codec().control_bytes(n)
+
+
+def max_compressed_size(n: int) -> int:
+    return codec().max_compressed_size(n)
+
+
+def data_bytes(ctrl, n: int) -> int:
+    return codec().data_bytes(ctrl, n)

@@ -1,0 +1,227 @@
+"""Checks that tie a build of the oracle to what the paper fixes.
+
+Each function takes an ``oracle.Codec`` and returns a list of failure
+messages (empty when the build agrees with the paper).  The same checks run
+against the real oracle, where they must all pass, and against copies of the
+oracle with a mistake planted on purpose, where at least one must fail.
+"""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+
+import svb_definition as D
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _read_golden(name: str) -> dict[str, list[str]]:
+    out: dict[str, list[str]] = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            key, val = line.split(":", 1)
+            out.setdefault(key.strip(), []).append(val.strip())
+    return out
+
+
+def fig3_stream(c) -> list[str]:
+    """Fig. 3 (Sec. 4): the exact 15 bytes of 1024,12,10,2^30,1,2,3,1024."""
+    g = _read_golden("fig3_stream.txt")
+    vals = [int(v) for v in g["values"][0].split()]
+    want = bytes(int(b, 16) for b in g["stream"][0].split())
+    errs = []
+    got = c.encode(np.array(vals, dtype=np.uint32)).tobytes()
+    if got != want:
+        errs.append(f"fig3 encode {got.hex()} != {want.hex()}")
+    back, k = c.decode(np.frombuffer(want, dtype=np.uint8), len(vals))
+    if k != len(want) or back.tolist() != vals:
+        errs.append(f"fig3 decode {back.tolist()} consumed {k}")
+    rejected = bytes(int(b, 16) for b in g["rejected_msb_first_ctrl"][0].split())
+    if got[:2] == rejected:
+        errs.append("fig3 control bytes follow the rejected MSB-first reading")
+    return errs
+
+
+def fig1_blocks(c) -> list[str]:
+    """Fig. 1 (Sec. 3): one block of four takes 9 resp. 6 bytes."""
+    g = _read_golden("fig1_blocks.txt")
+    errs = []
+    for blk, nb in zip(g["block"], g["bytes"]):
+        vals = np.array([int(v) for v in blk.split()], dtype=np.uint32)
+        s = c.encode(vals)
+        if s.size != int(nb):
+            errs.append(f"fig1 block {blk}: {s.size} bytes, want {nb}")
+    return errs
+
+
+def sec2_prefix_sum(c) -> list[str]:
+    """Sec. 2: the prefix sum of deltas (3,4,12,1) is (3,7,19,20)."""
+    g = _read_golden("sec2_prefix_sum.txt")
+    deltas = [int(v) for v in g["deltas"][0].split()]
+    prefix = [int(v) for v in g["prefix"][0].split()]
+    errs = []
+    s = c.encode(np.array(prefix, dtype=np.uint32), prev=0, delta=True)
+    if s.tobytes() != bytes([0] + deltas):
+        errs.append(f"delta encode of {prefix}: {s.tobytes().hex()}")
+    back, k = c.decode(np.array([0] + deltas, dtype=np.uint8), 4, prev=0, delta=True)
+    if back.tolist() != prefix or k != 5:
+        errs.append(f"delta decode of {deltas}: {back.tolist()}")
+    return errs
+
+
+def zero_control(c) -> list[str]:
+    """Sec. 4: an all-zero control byte covers C = 4 data bytes."""
+    s = np.array([0, 9, 8, 7, 6, 99, 99], dtype=np.uint8)
+    back, k = c.decode(s, 4)
+    if k != 5 or back.tolist() != [9, 8, 7, 6]:
+        return [f"zero control byte: consumed {k}, values {back.tolist()}"]
+    return []
+
+
+def control_range(c) -> list[str]:
+    """Sec. 4, Fig. 4: every control byte covers C in [4, 16] bytes, and
+    the stream after it is consumed by exactly that many."""
+    errs = []
+    data = np.arange(1, 17, dtype=np.uint8)
+    for cb in range(256):
+        s = np.concatenate([np.array([cb], dtype=np.uint8), data])
+        _, k = c.decode(s, 4)
+        if not (5 <= k <= 17):
+            errs.append(f"control byte {cb:#04x} consumed {k}")
+    _, k0 = c.decode(np.concatenate([[0], data]).astype(np.uint8), 4)
+    _, k1 = c.decode(np.concatenate([[255], data]).astype(np.uint8), 4)
+    if (k0, k1) != (5, 17):
+        errs.append(f"extremes 0x00/0xff consumed {k0}/{k1}")
+    return errs
+
+
+BOUNDARIES = [0, 1, 255, 256, 65535, 65536, (1 << 24) - 1, 1 << 24, 1 << 30, (1 << 32) - 1]
+
+
+def _paper_length(x: int) -> int:
+    # Sec. 3: the smallest L in {1,2,3,4} with x in [0, 2^(8L)).
+    for L in (1, 2, 3, 4):
+        if x < 1 << (8 * L):
+            return L
+    raise ValueError(x)
+
+
+def length_boundaries(c) -> list[str]:
+    """Sec. 3: lengths change at 2^8, 2^16 and 2^24, in every position."""
+    errs = []
+    for b in BOUNDARIES:
+        for pos in range(4):
+            vals = [7, 7, 7, 7]
+            vals[pos] = b
+            s = c.encode(np.array(vals, dtype=np.uint32))
+            L = _paper_length(b)
+            if s.size != 1 + 3 + L:
+                errs.append(f"value {b} at {pos}: size {s.size}")
+            if (int(s[0]) >> (2 * pos)) & 3 != L - 1:
+                errs.append(f"value {b} at {pos}: control {int(s[0]):#04x}")
+            back, _ = c.decode(s, 4)
+            if back.tolist() != vals:
+                errs.append(f"value {b} at {pos}: decodes to {back.tolist()}")
+    return errs
+
+
+def round_trips(c, seed: int = 11) -> list[str]:
+    """decode(encode(x)) == x, plain and delta (any start, unsorted input
+    wraps mod 2^32), over sizes that cover every tail n mod 4."""
+    rng = np.random.default_rng(seed)
+    errs = []
+    for n in [0, 1, 2, 3, 4, 5, 7, 8, 13, 100, 1023, 4097]:
+        for delta in (False, True):
+            L = rng.integers(1, 5, n)
+            x = (rng.integers(0, 1 << 32, n, dtype=np.uint64) >> (8 * (4 - L)).astype(np.uint64)).astype(np.uint32)
+            prev = int(rng.integers(0, 1 << 32))
+            s = c.encode(x, prev=prev, delta=delta)
+            back, k = c.decode(s, n, prev=prev, delta=delta)
+            if k != s.size or not np.array_equal(back, x):
+                errs.append(f"round trip n={n} delta={delta}")
+    return errs
+
+
+def definition_agrees(c, seed: int = 12) -> list[str]:
+    """Bytes and values equal those of the independent Python definition."""
+    rng = np.random.default_rng(seed)
+    errs = []
+    for trial in range(300):
+        n = int(rng.integers(0, 14))
+        L = rng.integers(1, 5, n)
+        x = [int(v) >> (8 * (4 - int(l))) for v, l in zip(rng.integers(0, 1 << 32, n, dtype=np.uint64), L)]
+        prev = int(rng.integers(0, 1 << 32)) if trial % 2 else 0
+        delta = bool(trial % 3)
+        want = D.encode(x, prev, delta)
+        got = c.encode(np.array(x, dtype=np.uint32), prev=prev, delta=delta).tobytes()
+        if got != want:
+            errs.append(f"encode {x} prev={prev} delta={delta}: {got.hex()} != {want.hex()}")
+            break
+    for trial in range(300):
+        n = int(rng.integers(0, 14))
+        raw = rng.integers(0, 256, int(rng.integers(0, 70)), dtype=np.uint8)
+        prev = int(rng.integers(0, 1 << 32))
+        delta = bool(trial % 2)
+        wv, wk = D.decode(raw.tobytes(), n, prev, delta)
+        gv, gk = c.decode(raw, n, prev=prev, delta=delta)
+        if wv is None:
+            if gk != (1 << 64) - 1:
+                errs.append(f"random stream n={n}: truncation not reported")
+                break
+        elif gk != wk or gv.tolist() != wv:
+            errs.append(f"random stream n={n}: {gv.tolist()} / {gk} != {wv} / {wk}")
+            break
+    return errs
+
+
+def truncation(c) -> list[str]:
+    """A stream shorter than its control bytes require is an error, and the
+    decoder reads nothing beyond in_len."""
+    errs = []
+    x = np.array([1024, 12, 10, 1 << 30, 1, 2, 3, 1024, 5], dtype=np.uint32)
+    s = c.encode(x)
+    for cut in range(s.size):
+        _, k = c.decode(s, x.size, in_len=cut)
+        if k != (1 << 64) - 1:
+            errs.append(f"in_len={cut} of {s.size}: consumed {k}")
+    return errs
+
+
+def pad_fields_ignored(c) -> list[str]:
+    """The unused fields of an incomplete last control byte change nothing."""
+    errs = []
+    x = np.array([300, 5, 70000, 9, 1, 2], dtype=np.uint32)  # n mod 4 = 2
+    s = c.encode(x)
+    if s[1] >> 4:
+        errs.append(f"encoder wrote pad fields: {int(s[1]):#04x}")
+    base, k = c.decode(s, x.size)
+    for pad in (0x10, 0x20, 0xF0, 0xC0):
+        t = s.copy()
+        t[1] |= pad
+        v, k2 = c.decode(t, x.size)
+        if k2 != k or not np.array_equal(v, base):
+            errs.append(f"pad bits {pad:#04x} changed the result")
+    return errs
+
+
+def nonminimal_codes(c) -> list[str]:
+    """Any code decodes, e.g. 5 stored in four bytes (Sec. 4: C is read from
+    the control byte, not recomputed)."""
+    s = np.array([0b11, 5, 0, 0, 0, 1, 2, 3], dtype=np.uint8)
+    v, k = c.decode(s, 4)
+    if k != 8 or v.tolist() != [5, 1, 2, 3]:
+        return [f"non-minimal code: {v.tolist()} consumed {k}"]
+    return []
+
+
+ALL = [fig3_stream, fig1_blocks, sec2_prefix_sum, zero_control, control_range,
+       length_boundaries, round_trips, definition_agrees, truncation,
+       pad_fields_ignored, nonminimal_codes]
+
+
+def run_all(c) -> dict[str, list[str]]:
+    return {f.__name__: f(c) for f in ALL}
