@@ -1,0 +1,415 @@
+"""Stream VByte decode throughput on GB300.
+
+One step = one decode of the whole workload array (control-length reduce,
+look-back offset scan, staging, gather, stores: the decode hot path) through
+the library's async C entry point, input resident in HBM.
+
+Default workload: skewed_1g, n = 2^30 uint32, byte lengths with
+P = (.50, .30, .15, .05), values uniform within each length (seeded,
+synthetic: the paper's ClueWeb09 posting lists are not available).  Its 2 GiB
+stream and 4 GiB output are far larger than L2, so no flush is needed between
+steps.
+
+Prints one JSON line (rank 0).  Also reported in the same line:
+  roofline      decode kernel's algorithmic bytes / CUDA-event time vs the
+                measured HBM copy bandwidth
+  e2e           the same metric through svb_decode_host (host buffers, the
+                copies in and out inside the timed region)
+  cpu_baseline  the oracle (plain scalar C) on a bounded sample, one core
+  secondary     the delta_64m workload (delta decode and encode) and the
+                encoder on skewed_1g, each with its roofline fraction
+
+--impl reference times the oracle on the host cores instead (the paper's
+method as a plain scalar program; there is no other implementation to run).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="skewed_1g")
+    ap.add_argument("--n", type=int, default=0, help="decode only the first n integers")
+    ap.add_argument("--no-secondary", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    return ap.parse_args()
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": d["hbm_gbs"], "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("svb_decode.cu", "svb_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1709_08990_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, workload: str) -> int | None:
+    """DRAM bytes per launch from the committed ncu summary, when it was taken
+    on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(p):
+        return None
+    src = kernel_source_hash()
+    for line in open(p):
+        f = line.split()
+        if len(f) >= 4 and not line.startswith("#") and f[0] == kernel and f[1] == workload \
+                and f[3] == src:
+            return int(f[2])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during a timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.out = None
+
+    def __enter__(self):
+        try:
+            self.out = open(os.devnull if False else "/tmp/svb_clocks.csv", "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.out:
+            self.out.close()
+
+    def summary(self) -> dict:
+        try:
+            rows = [l.strip().split(", ") for l in open("/tmp/svb_clocks.csv") if l.strip()]
+        except Exception:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                mx = float(r[1])
+                for nm, v in zip(names, r[4:8]):
+                    if v.strip() == "Active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def oracle_decode_rate(stream: np.ndarray, n: int, delta: bool, seconds: float):
+    """Oracle decode of one sample, repeated for about `seconds`; Gints/s."""
+    import oracle
+    c = oracle.codec()
+    out = np.empty(n, dtype=np.uint32)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        if delta:
+            k = c.lib.svb_ref_delta_decode(stream.ctypes.data, stream.size, n, out.ctypes.data, 0)
+        else:
+            k = c.lib.svb_ref_decode(stream.ctypes.data, stream.size, n, out.ctypes.data)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    assert k == stream.size
+    return reps * n / el / 1e9, reps, el
+
+
+def reference_arm(args, rank: int):
+    """The oracle timed on the host cores, K steps of a bounded sample."""
+    if rank != 0:
+        return
+    from paper_1709_08990_gb300 import workloads as W
+    import oracle
+    w = W.WORKLOADS[args.workload]
+    # About 60 s of oracle work over all K steps (it decodes ~0.1 Gints/s).
+    m = 1 << 24
+    while m > (1 << 16) and args.steps * m > 6_000_000_000:
+        m >>= 1
+    x = W.array_values(args.workload, n=m)
+    s = oracle.encode(x, delta=w.delta)
+    c = oracle.codec()
+    out = np.empty(m, dtype=np.uint32)
+    fn = (lambda: c.lib.svb_ref_delta_decode(s.ctypes.data, s.size, m, out.ctypes.data, 0)) \
+        if w.delta else (lambda: c.lib.svb_ref_decode(s.ctypes.data, s.size, m, out.ctypes.data))
+    for _ in range(args.warmup):
+        fn()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        fn()
+    el = time.perf_counter() - t0
+    assert np.array_equal(out, x)
+    value = args.steps * m / el / 1e9
+    sample = f"first {m} integers of {args.workload}, decoded {args.steps} times"
+    line = {
+        "impl": "reference", "metric": "decode_gints_per_s", "value": value, "unit": "Gints/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": args.workload, "n": m, "delta": w.delta},
+        "cpu_baseline": {"value": value, "unit": "Gints/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "Gints/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank)
+        return
+
+    import torch
+    from paper_1709_08990_gb300 import svb
+    from paper_1709_08990_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    dev = torch.device("cuda", local)
+    w = W.WORKLOADS[args.workload]
+    n = args.n if args.n else w.n
+    peaks = measured_peaks()
+
+    # ---- inputs: values on the host (seeded), encoded on the device --------
+    h_x = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    W.array_values(args.workload, n=n, out=h_x.numpy().view(np.uint32))
+    d_x = h_x.to(dev, non_blocking=True)
+    torch.cuda.synchronize()
+    d_stream = svb.encode(d_x, delta=w.delta)
+    in_len = d_stream.numel()
+    d_out = torch.empty(n, dtype=torch.int32, device=dev)
+    ws_bytes = svb.svb_workspace_size(n)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    res = torch.zeros(2, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream()
+    svb.svb_workspace_init(ws, ws_bytes, stream)
+
+    def step():
+        st = svb.svb_decode_async(d_stream, in_len, n, d_out, 0, int(w.delta), res, ws, ws_bytes,
+                                  stream)
+        if st != 0:
+            raise RuntimeError(f"decode launch failed: {st}")
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    r = res.cpu().numpy()
+    if r[1] != 0 or r[0] != in_len or not torch.equal(d_out, d_x):
+        raise RuntimeError("decode result differs from the encoded values")
+    del d_x
+
+    # ---- timed region: K decodes, events per launch ---------------------------
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    total_ms = t_start.elapsed_time(t_end)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    kernel_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    value = n * args.steps * world / (total_ms / 1e3) / 1e9
+    alg_bytes = in_len + 4 * n  # control + data read, 4n written
+    achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["source"],
+                "kernel": "decode_kernel<false>" if not w.delta else "decode_kernel<true>",
+                "alg_bytes_per_launch": alg_bytes,
+                "traffic": ncu_traffic("decode_kernel", args.workload)}
+
+    line = {
+        "metric": "decode_gints_per_s", "value": value, "unit": "Gints/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n": n, "delta": w.delta, "stream_bytes": in_len,
+                   "bits_per_int": 8.0 * in_len / n, "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+        "roofline": roofline,
+        "clocks": clocks.summary(),
+        "gpu_launches": args.steps,
+    }
+
+    # ---- e2e: through the host-buffer C entry point ----------------------
+    if not args.no_e2e:
+        h_stream = torch.empty(in_len, dtype=torch.uint8, pin_memory=True)
+        h_stream.copy_(d_stream)
+        h_out = torch.empty(n, dtype=torch.int32, pin_memory=True)
+        d_in2 = torch.empty(in_len, dtype=torch.uint8, device=dev)
+        k_e2e = max(3, min(10, args.steps))
+        svb.svb_decode_host(h_stream, in_len, n, h_out, 0, int(w.delta), d_in2, d_out)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            svb.svb_decode_host(h_stream, in_len, n, h_out, 0, int(w.delta), d_in2, d_out)
+        el = time.perf_counter() - t0
+        barrier()
+        ok = torch.equal(h_out, h_x)
+        line["e2e"] = {"value": n * k_e2e * world / el / 1e9, "unit": "Gints/s",
+                       "h2d_bytes_per_step": in_len, "d2h_bytes_per_step": 4 * n + 16,
+                       "steps": k_e2e, "verified": bool(ok)}
+        del d_in2, h_out, h_stream
+
+    # ---- CPU baseline: the oracle on a bounded sample (rank 0, N=1) ---------
+    if not args.no_cpu and rank == 0 and world == 1:
+        import oracle
+        m = 1 << 25
+        xs = h_x.numpy().view(np.uint32)[:m]
+        s = oracle.encode(xs, delta=w.delta)
+        rate, reps, el = oracle_decode_rate(s, m, w.delta, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": "Gints/s", "cores": 1, "kind": "oracle",
+                                "sample": f"first 2^25 integers of {args.workload} "
+                                          f"({reps} decodes, {el:.1f} s)"}
+
+    # ---- secondary workloads --------------------------------------------------
+    if not args.no_secondary:
+        sec = {}
+        del d_out, d_stream
+        torch.cuda.empty_cache()
+        sec["encode_" + args.workload] = time_encode(svb, W, args.workload, dev, peaks, h_x)
+        del h_x
+        sec["delta_64m"] = time_codec(svb, W, "delta_64m", dev, peaks)
+        sec["uniform_1m"] = time_codec(svb, W, "uniform_1m", dev, peaks)
+        line["secondary"] = sec
+
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def _time(fn, steps, stream):
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    for a, b in ev:
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+
+def time_encode(svb, W, name, dev, peaks, h_x):
+    import torch
+    n = h_x.numel()
+    d_x = h_x.to(dev)
+    d_s = torch.empty(svb.svb_max_compressed_size(n), dtype=torch.uint8, device=dev)
+    ws_bytes = svb.svb_workspace_size(n)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    res = torch.zeros(2, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream()
+    svb.svb_workspace_init(ws, ws_bytes, stream)
+    delta = W.WORKLOADS[name].delta
+    ms = _time(lambda: svb.svb_encode_async(d_x, n, d_s, 0, int(delta), res, ws, ws_bytes, stream),
+               50, stream)
+    size = int(res[0].item())
+    alg = 4 * n + size
+    out = {"gints_per_s": n / ms / 1e6, "ms": ms, "frac": alg / (ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+           "alg_bytes": alg}
+    del d_x, d_s, ws
+    torch.cuda.empty_cache()
+    return out
+
+
+def time_codec(svb, W, name, dev, peaks):
+    import torch
+    w = W.WORKLOADS[name]
+    x = W.array_values(name)
+    d_x = torch.from_numpy(x.view(np.int32)).to(dev)
+    n = x.size
+    d_s = torch.empty(svb.svb_max_compressed_size(n), dtype=torch.uint8, device=dev)
+    d_o = torch.empty(n, dtype=torch.int32, device=dev)
+    ws_bytes = svb.svb_workspace_size(n)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    res = torch.zeros(2, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream()
+    svb.svb_workspace_init(ws, ws_bytes, stream)
+    steps = 200 if n > (1 << 22) else 2000
+    ms_e = _time(lambda: svb.svb_encode_async(d_x, n, d_s, 0, int(w.delta), res, ws, ws_bytes, stream),
+                 steps, stream)
+    size = int(res[0].item())
+    ms_d = _time(lambda: svb.svb_decode_async(d_s, size, n, d_o, 0, int(w.delta), res, ws, ws_bytes,
+                                              stream), steps, stream)
+    ok = torch.equal(d_o, d_x)
+    alg = 4 * n + size
+    hb = peaks["hbm_gbs"]
+    return {"n": n, "delta": w.delta, "stream_bytes": size, "verified": bool(ok),
+            "decode": {"gints_per_s": n / ms_d / 1e6, "us": ms_d * 1e3,
+                       "frac": alg / (ms_d / 1e3) / 1e9 / hb},
+            "encode": {"gints_per_s": n / ms_e / 1e6, "us": ms_e * 1e3,
+                       "frac": alg / (ms_e / 1e3) / 1e9 / hb}}
+
+
+if __name__ == "__main__":
+    main()

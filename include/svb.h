@@ -1,0 +1,164 @@
+/*
+ * svb.h - Stream VByte codec on the GPU (sm_103a), C ABI.
+ *
+ * Format (Lemire, Kurz, Rupp, arXiv 1709.08990, Sec. 4 and Fig. 3): n
+ * unsigned 32-bit integers become ceil(n/4) control bytes followed by a data
+ * stream.  Integer i has a 2-bit code, length - 1, in control byte i/4 at
+ * bits 2(i mod 4)..2(i mod 4)+1 (first integer in the low bits); its value
+ * takes `length` bytes of the data stream, least significant byte first.
+ * The length of v is ceil(log_256(v + 1)) bytes, one byte for v = 0
+ * (Sec. 3).  Pad fields of an incomplete last control byte are written as 0
+ * and ignored when decoding.  n is not stored in the stream (Sec. 4: "we
+ * record how many integers N are compressed"); every call takes it.
+ *
+ * Differential coding (Sec. 1, Sec. 2 "Differential Coding", Sec. 5): the
+ * stream holds delta_1 = x_1 - prev, delta_i = x_i - x_{i-1}, modulo 2^32;
+ * decoding computes x_i = prev + delta_1 + ... + delta_i modulo 2^32.  The
+ * paper starts from prev = 0; here the caller chooses prev.
+ *
+ * Memory.  Every data pointer is a DEVICE pointer unless its name starts
+ * with h_.  The caller allocates and owns every buffer.  No entry point
+ * retains a pointer after it returns (async forms: after the stream reaches
+ * the launched work).  Buffers need no particular alignment; 16-byte aligned
+ * buffers take the fastest path.
+ *
+ * Streams.  svb_stream_t is cudaStream_t.  The synchronous forms run on the
+ * calling thread's stream set by svb_set_stream (default: the legacy default
+ * stream 0) and wait for it.  The async forms enqueue work on the stream they
+ * are given and return at once.
+ *
+ * Errors.  Size-returning calls return SVB_ERROR ((size_t)-1) on failure and
+ * set the calling thread's svb_last_error(); int-returning calls return the
+ * status code itself.  n = 0 returns 0 and touches nothing.
+ */
+#ifndef SVB_H
+#define SVB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+typedef struct CUstream_st *svb_stream_t; /* == cudaStream_t */
+
+#define SVB_ERROR ((size_t)-1)
+
+enum svb_status {
+    SVB_OK = 0,
+    SVB_EINVAL = 1,     /* null pointer with n > 0, workspace too small, bad argument */
+    SVB_ETRUNCATED = 2, /* the compressed input is shorter than its control bytes require */
+    SVB_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed */
+    SVB_ETIMEOUT = 4,   /* a cross-tile wait ran past its spin limit; outputs are undefined */
+    SVB_ENOMEM = 5      /* the library could not allocate its per-device workspace */
+};
+
+/* Written by the device at the end of an async call.  bytes: bytes written
+ * (encode) or consumed (decode), or SVB_ERROR; status: an svb_status. */
+typedef struct svb_result {
+    uint64_t bytes;
+    uint64_t status;
+} svb_result;
+
+/* ---- sizes -------------------------------------------------------------- */
+
+/* Largest compressed size of n integers: ceil(n/4) + 4n (Sec. 4: control
+ * bytes plus at most four data bytes per integer). */
+size_t svb_max_compressed_size(size_t n);
+
+/* Compressed size of n integers whose control bytes are ctrl (a HOST copy of
+ * the first ceil(n/4) bytes of a stream): ceil(n/4) + sum of the lengths the
+ * codes give, pad fields not counted. */
+size_t svb_compressed_size_from_control(const uint8_t *h_ctrl, size_t n);
+
+/* ---- the four codec calls (Sec. 4; synchronous) ------------------------ */
+
+/* Encode in[0..n) into out (capacity >= svb_max_compressed_size(n)).
+ * Returns the bytes written, ceil(n/4) + sum of lengths. */
+size_t svb_encode(const uint32_t *in, size_t n, uint8_t *out);
+
+/* Decode n integers from the stream at in into out[0..n).  The caller
+ * guarantees that in holds the whole stream (its length follows from the
+ * control bytes; use svb_decode_checked when it is not known).  Returns the
+ * bytes consumed.  Reads no byte outside the stream. */
+size_t svb_decode(const uint8_t *in, size_t n, uint32_t *out);
+
+/* Differential forms: the stream codes in[0] - prev, then in[i] - in[i-1]
+ * for i >= 1, modulo 2^32; decoding restores out[i] = prev + the sum of the
+ * first i + 1 coded values, modulo 2^32 (Sec. 2, Sec. 5). */
+size_t svb_delta_encode(const uint32_t *in, size_t n, uint8_t *out, uint32_t prev);
+size_t svb_delta_decode(const uint8_t *in, size_t n, uint32_t *out, uint32_t prev);
+
+/* Decode with the input length known: in[0..in_len) is all that may be
+ * read.  A stream shorter than its control bytes require returns SVB_ERROR
+ * with SVB_ETRUNCATED and leaves out partly written.  delta selects
+ * differential decoding from prev. */
+size_t svb_decode_checked(const uint8_t *in, size_t in_len, size_t n, uint32_t *out,
+                          uint32_t prev, int delta);
+
+/* ---- host-buffer forms (copies inside the call) ------------------------ */
+
+/* Decode a stream held in HOST memory h_in[0..in_len) into HOST memory
+ * h_out[0..n).  d_in (>= in_len bytes) and d_out (>= 4n bytes) are caller-
+ * owned device staging buffers.  Copies in, decodes and copies out on the
+ * calling thread's stream; pinned host memory gives full link speed. */
+size_t svb_decode_host(const uint8_t *h_in, size_t in_len, size_t n, uint32_t *h_out,
+                       uint32_t prev, int delta, uint8_t *d_in, uint32_t *d_out);
+
+/* Encode HOST h_in[0..n) into HOST h_out (capacity >=
+ * svb_max_compressed_size(n)) through device staging buffers d_in (>= 4n
+ * bytes) and d_out (>= svb_max_compressed_size(n) bytes). */
+size_t svb_encode_host(const uint32_t *h_in, size_t n, uint8_t *h_out, uint32_t prev,
+                       int delta, uint32_t *d_in, uint8_t *d_out);
+
+/* ---- streams and errors ------------------------------------------------ */
+
+/* Stream used by the synchronous forms in the calling thread. */
+int svb_set_stream(svb_stream_t stream);
+svb_stream_t svb_get_stream(void);
+
+/* Status of the calling thread's last failed (or successful) call. */
+int svb_last_error(void);
+const char *svb_error_string(int status);
+
+/* Spin limit of the cross-tile waits (iterations of a bounded, backing-off
+ * poll, about a microsecond each at most).  0 restores the default, which is
+ * also overridable with the environment variable SVB_LOOKBACK_SPIN_LIMIT. */
+void svb_set_spin_limit(uint64_t iterations);
+
+/* ---- async forms with a caller-owned workspace ------------------------- */
+
+/* Bytes of workspace one async call over n integers needs. */
+size_t svb_workspace_size(size_t n);
+
+/* Zero a workspace once before its first use (enqueued on stream).  A
+ * workspace serves one call at a time: calls that share one must be ordered
+ * on one stream. */
+int svb_workspace_init(void *ws, size_t ws_bytes, svb_stream_t stream);
+
+/* Enqueue an encode / decode on stream.  d_result (device memory) receives
+ * the byte count and status when the work completes.  in_len bounds the
+ * decoder's reads (pass SIZE_MAX when the stream is known to be complete). */
+int svb_encode_async(const uint32_t *in, size_t n, uint8_t *out, uint32_t prev, int delta,
+                     svb_result *d_result, void *ws, size_t ws_bytes, svb_stream_t stream);
+int svb_decode_async(const uint8_t *in, size_t in_len, size_t n, uint32_t *out,
+                     uint32_t prev, int delta, svb_result *d_result, void *ws,
+                     size_t ws_bytes, svb_stream_t stream);
+
+/* ---- test hook ---------------------------------------------------------- */
+
+/* Failure-detection check: launches one decode tile whose predecessor is
+ * never published, so its cross-tile wait runs out after spin_limit polls.
+ * The call must report SVB_ETIMEOUT in d_result and leave the context
+ * usable.  stream_in holds a stream of n >= 2 * 4096 integers. */
+int svb_testhook_lookback_timeout(const uint8_t *stream_in, size_t n, uint32_t *out,
+                                  uint64_t spin_limit, svb_result *d_result, void *ws,
+                                  size_t ws_bytes, svb_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SVB_H */

@@ -1,0 +1,329 @@
+// The C ABI of include/svb.h: argument checks, the per-device workspace used
+// by the synchronous calls, stream and error bookkeeping.  All computation
+// happens in the kernels; nothing here decodes or encodes on the host.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+
+#include "svb.h"
+#include "svb_device.cuh"
+#include "svb_internal.h"
+
+using svb::u64;
+
+namespace {
+
+thread_local int t_last_error = SVB_OK;
+thread_local cudaStream_t t_stream = nullptr;
+std::atomic<u64> g_spin_limit{0};
+
+constexpr u64 kDefaultSpinLimit = 1ull << 21;  // ~2 s of polling at most
+
+u64 spin_limit()
+{
+    u64 v = g_spin_limit.load(std::memory_order_relaxed);
+    if (v)
+        return v;
+    static const u64 env = [] {
+        const char *s = std::getenv("SVB_LOOKBACK_SPIN_LIMIT");
+        if (s && *s) {
+            unsigned long long x = std::strtoull(s, nullptr, 10);
+            if (x > 0)
+                return (u64)x;
+        }
+        return kDefaultSpinLimit;
+    }();
+    return env;
+}
+
+size_t set_error(int code)
+{
+    t_last_error = code;
+    return code == SVB_OK ? 0 : SVB_ERROR;
+}
+
+u64 tiles_for(size_t n)
+{
+    u64 nq = ((u64)n + 3) / 4;
+    return (nq + svb::kMinQuadsPerTile - 1) / svb::kMinQuadsPerTile;
+}
+
+// Workspace kept per device for the synchronous calls.  The calls on one
+// device serialise on its mutex: they share the workspace and wait anyway.
+struct DeviceCache {
+    std::mutex mu;
+    void *ws = nullptr;
+    size_t bytes = 0;
+    svb_result *h_res = nullptr;  // pinned
+};
+
+constexpr int kMaxDevices = 64;
+DeviceCache g_cache[kMaxDevices];
+
+template <class F>
+size_t run_sync(size_t n, F &&launch)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return set_error(SVB_ECUDA);
+    DeviceCache &c = g_cache[dev];
+    std::lock_guard<std::mutex> lock(c.mu);
+    cudaStream_t s = t_stream;
+    size_t need = svb_workspace_size(n);
+    if (c.bytes < need) {
+        size_t grow = std::max(need, 2 * c.bytes);
+        if (c.ws) {
+            cudaDeviceSynchronize();
+            cudaFree(c.ws);
+            c.ws = nullptr;
+            c.bytes = 0;
+        }
+        if (cudaMalloc(&c.ws, grow) != cudaSuccess) {
+            cudaGetLastError();
+            c.ws = nullptr;
+            return set_error(SVB_ENOMEM);
+        }
+        if (cudaMemsetAsync(c.ws, 0, grow, s) != cudaSuccess)
+            return set_error(SVB_ECUDA);
+        c.bytes = grow;
+    }
+    if (!c.h_res && cudaMallocHost(&c.h_res, sizeof(svb_result)) != cudaSuccess) {
+        c.h_res = nullptr;
+        return set_error(SVB_ENOMEM);
+    }
+    auto *d_res = reinterpret_cast<svb::DeviceResult *>(static_cast<char *>(c.ws) +
+                                                         svb::kResultOffset);
+    int st = launch(c.ws, d_res, s);
+    if (st != SVB_OK)
+        return set_error(st);
+    if (cudaMemcpyAsync(c.h_res, d_res, sizeof(svb_result), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return set_error(SVB_ECUDA);
+    if (c.h_res->status != SVB_OK)
+        return set_error((int)c.h_res->status);
+    t_last_error = SVB_OK;
+    return (size_t)c.h_res->bytes;
+}
+
+size_t encode_sync(const uint32_t *in, size_t n, uint8_t *out, uint32_t prev, bool delta)
+{
+    if (n == 0)
+        return set_error(SVB_OK);
+    if (!in || !out)
+        return set_error(SVB_EINVAL);
+    return run_sync(n, [&](void *ws, svb::DeviceResult *r, cudaStream_t s) {
+        return svb::launch_encode(in, n, out, prev, delta, ws, r, s, spin_limit());
+    });
+}
+
+size_t decode_sync(const uint8_t *in, u64 in_len, size_t n, uint32_t *out, uint32_t prev,
+                   bool delta)
+{
+    if (n == 0)
+        return set_error(SVB_OK);
+    if (!in || !out)
+        return set_error(SVB_EINVAL);
+    if (in_len < ((u64)n + 3) / 4)
+        return set_error(SVB_ETRUNCATED);
+    return run_sync(n, [&](void *ws, svb::DeviceResult *r, cudaStream_t s) {
+        return svb::launch_decode(in, in_len, n, out, prev, delta, ws, r, s, spin_limit());
+    });
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t svb_max_compressed_size(size_t n)
+{
+    return (n + 3) / 4 + 4 * n;
+}
+
+size_t svb_compressed_size_from_control(const uint8_t *h_ctrl, size_t n)
+{
+    if (n == 0)
+        return 0;
+    if (!h_ctrl)
+        return set_error(SVB_EINVAL);
+    size_t nq = (n + 3) / 4, total = nq;
+    for (size_t q = 0; q < nq; q++) {
+        unsigned c = h_ctrl[q];
+        unsigned k = (q == nq - 1) ? (unsigned)(n - 4 * q) : 4u;
+        if (k < 4)
+            c &= (1u << (2 * k)) - 1u;
+        total += k + (unsigned)__builtin_popcount(c & 0x55u) +
+                 2u * (unsigned)__builtin_popcount(c & 0xAAu);
+    }
+    t_last_error = SVB_OK;
+    return total;
+}
+
+size_t svb_encode(const uint32_t *in, size_t n, uint8_t *out)
+{
+    return encode_sync(in, n, out, 0, false);
+}
+
+size_t svb_decode(const uint8_t *in, size_t n, uint32_t *out)
+{
+    return decode_sync(in, ~0ull, n, out, 0, false);
+}
+
+size_t svb_delta_encode(const uint32_t *in, size_t n, uint8_t *out, uint32_t prev)
+{
+    return encode_sync(in, n, out, prev, true);
+}
+
+size_t svb_delta_decode(const uint8_t *in, size_t n, uint32_t *out, uint32_t prev)
+{
+    return decode_sync(in, ~0ull, n, out, prev, true);
+}
+
+size_t svb_decode_checked(const uint8_t *in, size_t in_len, size_t n, uint32_t *out,
+                          uint32_t prev, int delta)
+{
+    return decode_sync(in, in_len, n, out, prev, delta != 0);
+}
+
+size_t svb_decode_host(const uint8_t *h_in, size_t in_len, size_t n, uint32_t *h_out,
+                       uint32_t prev, int delta, uint8_t *d_in, uint32_t *d_out)
+{
+    if (n == 0)
+        return set_error(SVB_OK);
+    if (!h_in || !h_out || !d_in || !d_out)
+        return set_error(SVB_EINVAL);
+    cudaStream_t s = t_stream;
+    if (cudaMemcpyAsync(d_in, h_in, in_len, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return set_error(SVB_ECUDA);
+    size_t k = decode_sync(d_in, in_len, n, d_out, prev, delta != 0);
+    if (k == SVB_ERROR)
+        return k;
+    if (cudaMemcpyAsync(h_out, d_out, 4 * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return set_error(SVB_ECUDA);
+    t_last_error = SVB_OK;
+    return k;
+}
+
+size_t svb_encode_host(const uint32_t *h_in, size_t n, uint8_t *h_out, uint32_t prev,
+                       int delta, uint32_t *d_in, uint8_t *d_out)
+{
+    if (n == 0)
+        return set_error(SVB_OK);
+    if (!h_in || !h_out || !d_in || !d_out)
+        return set_error(SVB_EINVAL);
+    cudaStream_t s = t_stream;
+    if (cudaMemcpyAsync(d_in, h_in, 4 * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return set_error(SVB_ECUDA);
+    size_t k = encode_sync(d_in, n, d_out, prev, delta != 0);
+    if (k == SVB_ERROR)
+        return k;
+    if (cudaMemcpyAsync(h_out, d_out, k, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return set_error(SVB_ECUDA);
+    t_last_error = SVB_OK;
+    return k;
+}
+
+int svb_set_stream(svb_stream_t stream)
+{
+    t_stream = reinterpret_cast<cudaStream_t>(stream);
+    return SVB_OK;
+}
+
+svb_stream_t svb_get_stream(void)
+{
+    return reinterpret_cast<svb_stream_t>(t_stream);
+}
+
+int svb_last_error(void)
+{
+    return t_last_error;
+}
+
+const char *svb_error_string(int status)
+{
+    switch (status) {
+    case SVB_OK: return "ok";
+    case SVB_EINVAL: return "invalid argument";
+    case SVB_ETRUNCATED: return "compressed input shorter than its control bytes require";
+    case SVB_ECUDA: return "CUDA error";
+    case SVB_ETIMEOUT: return "cross-tile wait exceeded its spin limit";
+    case SVB_ENOMEM: return "out of device memory";
+    default: return "unknown status";
+    }
+}
+
+void svb_set_spin_limit(uint64_t iterations)
+{
+    g_spin_limit.store(iterations, std::memory_order_relaxed);
+}
+
+size_t svb_workspace_size(size_t n)
+{
+    return svb::kStatusOffset + sizeof(svb::TileStatus) * std::max<u64>(1, tiles_for(n));
+}
+
+int svb_workspace_init(void *ws, size_t ws_bytes, svb_stream_t stream)
+{
+    if (!ws || ws_bytes < svb::kStatusOffset)
+        return SVB_EINVAL;
+    return cudaMemsetAsync(ws, 0, ws_bytes, reinterpret_cast<cudaStream_t>(stream)) ==
+                   cudaSuccess
+               ? SVB_OK
+               : SVB_ECUDA;
+}
+
+int svb_encode_async(const uint32_t *in, size_t n, uint8_t *out, uint32_t prev, int delta,
+                     svb_result *d_result, void *ws, size_t ws_bytes, svb_stream_t stream)
+{
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (!d_result)
+        return SVB_EINVAL;
+    if (n == 0)
+        return cudaMemsetAsync(d_result, 0, sizeof(svb_result), s) == cudaSuccess ? SVB_OK
+                                                                                 : SVB_ECUDA;
+    if (!in || !out || !ws || ws_bytes < svb_workspace_size(n))
+        return SVB_EINVAL;
+    return svb::launch_encode(in, n, out, prev, delta != 0, ws,
+                              reinterpret_cast<svb::DeviceResult *>(d_result), s, spin_limit());
+}
+
+int svb_decode_async(const uint8_t *in, size_t in_len, size_t n, uint32_t *out,
+                     uint32_t prev, int delta, svb_result *d_result, void *ws,
+                     size_t ws_bytes, svb_stream_t stream)
+{
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (!d_result)
+        return SVB_EINVAL;
+    if (n == 0)
+        return cudaMemsetAsync(d_result, 0, sizeof(svb_result), s) == cudaSuccess ? SVB_OK
+                                                                                 : SVB_ECUDA;
+    if (!in || !out || !ws || ws_bytes < svb_workspace_size(n))
+        return SVB_EINVAL;
+    if (in_len < ((u64)n + 3) / 4)
+        return SVB_ETRUNCATED;
+    return svb::launch_decode(in, in_len, n, out, prev, delta != 0, ws,
+                              reinterpret_cast<svb::DeviceResult *>(d_result), s, spin_limit());
+}
+
+int svb_testhook_lookback_timeout(const uint8_t *stream_in, size_t n, uint32_t *out,
+                                  uint64_t spin_limit_, svb_result *d_result, void *ws,
+                                  size_t ws_bytes, svb_stream_t stream)
+{
+    if (!stream_in || !out || !d_result || !ws || ws_bytes < svb_workspace_size(n))
+        return SVB_EINVAL;
+    if (svb::decode_tiles(n) < 2)
+        return SVB_EINVAL;
+    // One CTA that takes tile 1; tile 0 is never launched, so its status is
+    // never published in this launch and the wait must run out.
+    return svb::launch_decode(stream_in, ~0ull, n, out, 0, false, ws,
+                              reinterpret_cast<svb::DeviceResult *>(d_result),
+                              reinterpret_cast<cudaStream_t>(stream), spin_limit_, 1, 1);
+}
+
+}  // extern "C"

@@ -1,0 +1,221 @@
+// Device-side building blocks shared by the Stream VByte kernels:
+// the workspace layout, tile-status records, ordered loads and stores, warp
+// and block scans, and the bounded decoupled look-back that turns per-tile
+// aggregates into exclusive prefixes in one pass.
+//
+// The paper's decoder walks the stream serially: each control byte tells how
+// far the data pointer moves (Sec. 4, Fig. 4), the dependency the paper
+// blames for varint-GB's slowness (Sec. 4, "strong data dependency").  On the
+// GPU that chain becomes a prefix sum of the per-quad byte counts over the
+// whole stream; tiles compute their own sums from their control bytes and
+// chain them with a decoupled look-back (a single-pass scan: each tile
+// publishes its aggregate early and sums its predecessors' published values).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+namespace svb {
+
+typedef unsigned long long u64;
+
+constexpr int kThreads = 256;                      // threads per CTA
+constexpr int kWarps = kThreads / 32;
+constexpr int kMinQuadsPerTile = 256;              // workspace sizing unit
+
+// Status word low bits: what the tile has published.
+constexpr u64 kFlagNone = 0, kFlagAgg = 1, kFlagPrefix = 2;
+
+// Error codes written to the workspace (same values as svb_status).
+constexpr u64 kErrTruncated = 2, kErrTimeout = 4;
+
+// One tile's published values.  Each scan has a tag word and two slots; a
+// reader that has seen a tag reads a slot that is written once per launch
+// and before the tag, so it never sees a half-updated record.  The tag is
+// ((epoch + 1) << 2) | flag: records left by earlier launches on the same
+// workspace never match, so the array is zeroed only once.
+struct __align__(64) TileStatus {
+    u64 off_tag, off_agg, off_pre;   // data-stream byte offsets
+    u64 val_tag, val_agg, val_pre;   // running sum of deltas (mod 2^32)
+    u64 pad0, pad1;
+};
+
+// Workspace layout: [header 128 B][result 16 B, padded to 128 B][TileStatus...]
+struct __align__(128) WsHeader {
+    u64 tile_counter;   // next dynamic tile id
+    u64 done_counter;   // CTAs that have finished this launch
+    u64 epoch;          // launches finished on this workspace
+    u64 error;          // first error of this launch, 0 if none
+    u64 total;          // stream size, written by the last tile
+    u64 pad[11];
+};
+
+constexpr size_t kResultOffset = 128;
+constexpr size_t kStatusOffset = 256;
+
+struct DeviceResult {
+    u64 bytes;
+    u64 status;
+};
+
+// ---- ordered global accesses (GPU scope) ---------------------------------
+
+__device__ __forceinline__ u64 ld_acquire(const u64 *p)
+{
+    u64 v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ u64 ld_relaxed(const u64 *p)
+{
+    u64 v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(u64 *p, u64 v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ void st_relaxed(u64 *p, u64 v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Read-only, not-allocating-in-L1 loads of the compressed input.
+__device__ __forceinline__ uint4 ldg_stream128(const void *p)
+{
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+// Output stores that should not linger in L2 (evict-first).
+__device__ __forceinline__ void stg_stream128(void *p, uint4 v)
+{
+    asm volatile("st.global.cs.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(v.x), "r"(v.y),
+                 "r"(v.z), "r"(v.w)
+                 : "memory");
+}
+
+__device__ __forceinline__ void raise_error(WsHeader *h, u64 code)
+{
+    atomicCAS(&h->error, 0ull, code);
+}
+
+__device__ __forceinline__ bool error_raised(const WsHeader *h)
+{
+    return ld_relaxed(&h->error) != 0;
+}
+
+// ---- scans ---------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d)
+            v += t;
+    }
+    return v;
+}
+
+__device__ __forceinline__ u64 warp_sum64(u64 v)
+{
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, d);
+    return v;
+}
+
+// ---- decoupled look-back ---------------------------------------------------
+
+// Publish one value of a scan: slot first, then the tag with release order.
+__device__ __forceinline__ void publish(u64 *tag, u64 *slot, u64 value, u64 flag, u64 etag)
+{
+    st_relaxed(slot, value);
+    st_release(tag, etag | flag);
+}
+
+// Exclusive prefix of tile `tile` (> 0) for one scan (kVal: the delta
+// running sum, else the byte offsets), computed by one whole warp.  Each lane
+// watches one predecessor; a window of 32 is summed until some lane sees a
+// published inclusive prefix.  Every poll is bounded: after spin_limit polls
+// (backing off to ~1 us each), or as soon as another tile has raised an
+// error, it returns with ok = false and the caller records the failure.
+template <bool kVal>
+__device__ u64 lookback(TileStatus *st, u64 tile, u64 etag, u64 spin_limit, WsHeader *hdr,
+                        bool &ok)
+{
+    const int lane = threadIdx.x & 31;
+    u64 excl = 0;
+    long long base = (long long)tile - 1;
+    ok = true;
+    for (;;) {
+        long long p = base - lane;
+        u64 flag = kFlagPrefix, v = 0;
+        if (p >= 0) {
+            const u64 *tagp = kVal ? &st[p].val_tag : &st[p].off_tag;
+            u64 t = ld_acquire(tagp);
+            u64 spins = 0;
+            unsigned ns = 32;
+            while ((t & ~3ull) != etag || (t & 3ull) == kFlagNone) {
+                if (++spins > spin_limit || ((spins & 31) == 0 && error_raised(hdr))) {
+                    t = 0;
+                    break;
+                }
+                __nanosleep(ns);
+                if (ns < 1024)
+                    ns <<= 1;
+                t = ld_acquire(tagp);
+            }
+            flag = t & 3ull;
+            if (flag == kFlagPrefix)
+                v = ld_relaxed(kVal ? &st[p].val_pre : &st[p].off_pre);
+            else if (flag == kFlagAgg)
+                v = ld_relaxed(kVal ? &st[p].val_agg : &st[p].off_agg);
+        }
+        if (__any_sync(0xffffffffu, flag == kFlagNone)) {
+            ok = false;
+            return 0;
+        }
+        unsigned pm = __ballot_sync(0xffffffffu, flag == kFlagPrefix);
+        int k = pm ? __ffs(pm) - 1 : 31;
+        excl += warp_sum64(lane <= k ? v : 0ull);
+        if (pm)
+            break;
+        base -= 32;
+    }
+    return kVal ? (excl & 0xffffffffull) : excl;
+}
+
+// The last CTA to finish writes the launch's result and readies the
+// workspace for the next launch (counters to zero, epoch + 1).
+__device__ __forceinline__ void finish_launch(WsHeader *hdr, DeviceResult *result)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        u64 done = atomicAdd(&hdr->done_counter, 1ull);
+        if (done == (u64)gridDim.x - 1) {
+            __threadfence();
+            u64 err = ld_relaxed(&hdr->error);
+            u64 total = ld_relaxed(&hdr->total);
+            result->bytes = err ? ~0ull : total;
+            result->status = err;
+            st_relaxed(&hdr->error, 0);
+            st_relaxed(&hdr->total, 0);
+            st_relaxed(&hdr->tile_counter, 0);
+            st_relaxed(&hdr->done_counter, 0);
+            st_relaxed(&hdr->epoch, ld_relaxed(&hdr->epoch) + 1);
+        }
+    }
+}
+
+}  // namespace svb

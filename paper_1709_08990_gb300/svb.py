@@ -1,0 +1,220 @@
+"""Python binding of libsvb.so: argument marshalling only.
+
+Each function has the name and argument order of its C counterpart in
+``include/svb.h``; device buffers are passed as torch CUDA tensors (or raw
+integer device addresses), sizes as ints.  Every computation runs in the
+library's CUDA kernels; there is no host or PyTorch fallback, and importing
+a function without the built library raises.
+
+Synchronous calls run on torch's current CUDA stream (``svb_set_stream`` is
+called with it before each call).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsvb.so")
+ERROR = (1 << 64) - 1  # SVB_ERROR
+
+SVB_OK, SVB_EINVAL, SVB_ETRUNCATED, SVB_ECUDA, SVB_ETIMEOUT, SVB_ENOMEM = range(6)
+
+
+class SvbError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {error_string(status)} (status {status})")
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libsvb.so; raises when it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        sz, u32, u64, i32, vp = (ctypes.c_size_t, ctypes.c_uint32, ctypes.c_uint64,
+                                 ctypes.c_int, ctypes.c_void_p)
+        sig = {
+            "svb_max_compressed_size": ([sz], sz),
+            "svb_compressed_size_from_control": ([vp, sz], sz),
+            "svb_encode": ([vp, sz, vp], sz),
+            "svb_decode": ([vp, sz, vp], sz),
+            "svb_delta_encode": ([vp, sz, vp, u32], sz),
+            "svb_delta_decode": ([vp, sz, vp, u32], sz),
+            "svb_decode_checked": ([vp, sz, sz, vp, u32, i32], sz),
+            "svb_decode_host": ([vp, sz, sz, vp, u32, i32, vp, vp], sz),
+            "svb_encode_host": ([vp, sz, vp, u32, i32, vp, vp], sz),
+            "svb_set_stream": ([vp], i32),
+            "svb_get_stream": ([], vp),
+            "svb_last_error": ([], i32),
+            "svb_error_string": ([i32], ctypes.c_char_p),
+            "svb_set_spin_limit": ([u64], None),
+            "svb_workspace_size": ([sz], sz),
+            "svb_workspace_init": ([vp, sz, vp], i32),
+            "svb_encode_async": ([vp, sz, vp, u32, i32, vp, vp, sz, vp], i32),
+            "svb_decode_async": ([vp, sz, sz, vp, u32, i32, vp, vp, sz, vp], i32),
+            "svb_testhook_lookback_timeout": ([vp, sz, vp, u64, vp, vp, sz, vp], i32),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _p(x) -> int:
+    """Device (or host) address of a tensor, array or integer."""
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(type(x))
+
+
+def _stream(stream=None) -> int:
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _sized(k: int, what: str) -> int:
+    if k == ERROR:
+        raise SvbError(lib().svb_last_error(), what)
+    return k
+
+
+def error_string(status: int) -> str:
+    return lib().svb_error_string(status).decode()
+
+
+def svb_max_compressed_size(n: int) -> int:
+    return lib().svb_max_compressed_size(n)
+
+
+def svb_compressed_size_from_control(h_ctrl, n: int) -> int:
+    return _sized(lib().svb_compressed_size_from_control(_p(h_ctrl), n),
+                  "svb_compressed_size_from_control")
+
+
+def svb_encode(inp, n: int, out) -> int:
+    lib().svb_set_stream(_stream())
+    return _sized(lib().svb_encode(_p(inp), n, _p(out)), "svb_encode")
+
+
+def svb_decode(inp, n: int, out) -> int:
+    lib().svb_set_stream(_stream())
+    return _sized(lib().svb_decode(_p(inp), n, _p(out)), "svb_decode")
+
+
+def svb_delta_encode(inp, n: int, out, prev: int) -> int:
+    lib().svb_set_stream(_stream())
+    return _sized(lib().svb_delta_encode(_p(inp), n, _p(out), prev & 0xFFFFFFFF),
+                  "svb_delta_encode")
+
+
+def svb_delta_decode(inp, n: int, out, prev: int) -> int:
+    lib().svb_set_stream(_stream())
+    return _sized(lib().svb_delta_decode(_p(inp), n, _p(out), prev & 0xFFFFFFFF),
+                  "svb_delta_decode")
+
+
+def svb_decode_checked(inp, in_len: int, n: int, out, prev: int, delta: int) -> int:
+    lib().svb_set_stream(_stream())
+    return _sized(lib().svb_decode_checked(_p(inp), in_len, n, _p(out), prev & 0xFFFFFFFF,
+                                           int(delta)), "svb_decode_checked")
+
+
+def svb_decode_host(h_in, in_len: int, n: int, h_out, prev: int, delta: int, d_in, d_out) -> int:
+    lib().svb_set_stream(_stream())
+    return _sized(lib().svb_decode_host(_p(h_in), in_len, n, _p(h_out), prev & 0xFFFFFFFF,
+                                        int(delta), _p(d_in), _p(d_out)), "svb_decode_host")
+
+
+def svb_encode_host(h_in, n: int, h_out, prev: int, delta: int, d_in, d_out) -> int:
+    lib().svb_set_stream(_stream())
+    return _sized(lib().svb_encode_host(_p(h_in), n, _p(h_out), prev & 0xFFFFFFFF,
+                                        int(delta), _p(d_in), _p(d_out)), "svb_encode_host")
+
+
+def svb_set_spin_limit(iterations: int) -> None:
+    lib().svb_set_spin_limit(iterations)
+
+
+def svb_last_error() -> int:
+    return lib().svb_last_error()
+
+
+def svb_workspace_size(n: int) -> int:
+    return lib().svb_workspace_size(n)
+
+
+def svb_workspace_init(ws, ws_bytes: int, stream=None) -> int:
+    return lib().svb_workspace_init(_p(ws), ws_bytes, _stream(stream))
+
+
+def svb_encode_async(inp, n, out, prev, delta, d_result, ws, ws_bytes, stream=None) -> int:
+    return lib().svb_encode_async(_p(inp), n, _p(out), prev & 0xFFFFFFFF, int(delta),
+                                  _p(d_result), _p(ws), ws_bytes, _stream(stream))
+
+
+def svb_decode_async(inp, in_len, n, out, prev, delta, d_result, ws, ws_bytes, stream=None) -> int:
+    return lib().svb_decode_async(_p(inp), in_len, n, _p(out), prev & 0xFFFFFFFF, int(delta),
+                                  _p(d_result), _p(ws), ws_bytes, _stream(stream))
+
+
+def svb_testhook_lookback_timeout(stream_in, n, out, spin_limit, d_result, ws, ws_bytes,
+                                  stream=None) -> int:
+    return lib().svb_testhook_lookback_timeout(_p(stream_in), n, _p(out), spin_limit,
+                                               _p(d_result), _p(ws), ws_bytes, _stream(stream))
+
+
+# ---- tensor conveniences (allocation through torch, compute in the library) --
+
+def encode(x, delta: bool = False, prev: int = 0):
+    """Compressed stream (uint8 CUDA tensor, exact length) of a CUDA tensor of
+    4-byte integers."""
+    import torch
+    n = x.numel()
+    out = torch.empty(max(1, svb_max_compressed_size(n)), dtype=torch.uint8, device=x.device)
+    if delta:
+        k = svb_delta_encode(x, n, out, prev)
+    else:
+        k = svb_encode(x, n, out)
+    return out[:k]
+
+
+def decode(stream, n: int, delta: bool = False, prev: int = 0, checked: bool = True):
+    """Decoded int32-typed CUDA tensor (the bits of the uint32 values)."""
+    import torch
+    out = torch.empty(max(1, n), dtype=torch.int32, device=stream.device)
+    if checked:
+        svb_decode_checked(stream, stream.numel(), n, out, prev, int(delta))
+    elif delta:
+        svb_delta_decode(stream, n, out, prev)
+    else:
+        svb_decode(stream, n, out)
+    return out[:n]
+
+
+def svb_error_string(status: int) -> str:
+    return error_string(status)
+
+
+def svb_set_stream(stream) -> int:
+    return lib().svb_set_stream(_stream(stream))
+
+
+def svb_get_stream() -> int:
+    return lib().svb_get_stream() or 0

@@ -1,0 +1,73 @@
+"""The C ABI library builds, loads and exports every symbol include/svb.h
+declares; its host-side size helpers agree with the oracle (no GPU needed)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1709_08990_gb300 import _build, svb
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "svb.h")
+
+
+def declared_functions(path: str = HEADER) -> list[str]:
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return sorted(set(re.findall(r"\b(svb_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return svb.lib()
+
+
+def test_header_declares_the_codec_calls():
+    names = declared_functions()
+    for f in ("svb_encode", "svb_decode", "svb_delta_encode", "svb_delta_decode",
+              "svb_decode_checked", "svb_encode_async", "svb_decode_async",
+              "svb_max_compressed_size", "svb_last_error"):
+        assert f in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    raw = ctypes.CDLL(svb.LIB_PATH)
+    missing = [f for f in declared_functions() if not hasattr(raw, f)]
+    assert missing == []
+
+
+def test_binding_has_every_declared_name():
+    missing = [f for f in declared_functions() if not hasattr(svb, f)]
+    assert missing == []
+
+
+def test_max_compressed_size_matches_oracle(lib):
+    for n in [0, 1, 2, 3, 4, 5, 4095, 4096, 4097, 1 << 30, (1 << 32) + 3]:
+        assert svb.svb_max_compressed_size(n) == oracle.max_compressed_size(n)
+
+
+def test_size_from_control_matches_oracle(lib):
+    rng = np.random.default_rng(5)
+    for n in [1, 2, 3, 4, 5, 17, 1000, 4099]:
+        L = rng.integers(1, 5, n)
+        x = (rng.integers(0, 1 << 32, n, dtype=np.uint64) >> (8 * (4 - L)).astype(np.uint64)).astype(np.uint32)
+        s = oracle.encode(x)
+        ctrl = np.ascontiguousarray(s[: (n + 3) // 4])
+        assert svb.svb_compressed_size_from_control(ctrl, n) == s.size
+        # pad fields of the last control byte carry no bytes
+        if n % 4:
+            ctrl2 = ctrl.copy()
+            ctrl2[-1] |= np.uint8((0xFF << (2 * (n % 4))) & 0xFF)
+            assert svb.svb_compressed_size_from_control(ctrl2, n) == s.size
+
+
+def test_error_strings(lib):
+    for code in range(6):
+        assert svb.error_string(code)

@@ -1,0 +1,239 @@
+"""GPU codec against the oracle, bit for bit, through the C ABI.
+
+Sizes span several 4096-integer tiles with ragged tails, every tail n mod 4,
+misaligned buffers, and the three single-array workloads at full size.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1709_08990_gb300 import svb
+from paper_1709_08990_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def to_dev(a: np.ndarray):
+    if a.dtype == np.uint32:
+        a = a.view(np.int32)
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def host_u32(t) -> np.ndarray:
+    return t.cpu().numpy().view(np.uint32)
+
+
+SIZES = [1, 2, 3, 4, 5, 7, 8, 15, 16, 17, 1023, 1024, 1025, 4095, 4096, 4097,
+         3 * 4096 - 3, 3 * 4096 + 3, 8191, 8192, 8193, 65541, 1_000_003]
+
+
+def values(kind: str, n: int, seed: int = 0) -> np.ndarray:
+    if kind == "uniform":
+        return W.uniform_lengths(100 + seed, n)
+    if kind == "skewed":
+        return W.skewed_lengths(200 + seed, n)
+    if kind == "sorted":
+        return W.sorted_geometric(300 + seed, n, 16.0, 0)
+    if kind == "zeros":
+        return np.zeros(n, dtype=np.uint32)
+    if kind == "max":
+        return np.full(n, 0xFFFFFFFF, dtype=np.uint32)
+    raise KeyError(kind)
+
+
+@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("kind", ["uniform", "skewed", "sorted"])
+@pytest.mark.parametrize("delta", [False, True])
+def test_encode_decode_parity(n, kind, delta):
+    x = values(kind, n)
+    prev = 0 if kind == "sorted" else 0x9E3779B9
+    want = oracle.encode(x, prev=prev, delta=delta)
+    got = svb.encode(to_dev(x), delta=delta, prev=prev).cpu().numpy()
+    assert got.size == want.size
+    assert np.array_equal(got, want)
+    back = svb.decode(to_dev(want), n, delta=delta, prev=prev)
+    assert np.array_equal(host_u32(back), x)
+
+
+@pytest.mark.parametrize("kind", ["zeros", "max"])
+@pytest.mark.parametrize("n", [1, 6, 4096, 4099, 70001])
+def test_uniform_length_extremes(kind, n):
+    x = values(kind, n)
+    for delta in (False, True):
+        want = oracle.encode(x, delta=delta)
+        got = svb.encode(to_dev(x), delta=delta).cpu().numpy()
+        assert np.array_equal(got, want)
+        assert np.array_equal(host_u32(svb.decode(to_dev(want), n, delta=delta)), x)
+
+
+@pytest.mark.parametrize("n", [5, 4097, 100_003])
+def test_random_byte_streams_decode_like_oracle(n):
+    """Arbitrary control and data bytes, non-minimal codes included."""
+    rng = np.random.default_rng(n)
+    stream = rng.integers(0, 256, (n + 3) // 4 + 4 * n, dtype=np.uint8)
+    for delta, prev in ((False, 0), (True, 77)):
+        want, k = oracle.decode(stream, n, prev=prev, delta=delta)
+        assert k != oracle.ERROR
+        d_out = torch.empty(n, dtype=torch.int32, device=DEV)
+        got_k = svb.svb_decode_checked(to_dev(stream), stream.size, n, d_out, prev, int(delta))
+        assert got_k == k
+        assert np.array_equal(host_u32(d_out), want)
+
+
+@pytest.mark.parametrize("off_bytes,off_words", [(1, 1), (3, 2), (7, 3), (13, 1), (0, 2)])
+def test_misaligned_buffers(off_bytes, off_words):
+    """Streams at any byte offset, integer arrays 4-byte but not 16-byte aligned."""
+    n = 3 * 4096 + 7
+    x = values("uniform", n, 3)
+    want = oracle.encode(x)
+    xbuf = torch.zeros(n + 8, dtype=torch.int32, device=DEV)
+    xin = xbuf[off_words:off_words + n]
+    xin.copy_(to_dev(x))
+    out = torch.zeros(want.size + 64, dtype=torch.uint8, device=DEV)
+    k = svb.svb_encode(xin, n, out[off_bytes:])
+    assert k == want.size
+    assert np.array_equal(out[off_bytes:off_bytes + k].cpu().numpy(), want)
+    sbuf = torch.zeros(want.size + 64, dtype=torch.uint8, device=DEV)
+    sbuf[off_bytes:off_bytes + want.size] = to_dev(want)
+    obuf = torch.zeros(n + 8, dtype=torch.int32, device=DEV)
+    o = obuf[off_words:off_words + n]
+    k = svb.svb_decode(sbuf[off_bytes:], n, o)
+    assert k == want.size
+    assert np.array_equal(host_u32(o), x)
+    for delta in (True,):
+        wd = oracle.encode(x, delta=True, prev=5)
+        sbuf[off_bytes:off_bytes + wd.size] = to_dev(wd)
+        k = svb.svb_delta_decode(sbuf[off_bytes:], n, o, 5)
+        assert k == wd.size and np.array_equal(host_u32(o), x)
+
+
+def test_empty_input_returns_zero():
+    t = torch.zeros(16, dtype=torch.uint8, device=DEV)
+    o = torch.zeros(4, dtype=torch.int32, device=DEV)
+    assert svb.svb_encode(o, 0, t) == 0
+    assert svb.svb_decode(t, 0, o) == 0
+    assert svb.svb_delta_decode(t, 0, o, 5) == 0
+
+
+def test_truncated_stream_is_reported():
+    n = 10_000
+    x = values("uniform", n, 9)
+    s = oracle.encode(x)
+    d = to_dev(s)
+    out = torch.zeros(n, dtype=torch.int32, device=DEV)
+    for cut in (s.size - 1, s.size - 17, (n + 3) // 4 + 3, (n + 3) // 4 - 1):
+        with pytest.raises(svb.SvbError) as e:
+            svb.svb_decode_checked(d, cut, n, out, 0, 0)
+        assert e.value.status == svb.SVB_ETRUNCATED
+    # and a complete stream still decodes afterwards
+    assert svb.svb_decode_checked(d, s.size, n, out, 0, 0) == s.size
+    assert np.array_equal(host_u32(out), x)
+
+
+def test_null_pointers_rejected():
+    lib = svb.lib()
+    assert lib.svb_encode(None, 10, None) == svb.ERROR
+    assert lib.svb_last_error() == svb.SVB_EINVAL
+    assert lib.svb_decode(None, 10, None) == svb.ERROR
+    assert lib.svb_last_error() == svb.SVB_EINVAL
+
+
+def test_async_calls_share_a_workspace():
+    """Several launches in a row on one caller-owned workspace (the tile
+    records of earlier launches must never be mistaken for current ones)."""
+    n = 50_000
+    ws_bytes = svb.svb_workspace_size(n)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=DEV)
+    res = torch.zeros(2, dtype=torch.int64, device=DEV)
+    assert svb.svb_workspace_init(ws, ws_bytes) == 0
+    for i, kind in enumerate(["uniform", "sorted", "skewed", "uniform"]):
+        m = n - 1000 * i
+        x = values(kind, m, i)
+        delta = kind == "sorted"
+        want = oracle.encode(x, delta=delta)
+        out = torch.empty(svb.svb_max_compressed_size(m), dtype=torch.uint8, device=DEV)
+        assert svb.svb_encode_async(to_dev(x), m, out, 0, delta, res, ws, ws_bytes) == 0
+        r = res.cpu().numpy()
+        assert r[1] == 0 and r[0] == want.size
+        assert np.array_equal(out[: want.size].cpu().numpy(), want)
+        dec = torch.empty(m, dtype=torch.int32, device=DEV)
+        assert svb.svb_decode_async(to_dev(want), want.size, m, dec, 0, delta, res, ws, ws_bytes) == 0
+        r = res.cpu().numpy()
+        assert r[1] == 0 and r[0] == want.size
+        assert np.array_equal(host_u32(dec), x)
+
+
+def test_workspace_too_small_rejected():
+    n = 100_000
+    ws = torch.zeros(256, dtype=torch.uint8, device=DEV)
+    res = torch.zeros(2, dtype=torch.int64, device=DEV)
+    x = torch.zeros(n, dtype=torch.int32, device=DEV)
+    out = torch.empty(svb.svb_max_compressed_size(n), dtype=torch.uint8, device=DEV)
+    assert svb.svb_encode_async(x, n, out, 0, 0, res, ws, 256) == svb.SVB_EINVAL
+
+
+def test_lookback_timeout_is_reported_and_context_survives():
+    """A tile whose predecessor never publishes gives up after its spin limit
+    and reports SVB_ETIMEOUT; the next call on the same workspace works."""
+    n = 3 * 4096
+    x = values("uniform", n, 4)
+    s = oracle.encode(x)
+    d = to_dev(s)
+    ws_bytes = svb.svb_workspace_size(n)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=DEV)
+    svb.svb_workspace_init(ws, ws_bytes)
+    res = torch.zeros(2, dtype=torch.int64, device=DEV)
+    out = torch.zeros(n, dtype=torch.int32, device=DEV)
+    assert svb.svb_testhook_lookback_timeout(d, n, out, 2000, res, ws, ws_bytes) == 0
+    r = res.cpu().numpy()
+    assert r[1] == svb.SVB_ETIMEOUT
+    assert r[0] == -1  # SVB_ERROR as int64
+    assert svb.svb_decode_async(d, s.size, n, out, 0, 0, res, ws, ws_bytes) == 0
+    r = res.cpu().numpy()
+    assert r[1] == 0 and r[0] == s.size
+    assert np.array_equal(host_u32(out), x)
+
+
+def test_host_buffer_forms():
+    n = 123_457
+    x = values("sorted", n, 5)
+    want = oracle.encode(x, delta=True, prev=0)
+    d_in = torch.empty(4 * n, dtype=torch.uint8, device=DEV)
+    d_out = torch.empty(svb.svb_max_compressed_size(n), dtype=torch.uint8, device=DEV)
+    h_out = np.zeros(svb.svb_max_compressed_size(n), dtype=np.uint8)
+    k = svb.svb_encode_host(x, n, h_out, 0, 1, d_in, d_out)
+    assert k == want.size and np.array_equal(h_out[:k], want)
+    h_back = np.zeros(n, dtype=np.uint32)
+    k2 = svb.svb_decode_host(want, want.size, n, h_back, 0, 1, d_out, d_in)
+    assert k2 == want.size and np.array_equal(h_back, x)
+
+
+@pytest.mark.parametrize("name", ["uniform_1m", "delta_64m"])
+def test_full_size_workloads(name):
+    w = W.WORKLOADS[name]
+    x = W.array_values(name)
+    want = oracle.encode(x, delta=w.delta)
+    got = svb.encode(to_dev(x), delta=w.delta)
+    assert got.numel() == want.size
+    assert np.array_equal(got.cpu().numpy(), want)
+    back = svb.decode(got, x.size, delta=w.delta, checked=False)
+    assert np.array_equal(host_u32(back), x)
+
+
+def test_full_size_skewed_1g():
+    """n = 2^30, the roofline workload: 2 GiB stream, offsets past 2^31."""
+    x = W.array_values("skewed_1g")
+    want = oracle.encode(x)
+    assert want.size > (1 << 31)
+    d_x = to_dev(x)
+    got = svb.encode(d_x)
+    assert got.numel() == want.size
+    assert np.array_equal(got.cpu().numpy(), want)
+    del d_x
+    back = svb.decode(got, x.size, checked=False)
+    assert np.array_equal(host_u32(back), x)
