@@ -331,6 +331,13 @@ def main():
     # ---- secondary workloads --------------------------------------------------
     if not args.no_secondary:
         sec = {}
+        svb.svb_set_decode_variant(svb.SVB_DECODE_SINGLE_PASS)
+        ms1 = _time(step, 50, stream)
+        svb.svb_set_decode_variant(svb.SVB_DECODE_AUTO)
+        ok1 = torch.equal(d_out[:1 << 20], h_x[:1 << 20].to(dev))
+        sec["decode_single_pass_" + args.workload] = {
+            "gints_per_s": n / ms1 / 1e6, "ms": ms1, "frac": alg_bytes / (ms1 / 1e3) / 1e9 /
+            peaks["hbm_gbs"], "verified_prefix": bool(ok1)}
         del d_out, d_stream
         torch.cuda.empty_cache()
         sec["encode_" + args.workload] = time_encode(svb, W, args.workload, dev, peaks, h_x)

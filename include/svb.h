@@ -8,10 +8,10 @@
  * takes `length` bytes of the data stream, least significant byte first.
  * The length of v is ceil(log_256(v + 1)) bytes, one byte for v = 0
  * (Sec. 3).  Pad fields of an incomplete last control byte are written as 0
- * and ignored when decoding.  n is not stored in the stream (Sec. 4: "we
- * record how many integers N are compressed"); every call takes it.
+ * and ignored when decoding.  n is not stored in the stream (Sec. 4 keeps
+ * the count outside it); every call takes it.
  *
- * Differential coding (Sec. 1, Sec. 2 "Differential Coding", Sec. 5): the
+ * Differential coding (Sec. 1, Sec. 2, Sec. 5): the
  * stream holds delta_1 = x_1 - prev, delta_i = x_i - x_{i-1}, modulo 2^32;
  * decoding computes x_i = prev + delta_1 + ... + delta_i modulo 2^32.  The
  * paper starts from prev = 0; here the caller chooses prev.
@@ -127,6 +127,21 @@ const char *svb_error_string(int status);
  * poll, about a microsecond each at most).  0 restores the default, which is
  * also overridable with the environment variable SVB_LOOKBACK_SPIN_LIMIT. */
 void svb_set_spin_limit(uint64_t iterations);
+
+/* Decoder variant used by every decode call of this process:
+ *   SVB_DECODE_AUTO (0)        the default, currently SVB_DECODE_TWO_PASS;
+ *   SVB_DECODE_SINGLE_PASS (1) one kernel: each tile sums its control bytes,
+ *                              finds its data offset by a decoupled look-back
+ *                              over its predecessors, then decodes;
+ *   SVB_DECODE_TWO_PASS (2)    an offsets pass over the control stream, then
+ *                              a persistent decode with bulk-copy staging.
+ * Both give identical results.  Returns SVB_EINVAL for an unknown variant. */
+enum svb_decode_variant {
+    SVB_DECODE_AUTO = 0,
+    SVB_DECODE_SINGLE_PASS = 1,
+    SVB_DECODE_TWO_PASS = 2
+};
+int svb_set_decode_variant(int variant);
 
 /* ---- async forms with a caller-owned workspace ------------------------- */
 

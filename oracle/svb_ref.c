@@ -11,7 +11,7 @@
  * Every function below follows the paper's definition step by step, in the
  * paper's order, with no blocking, fusion or reordering:
  *   1. differential coding: delta_1 = x_1 - prev, delta_i = x_i - x_{i-1}
- *      (Sec. 1; Sec. 5 "posting lists"; all arithmetic mod 2^32);
+ *      (Sec. 1; Sec. 5 on posting lists; all arithmetic mod 2^32);
  *   2. byte length of each coded value, ceil(log_256(v + 1)) in {1,2,3,4}
  *      (Sec. 3, the varint-GB length rule), with v = 0 taking one byte
  *      because code 00 means one byte (Sec. 4: an all-zero control byte
@@ -24,11 +24,11 @@
  *      coded value's length-many low-order bytes, least significant first
  *      (Sec. 2: pshufb zero-fills the high bytes of each 32-bit lane);
  *   5. the compressed size is ceil(N/4) + sum of lengths (Sec. 4; Sec. 5
- *      "almost exactly the same storage" as varint-GB).
+ *      reports the same storage as varint-GB, whose blocks have this size).
  * Decoding reverses these steps (Sec. 4, Fig. 4): the code of each integer
  * gives its byte count C, the low C bytes are read little-endian, and for
  * differential coding a prefix sum restores x_i = x_{i-1} + delta_i
- * (Sec. 2 "Differential Coding").  The decoder accepts any code, including
+ * (Sec. 2, differential coding).  The decoder accepts any code, including
  * non-minimal ones, ignores the pad fields of an incomplete last control
  * byte, and never reads past in_len.
  *

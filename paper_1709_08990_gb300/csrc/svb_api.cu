@@ -20,6 +20,7 @@ namespace {
 thread_local int t_last_error = SVB_OK;
 thread_local cudaStream_t t_stream = nullptr;
 std::atomic<u64> g_spin_limit{0};
+std::atomic<int> g_decode_variant{SVB_DECODE_AUTO};
 
 constexpr u64 kDefaultSpinLimit = 1ull << 21;  // ~2 s of polling at most
 
@@ -40,16 +41,18 @@ u64 spin_limit()
     return env;
 }
 
+int decode_dispatch(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, uint32_t prev,
+                    bool delta, void *ws, svb::DeviceResult *r, cudaStream_t s)
+{
+    if (g_decode_variant.load(std::memory_order_relaxed) == SVB_DECODE_SINGLE_PASS)
+        return svb::launch_decode(in, in_len, n, out, prev, delta, ws, r, s, spin_limit());
+    return svb::launch_decode_tiled(in, in_len, n, out, prev, delta, ws, r, s, spin_limit());
+}
+
 size_t set_error(int code)
 {
     t_last_error = code;
     return code == SVB_OK ? 0 : SVB_ERROR;
-}
-
-u64 tiles_for(size_t n)
-{
-    u64 nq = ((u64)n + 3) / 4;
-    return (nq + svb::kMinQuadsPerTile - 1) / svb::kMinQuadsPerTile;
 }
 
 // Workspace kept per device for the synchronous calls.  The calls on one
@@ -131,7 +134,7 @@ size_t decode_sync(const uint8_t *in, u64 in_len, size_t n, uint32_t *out, uint3
     if (in_len < ((u64)n + 3) / 4)
         return set_error(SVB_ETRUNCATED);
     return run_sync(n, [&](void *ws, svb::DeviceResult *r, cudaStream_t s) {
-        return svb::launch_decode(in, in_len, n, out, prev, delta, ws, r, s, spin_limit());
+        return decode_dispatch(in, in_len, n, out, prev, delta, ws, r, s);
     });
 }
 
@@ -258,6 +261,14 @@ const char *svb_error_string(int status)
     }
 }
 
+int svb_set_decode_variant(int variant)
+{
+    if (variant < SVB_DECODE_AUTO || variant > SVB_DECODE_TWO_PASS)
+        return SVB_EINVAL;
+    g_decode_variant.store(variant, std::memory_order_relaxed);
+    return SVB_OK;
+}
+
 void svb_set_spin_limit(uint64_t iterations)
 {
     g_spin_limit.store(iterations, std::memory_order_relaxed);
@@ -265,12 +276,12 @@ void svb_set_spin_limit(uint64_t iterations)
 
 size_t svb_workspace_size(size_t n)
 {
-    return svb::kStatusOffset + sizeof(svb::TileStatus) * std::max<u64>(1, tiles_for(n));
+    return svb::ws_layout(n).total;
 }
 
 int svb_workspace_init(void *ws, size_t ws_bytes, svb_stream_t stream)
 {
-    if (!ws || ws_bytes < svb::kStatusOffset)
+    if (!ws || ws_bytes < svb::kOffsetsOffset)
         return SVB_EINVAL;
     return cudaMemsetAsync(ws, 0, ws_bytes, reinterpret_cast<cudaStream_t>(stream)) ==
                    cudaSuccess
@@ -307,8 +318,8 @@ int svb_decode_async(const uint8_t *in, size_t in_len, size_t n, uint32_t *out,
         return SVB_EINVAL;
     if (in_len < ((u64)n + 3) / 4)
         return SVB_ETRUNCATED;
-    return svb::launch_decode(in, in_len, n, out, prev, delta != 0, ws,
-                              reinterpret_cast<svb::DeviceResult *>(d_result), s, spin_limit());
+    return decode_dispatch(in, in_len, n, out, prev, delta != 0, ws,
+                           reinterpret_cast<svb::DeviceResult *>(d_result), s);
 }
 
 int svb_testhook_lookback_timeout(const uint8_t *stream_in, size_t n, uint32_t *out,

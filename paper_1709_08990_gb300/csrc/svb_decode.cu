@@ -337,7 +337,7 @@ int launch_decode(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, uint32_t 
     a.nquads = (n + 3) / 4;
     a.ntiles = (a.nquads + kDecQuads - 1) / kDecQuads;
     a.hdr = reinterpret_cast<WsHeader *>(ws);
-    a.st = reinterpret_cast<TileStatus *>(static_cast<char *>(ws) + kStatusOffset);
+    a.st = reinterpret_cast<TileStatus *>(static_cast<char *>(ws) + ws_layout(n).status);
     a.result = result;
     a.spin_limit = spin_limit;
     a.tile_base = tile_base;

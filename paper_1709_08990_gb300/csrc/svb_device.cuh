@@ -4,8 +4,8 @@
 // aggregates into exclusive prefixes in one pass.
 //
 // The paper's decoder walks the stream serially: each control byte tells how
-// far the data pointer moves (Sec. 4, Fig. 4), the dependency the paper
-// blames for varint-GB's slowness (Sec. 4, "strong data dependency").  On the
+// far the data pointer moves (Sec. 4, Fig. 4), the dependency that Sec. 4
+// names as the reason varint-GB resists vectorisation.  On the
 // GPU that chain becomes a prefix sum of the per-quad byte counts over the
 // whole stream; tiles compute their own sums from their control bytes and
 // chain them with a decoupled look-back (a single-pass scan: each tile
@@ -40,18 +40,44 @@ struct __align__(64) TileStatus {
     u64 pad0, pad1;
 };
 
-// Workspace layout: [header 128 B][result 16 B, padded to 128 B][TileStatus...]
+// Workspace layout (see ws_layout): [header 128 B][result 16 B, padded to
+// 128 B][tile offsets: u64 x (tiles + 1)][TileStatus x tiles]
 struct __align__(128) WsHeader {
-    u64 tile_counter;   // next dynamic tile id
+    u64 tile_counter;   // next dynamic tile id (the decode or encode kernel)
     u64 done_counter;   // CTAs that have finished this launch
     u64 epoch;          // launches finished on this workspace
     u64 error;          // first error of this launch, 0 if none
     u64 total;          // stream size, written by the last tile
-    u64 pad[11];
+    u64 a_counter;      // dynamic CTA id of the offsets pass
+    u64 a_done;         // CTAs of the offsets pass that have finished
+    u64 pad[9];
 };
 
 constexpr size_t kResultOffset = 128;
-constexpr size_t kStatusOffset = 256;
+constexpr size_t kOffsetsOffset = 256;
+
+struct WsLayout {
+    size_t offs;     // byte offset of the tile-offset array
+    size_t status;   // byte offset of the TileStatus array
+    size_t total;    // workspace bytes
+};
+
+// Layout for up to `tiles` tiles (of any tile size >= kMinQuadsPerTile quads).
+inline WsLayout ws_layout_for_tiles(u64 tiles)
+{
+    WsLayout l;
+    l.offs = kOffsetsOffset;
+    size_t st = l.offs + 8 * (tiles + 1);
+    l.status = (st + 63) & ~(size_t)63;
+    l.total = l.status + sizeof(TileStatus) * (tiles ? tiles : 1);
+    return l;
+}
+
+inline WsLayout ws_layout(u64 n)
+{
+    u64 nq = (n + 3) / 4;
+    return ws_layout_for_tiles((nq + kMinQuadsPerTile - 1) / kMinQuadsPerTile);
+}
 
 struct DeviceResult {
     u64 bytes;
@@ -143,54 +169,82 @@ __device__ __forceinline__ void publish(u64 *tag, u64 *slot, u64 value, u64 flag
     st_release(tag, etag | flag);
 }
 
-// Exclusive prefix of tile `tile` (> 0) for one scan (kVal: the delta
-// running sum, else the byte offsets), computed by one whole warp.  Each lane
-// watches one predecessor; a window of 32 is summed until some lane sees a
-// published inclusive prefix.  Every poll is bounded: after spin_limit polls
-// (backing off to ~1 us each), or as soon as another tile has raised an
+constexpr int kLookbackPerLane = 4;  // predecessors each lane inspects per round trip
+
+// Exclusive prefix of tile `tile` (> 0) for one scan (kVal: the delta running
+// sum, else the byte offsets), computed by one whole warp.  One round trip
+// inspects a window of 32 * kLookbackPerLane predecessors (lane l owns the
+// kLookbackPerLane nearest-to-farthest run starting l * kLookbackPerLane
+// tiles back); the window's values are summed up to the nearest published
+// inclusive prefix, or wholly and the next window is taken.  A window this
+// wide keeps the look-back shallow even when tiles are claimed faster than
+// one L2 round trip per 128 tiles.  Every poll is bounded: after spin_limit
+// polls (backing off to ~1 us each), or as soon as another tile has raised an
 // error, it returns with ok = false and the caller records the failure.
 template <bool kVal>
 __device__ u64 lookback(TileStatus *st, u64 tile, u64 etag, u64 spin_limit, WsHeader *hdr,
                         bool &ok)
 {
+    constexpr int K = kLookbackPerLane;
     const int lane = threadIdx.x & 31;
     u64 excl = 0;
     long long base = (long long)tile - 1;
     ok = true;
     for (;;) {
-        long long p = base - lane;
-        u64 flag = kFlagPrefix, v = 0;
-        if (p >= 0) {
-            const u64 *tagp = kVal ? &st[p].val_tag : &st[p].off_tag;
-            u64 t = ld_acquire(tagp);
+        u64 tags[K];
+#pragma unroll
+        for (int j = 0; j < K; j++) {
+            long long p = base - (lane * K + j);
+            tags[j] = p >= 0 ? ld_acquire(kVal ? &st[p].val_tag : &st[p].off_tag)
+                             : (etag | kFlagPrefix);
+        }
+        bool failed = false;
+#pragma unroll
+        for (int j = 0; j < K; j++) {
+            long long p = base - (lane * K + j);
             u64 spins = 0;
             unsigned ns = 32;
-            while ((t & ~3ull) != etag || (t & 3ull) == kFlagNone) {
+            while (!failed && p >= 0 &&
+                   ((tags[j] & ~3ull) != etag || (tags[j] & 3ull) == kFlagNone)) {
                 if (++spins > spin_limit || ((spins & 31) == 0 && error_raised(hdr))) {
-                    t = 0;
-                    break;
+                    failed = true;
+                } else {
+                    __nanosleep(ns);
+                    if (ns < 512)
+                        ns <<= 1;
+                    tags[j] = ld_acquire(kVal ? &st[p].val_tag : &st[p].off_tag);
                 }
-                __nanosleep(ns);
-                if (ns < 1024)
-                    ns <<= 1;
-                t = ld_acquire(tagp);
             }
-            flag = t & 3ull;
-            if (flag == kFlagPrefix)
-                v = ld_relaxed(kVal ? &st[p].val_pre : &st[p].off_pre);
-            else if (flag == kFlagAgg)
-                v = ld_relaxed(kVal ? &st[p].val_agg : &st[p].off_agg);
         }
-        if (__any_sync(0xffffffffu, flag == kFlagNone)) {
+        if (__any_sync(0xffffffffu, failed)) {
             ok = false;
             return 0;
         }
-        unsigned pm = __ballot_sync(0xffffffffu, flag == kFlagPrefix);
+        // Lane-local: sum up to and including this lane's nearest prefix.
+        u64 sum = 0;
+        bool has_prefix = false;
+#pragma unroll
+        for (int j = 0; j < K; j++) {
+            long long p = base - (lane * K + j);
+            if (!has_prefix) {
+                u64 v = 0;
+                if (p >= 0) {
+                    bool pre = (tags[j] & 3ull) == kFlagPrefix;
+                    v = ld_relaxed(kVal ? (pre ? &st[p].val_pre : &st[p].val_agg)
+                                        : (pre ? &st[p].off_pre : &st[p].off_agg));
+                    has_prefix = pre;
+                } else {
+                    has_prefix = true;
+                }
+                sum += v;
+            }
+        }
+        unsigned pm = __ballot_sync(0xffffffffu, has_prefix);
         int k = pm ? __ffs(pm) - 1 : 31;
-        excl += warp_sum64(lane <= k ? v : 0ull);
+        excl += warp_sum64(lane <= k ? sum : 0ull);
         if (pm)
             break;
-        base -= 32;
+        base -= 32 * K;
     }
     return kVal ? (excl & 0xffffffffull) : excl;
 }
@@ -216,6 +270,68 @@ __device__ __forceinline__ void finish_launch(WsHeader *hdr, DeviceResult *resul
             st_relaxed(&hdr->epoch, ld_relaxed(&hdr->epoch) + 1);
         }
     }
+}
+
+// ---- bulk asynchronous copies (TMA engine) and mbarriers -----------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of an mbarrier, at most `limit` polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, u64 limit)
+{
+    for (u64 i = 0; i < limit; i++) {
+        if (mbar_try_wait(bar, parity))
+            return true;
+        if (i > 64)
+            __nanosleep(64);
+    }
+    return false;
+}
+
+// Global -> shared bulk copy completing on an mbarrier.  dst and src 16-byte
+// aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
 }
 
 }  // namespace svb

@@ -226,7 +226,7 @@ int launch_encode(const uint32_t *in, u64 n, uint8_t *out, uint32_t prev, bool d
     a.nquads = (n + 3) / 4;
     a.ntiles = (a.nquads + kEncQuads - 1) / kEncQuads;
     a.hdr = reinterpret_cast<WsHeader *>(ws);
-    a.st = reinterpret_cast<TileStatus *>(static_cast<char *>(ws) + kStatusOffset);
+    a.st = reinterpret_cast<TileStatus *>(static_cast<char *>(ws) + ws_layout(n).status);
     a.result = result;
     a.spin_limit = spin_limit;
     a.prev = prev;

@@ -16,6 +16,12 @@ int launch_decode(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, uint32_t 
                   u64 spin_limit, u64 tile_base = 0, u64 grid_override = 0);
 u64 decode_tiles(u64 n);
 
+// Reduce-then-decode: control-stream offsets pass, then a persistent decode
+// with bulk-copy staging.
+int launch_decode_tiled(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, uint32_t prev,
+                        bool delta, void *ws, DeviceResult *result, cudaStream_t stream,
+                        u64 spin_limit);
+
 int launch_encode(const uint32_t *in, u64 n, uint8_t *out, uint32_t prev, bool delta, void *ws,
                   DeviceResult *result, cudaStream_t stream, u64 spin_limit);
 u64 encode_tiles(u64 n);

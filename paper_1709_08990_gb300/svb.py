@@ -55,6 +55,7 @@ def lib() -> ctypes.CDLL:
             "svb_last_error": ([], i32),
             "svb_error_string": ([i32], ctypes.c_char_p),
             "svb_set_spin_limit": ([u64], None),
+            "svb_set_decode_variant": ([i32], i32),
             "svb_workspace_size": ([sz], sz),
             "svb_workspace_init": ([vp, sz, vp], i32),
             "svb_encode_async": ([vp, sz, vp, u32, i32, vp, vp, sz, vp], i32),
@@ -150,6 +151,13 @@ def svb_encode_host(h_in, n: int, h_out, prev: int, delta: int, d_in, d_out) -> 
 
 def svb_set_spin_limit(iterations: int) -> None:
     lib().svb_set_spin_limit(iterations)
+
+
+SVB_DECODE_AUTO, SVB_DECODE_SINGLE_PASS, SVB_DECODE_TWO_PASS = 0, 1, 2
+
+
+def svb_set_decode_variant(variant: int) -> int:
+    return lib().svb_set_decode_variant(variant)
 
 
 def svb_last_error() -> int:

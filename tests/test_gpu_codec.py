@@ -18,6 +18,14 @@ pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 
 
+@pytest.fixture(params=[1, 2], ids=["single_pass", "two_pass"])
+def variant(request):
+    """Run a decode test under each decoder variant."""
+    assert svb.svb_set_decode_variant(request.param) == 0
+    yield request.param
+    svb.svb_set_decode_variant(0)
+
+
 def to_dev(a: np.ndarray):
     if a.dtype == np.uint32:
         a = a.view(np.int32)
@@ -49,7 +57,7 @@ def values(kind: str, n: int, seed: int = 0) -> np.ndarray:
 @pytest.mark.parametrize("n", SIZES)
 @pytest.mark.parametrize("kind", ["uniform", "skewed", "sorted"])
 @pytest.mark.parametrize("delta", [False, True])
-def test_encode_decode_parity(n, kind, delta):
+def test_encode_decode_parity(n, kind, delta, variant):
     x = values(kind, n)
     prev = 0 if kind == "sorted" else 0x9E3779B9
     want = oracle.encode(x, prev=prev, delta=delta)
@@ -62,7 +70,7 @@ def test_encode_decode_parity(n, kind, delta):
 
 @pytest.mark.parametrize("kind", ["zeros", "max"])
 @pytest.mark.parametrize("n", [1, 6, 4096, 4099, 70001])
-def test_uniform_length_extremes(kind, n):
+def test_uniform_length_extremes(kind, n, variant):
     x = values(kind, n)
     for delta in (False, True):
         want = oracle.encode(x, delta=delta)
@@ -72,7 +80,7 @@ def test_uniform_length_extremes(kind, n):
 
 
 @pytest.mark.parametrize("n", [5, 4097, 100_003])
-def test_random_byte_streams_decode_like_oracle(n):
+def test_random_byte_streams_decode_like_oracle(n, variant):
     """Arbitrary control and data bytes, non-minimal codes included."""
     rng = np.random.default_rng(n)
     stream = rng.integers(0, 256, (n + 3) // 4 + 4 * n, dtype=np.uint8)
@@ -86,7 +94,7 @@ def test_random_byte_streams_decode_like_oracle(n):
 
 
 @pytest.mark.parametrize("off_bytes,off_words", [(1, 1), (3, 2), (7, 3), (13, 1), (0, 2)])
-def test_misaligned_buffers(off_bytes, off_words):
+def test_misaligned_buffers(off_bytes, off_words, variant):
     """Streams at any byte offset, integer arrays 4-byte but not 16-byte aligned."""
     n = 3 * 4096 + 7
     x = values("uniform", n, 3)
@@ -105,11 +113,11 @@ def test_misaligned_buffers(off_bytes, off_words):
     k = svb.svb_decode(sbuf[off_bytes:], n, o)
     assert k == want.size
     assert np.array_equal(host_u32(o), x)
-    for delta in (True,):
-        wd = oracle.encode(x, delta=True, prev=5)
-        sbuf[off_bytes:off_bytes + wd.size] = to_dev(wd)
-        k = svb.svb_delta_decode(sbuf[off_bytes:], n, o, 5)
-        assert k == wd.size and np.array_equal(host_u32(o), x)
+    wd = oracle.encode(x, delta=True, prev=5)
+    dbuf = torch.zeros(wd.size + 64, dtype=torch.uint8, device=DEV)
+    dbuf[off_bytes:off_bytes + wd.size] = to_dev(wd)
+    k = svb.svb_delta_decode(dbuf[off_bytes:], n, o, 5)
+    assert k == wd.size and np.array_equal(host_u32(o), x)
 
 
 def test_empty_input_returns_zero():
@@ -120,7 +128,7 @@ def test_empty_input_returns_zero():
     assert svb.svb_delta_decode(t, 0, o, 5) == 0
 
 
-def test_truncated_stream_is_reported():
+def test_truncated_stream_is_reported(variant):
     n = 10_000
     x = values("uniform", n, 9)
     s = oracle.encode(x)
@@ -143,7 +151,7 @@ def test_null_pointers_rejected():
     assert lib.svb_last_error() == svb.SVB_EINVAL
 
 
-def test_async_calls_share_a_workspace():
+def test_async_calls_share_a_workspace(variant):
     """Several launches in a row on one caller-owned workspace (the tile
     records of earlier launches must never be mistaken for current ones)."""
     n = 50_000
@@ -214,7 +222,7 @@ def test_host_buffer_forms():
 
 
 @pytest.mark.parametrize("name", ["uniform_1m", "delta_64m"])
-def test_full_size_workloads(name):
+def test_full_size_workloads(name, variant):
     w = W.WORKLOADS[name]
     x = W.array_values(name)
     want = oracle.encode(x, delta=w.delta)
@@ -225,7 +233,7 @@ def test_full_size_workloads(name):
     assert np.array_equal(host_u32(back), x)
 
 
-def test_full_size_skewed_1g():
+def test_full_size_skewed_1g(variant):
     """n = 2^30, the roofline workload: 2 GiB stream, offsets past 2^31."""
     x = W.array_values("skewed_1g")
     want = oracle.encode(x)
