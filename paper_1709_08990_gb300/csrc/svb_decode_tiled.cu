@@ -8,16 +8,22 @@
 // alone, so:
 //   offsets_kernel   reads only the control stream (2 bits per integer) and
 //                    writes, for every tile of kTileQuads quads, its byte
-//                    offset in the data stream (a prefix sum of the per-quad
-//                    counts C, chained across CTAs by a decoupled look-back),
-//                    plus the stream's total size and the truncation check;
-//   decode_tiled     persistent CTAs claim tiles in order; the TMA engine
-//                    copies the next tile's control and data bytes into one
-//                    of two shared-memory stages (cp.async.bulk, completion on
-//                    an mbarrier) while the current tile is decoded, so every
-//                    SM keeps loads in flight without waiting on other CTAs.
+//                    offset in the data stream.  Persistent CTAs each sum a
+//                    contiguous range of tiles, chain the range totals with
+//                    one decoupled look-back, then add their base.  It also
+//                    writes the stream's size and checks it against in_len.
+//   decode_tiled     persistent CTAs with one producer warp and eight
+//                    consumer warps.  The producer claims tiles, reads their
+//                    offsets and has the TMA engine copy each tile's control
+//                    and data bytes into one of kStages shared-memory stages
+//                    (cp.async.bulk completing on the stage's "full"
+//                    mbarrier); consumers decode a full stage and release it
+//                    on its "empty" mbarrier.  Plain streams never wait on
+//                    another CTA; loads for later tiles are always in flight.
 // Differential streams add one look-back over the tiles' gap sums (the carry
-// of Sec. 2's prefix sum across tiles) before a tile's values are stored.
+// of Sec. 2's prefix sum across tiles) before a tile's values are stored; their
+// tiles are claimed from an atomic counter so that every predecessor of a
+// tile is already owned by a running CTA.
 //
 // Bytes outside the stream are never read: each tile's range is copied as its
 // 16-byte-aligned interior by the bulk engine plus a ragged head and tail of
@@ -34,16 +40,22 @@ constexpr int kTileRounds = kTileQuads / kThreads;  // quads per lane per tile
 constexpr int kTileData = 16 * kTileQuads;          // data bytes per tile, at most
 constexpr int kStageData = kTileData + 64;          // + 16-byte phase + 2-word read slack
 constexpr int kStageCtrl = kTileQuads + 32;
-constexpr int kOffTiles = 16;                       // tiles per CTA of the offsets pass
+constexpr int kStages = 4;
+constexpr int kDecBlock = kThreads + 32;            // 8 consumer warps + 1 producer warp
 constexpr u64 kBarrierPolls = 1ull << 24;           // bound on one mbarrier wait
+constexpr u64 kNoTile = ~0ull;
 
 // ---------------------------------------------------------------------------
 // Pass 1: tile offsets from the control stream.
 
+constexpr int kOffGroup = 16;                       // tiles summed per CTA iteration
+
 struct OffsetsArgs {
     const uint8_t *in;
     u64 in_len;
-    u64 n, nquads, ntiles, nctas;
+    u64 n, nquads, ntiles;
+    u64 groups;      // ceil(ntiles / kOffGroup)
+    u64 per_cta;     // groups per CTA
     u64 *offs;       // ntiles + 1 entries
     WsHeader *hdr;
     TileStatus *st;
@@ -56,15 +68,15 @@ struct OffsetsArgs {
 // fields of the last quad count nothing.
 __device__ __forceinline__ uint32_t chunk_bytes(uint4 v, u64 q, u64 nquads, uint32_t last_nints)
 {
+    uint32_t w[4] = {v.x, v.y, v.z, v.w};
     if (q + 16 < nquads) {  // no last quad inside: the common case
-        uint32_t w[4] = {v.x, v.y, v.z, v.w};
         uint32_t t = 64;
 #pragma unroll
         for (int i = 0; i < 4; i++)
             t += __popc(w[i] & 0x55555555u) + 2u * __popc(w[i] & 0xAAAAAAAAu);
         return t;
     }
-    uint32_t w[4] = {v.x, v.y, v.z, v.w}, t = 0;
+    uint32_t t = 0;
 #pragma unroll
     for (int b = 0; b < 16; b++) {
         u64 qq = q + b;
@@ -77,10 +89,41 @@ __device__ __forceinline__ uint32_t chunk_bytes(uint4 v, u64 q, u64 nquads, uint
     return t;
 }
 
+// Sum of the data bytes of 64 quads starting at q (one thread's share).
+__device__ __forceinline__ uint32_t sum64(const OffsetsArgs &a, u64 q, uint32_t last_nints)
+{
+    uint32_t sum = 0;
+    if (q >= a.nquads)
+        return 0;
+    if (a.in_aligned && q + 64 <= a.nquads) {
+        const uint4 *p = reinterpret_cast<const uint4 *>(a.in + q);
+        uint4 v[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+            v[i] = __ldg(p + i);
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+            sum += chunk_bytes(v[i], q + 16 * i, a.nquads, last_nints);
+    } else {
+        for (int i = 0; i < 4; i++) {
+            uint32_t w[4] = {0, 0, 0, 0};
+#pragma unroll
+            for (int b = 0; b < 16; b++) {
+                u64 qq = q + 16 * i + b;
+                if (qq < a.nquads)
+                    w[b >> 2] |= (uint32_t)__ldg(a.in + qq) << (8 * (b & 3));
+            }
+            sum += chunk_bytes(make_uint4(w[0], w[1], w[2], w[3]), q + 16 * i, a.nquads,
+                               last_nints);
+        }
+    }
+    return sum;
+}
+
 __global__ void __launch_bounds__(kThreads) offsets_kernel(OffsetsArgs a)
 {
-    __shared__ uint32_t s_tsum[kOffTiles];
-    __shared__ u64 s_cta, s_etag;
+    __shared__ uint32_t s_tsum[2][kOffGroup];
+    __shared__ u64 s_cta, s_etag, s_base;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
@@ -90,74 +133,68 @@ __global__ void __launch_bounds__(kThreads) offsets_kernel(OffsetsArgs a)
     __syncthreads();
     const u64 cta = s_cta, etag = s_etag;
     const uint32_t last_nints = (uint32_t)(a.n - 4 * (a.nquads - 1));
+    const u64 g0 = cta * a.per_cta;
+    const u64 g1 = min(g0 + a.per_cta, a.groups);
 
-    // Thread t sums control bytes [64t, 64t + 64) of this CTA's 16 tiles:
-    // 16 threads per tile.
-    const u64 q = cta * (u64)(kOffTiles * kTileQuads) + 64u * tid;
-    uint32_t sum = 0;
-    if (q < a.nquads) {
-        if (a.in_aligned && q + 64 <= a.nquads) {
-            const uint4 *p = reinterpret_cast<const uint4 *>(a.in + q);
-            uint4 v[4];
+    // Local offsets: each group of 16 tiles is 16 KB of control bytes, 64 per
+    // thread and 16 threads per tile; warp 0 keeps the running total.
+    u64 running = 0;  // meaningful in warp 0
+    int buf = 0;
+    for (u64 g = g0; g < g1; g++, buf ^= 1) {
+        const u64 q = g * (u64)(kOffGroup * kTileQuads) + 64u * tid;
+        uint32_t sum = sum64(a, q, last_nints);
 #pragma unroll
-            for (int i = 0; i < 4; i++)
-                v[i] = __ldg(p + i);
-#pragma unroll
-            for (int i = 0; i < 4; i++)
-                sum += chunk_bytes(v[i], q + 16 * i, a.nquads, last_nints);
-        } else {
-            for (int i = 0; i < 4; i++) {
-                uint32_t w[4] = {0, 0, 0, 0};
-#pragma unroll
-                for (int b = 0; b < 16; b++) {
-                    u64 qq = q + 16 * i + b;
-                    if (qq < a.nquads)
-                        w[b >> 2] |= (uint32_t)__ldg(a.in + qq) << (8 * (b & 3));
-                }
-                sum += chunk_bytes(make_uint4(w[0], w[1], w[2], w[3]), q + 16 * i, a.nquads,
-                                   last_nints);
-            }
+        for (int d = 8; d >= 1; d >>= 1)
+            sum += __shfl_xor_sync(0xffffffffu, sum, d);
+        if ((tid & 15) == 0)
+            s_tsum[buf][tid >> 4] = sum;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t ts = lane < kOffGroup ? s_tsum[buf][lane] : 0u;
+            uint32_t inc = warp_incl_scan(ts);
+            u64 tile = g * kOffGroup + lane;
+            if (lane < kOffGroup && tile < a.ntiles)
+                a.offs[tile] = running + (inc - ts);
+            running += __shfl_sync(0xffffffffu, inc, 31);
         }
+        // s_tsum is double-buffered: the next iteration writes the other half,
+        // and the barrier of that iteration orders this read before reuse.
     }
-#pragma unroll
-    for (int d = 8; d >= 1; d >>= 1)
-        sum += __shfl_xor_sync(0xffffffffu, sum, d);
-    if ((tid & 15) == 0)
-        s_tsum[tid >> 4] = sum;
-    __syncthreads();
 
+    // Chain the CTA totals, then add this CTA's base to its tiles.
     if (warp == 0) {
-        uint32_t ts = lane < kOffTiles ? s_tsum[lane] : 0u;
-        uint32_t inc = warp_incl_scan(ts);
-        uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
         TileStatus *me = &a.st[cta];
         u64 base = 0;
         bool ok = true;
         if (cta == 0) {
             if (lane == 0)
-                publish(&me->off_tag, &me->off_pre, total, kFlagPrefix, etag);
+                publish(&me->off_tag, &me->off_pre, running, kFlagPrefix, etag);
         } else {
             if (lane == 0)
-                publish(&me->off_tag, &me->off_agg, total, kFlagAgg, etag);
+                publish(&me->off_tag, &me->off_agg, running, kFlagAgg, etag);
             base = lookback<false>(a.st, cta, etag, a.spin_limit, a.hdr, ok);
             if (ok && lane == 0)
-                publish(&me->off_tag, &me->off_pre, base + total, kFlagPrefix, etag);
+                publish(&me->off_tag, &me->off_pre, base + running, kFlagPrefix, etag);
         }
-        if (!ok) {
-            if (lane == 0)
+        if (lane == 0) {
+            if (!ok)
                 raise_error(a.hdr, kErrTimeout);
-        } else {
-            u64 tile = cta * kOffTiles + lane;
-            if (lane < kOffTiles && tile < a.ntiles)
-                a.offs[tile] = base + (inc - ts);
-            if (cta == a.nctas - 1 && lane == 0) {
-                u64 stream = a.nquads + base + total;
-                a.offs[a.ntiles] = base + total;
+            if (ok && g1 == a.groups && g0 < g1) {  // the CTA holding the last tile
+                u64 stream = a.nquads + base + running;
+                a.offs[a.ntiles] = base + running;
                 st_relaxed(&a.hdr->total, stream);
                 if (stream > a.in_len)
                     raise_error(a.hdr, kErrTruncated);
             }
+            s_base = base;
         }
+    }
+    __syncthreads();
+    const u64 base = s_base;
+    if (base) {
+        const u64 t0 = g0 * kOffGroup, t1 = min(g1 * kOffGroup, a.ntiles);
+        for (u64 t = t0 + tid; t < t1; t += kThreads)
+            a.offs[t] += base;
     }
     __syncthreads();
     if (tid == 0) {
@@ -171,7 +208,7 @@ __global__ void __launch_bounds__(kThreads) offsets_kernel(OffsetsArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// Pass 2: persistent decode with double-buffered bulk staging.
+// Pass 2: persistent decode, producer warp + consumer warps.
 
 struct TiledArgs {
     const uint8_t *in;
@@ -186,17 +223,17 @@ struct TiledArgs {
     uint32_t out_aligned;
 };
 
-struct Stages {
-    uint8_t data[2][kStageData];
-    uint8_t ctrl[2][kStageCtrl];
-    uint64_t bar[2];
-    u64 tile[2];
-    uint32_t hd[2], hc[2];  // address phase (mod 16) of the data and control ranges
+struct Pipe {
+    uint8_t data[kStages][kStageData];
+    uint8_t ctrl[kStages][kStageCtrl];
+    uint64_t full[kStages];
+    uint64_t empty[kStages];
+    u64 tile[kStages];
+    uint32_t hd[kStages], hc[kStages];  // address phase (mod 16) of the data / control range
 };
 
-// Copy global [g, g + len) to smem base + (g mod 16) .. : interior by one
-// bulk copy (lane 0 issues it), head and tail bytes by the warp's lanes.
-// Returns the bulk byte count.
+// Interior of global [g, g + len): the 16-byte-aligned part, copied by the
+// bulk engine to smem base + off0 (base + (g mod 16) holds byte g).
 __device__ __forceinline__ uint32_t range_interior(const uint8_t *g, uint32_t len,
                                                    const uint8_t *&a0, uint32_t &off0)
 {
@@ -207,52 +244,19 @@ __device__ __forceinline__ uint32_t range_interior(const uint8_t *g, uint32_t le
     return c1 > c0 ? (uint32_t)(c1 - c0) : 0u;
 }
 
+// The ragged head and tail of [g, g + len) (< 16 bytes each), by plain loads.
 __device__ __forceinline__ void range_edges(const uint8_t *g, uint32_t len, uint8_t *base,
                                             int lane)
 {
     uintptr_t s = (uintptr_t)g, e = s + len;
     uintptr_t c0 = (s + 15) & ~(uintptr_t)15, c1 = e & ~(uintptr_t)15;
     uint32_t h = (uint32_t)(s & 15u);
-    uint32_t head = (uint32_t)((c0 < e ? c0 : e) - s);                 // bytes [0, head)
+    uint32_t head = (uint32_t)((c0 < e ? c0 : e) - s);                    // bytes [0, head)
     uint32_t tail0 = (uint32_t)((c1 > c0 ? c1 : (c0 < e ? c0 : e)) - s);  // bytes [tail0, len)
     for (uint32_t i = lane; i < head; i += 32)
         base[h + i] = __ldg(g + i);
     for (uint32_t i = tail0 + lane; i < len; i += 32)
         base[h + i] = __ldg(g + i);
-}
-
-// Warp 0: claim the next tile and start its copies into stage ns.
-__device__ __forceinline__ void claim_and_issue(const TiledArgs &a, Stages &S, int ns, int lane)
-{
-    u64 t = 0;
-    if (lane == 0)
-        t = atomicAdd(&a.hdr->tile_counter, 1ull);
-    t = __shfl_sync(0xffffffffu, t, 0);
-    if (lane == 0)
-        S.tile[ns] = t;
-    if (t >= a.ntiles)
-        return;
-    const u64 q0 = t * kTileQuads;
-    const uint32_t clen = (uint32_t)min((u64)kTileQuads, a.nquads - q0);
-    const uint8_t *gc = a.in + q0;
-    const u64 d0 = a.offs[t], d1 = a.offs[t + 1];
-    const uint8_t *gd = a.in + a.nquads + d0;
-    const uint32_t dlen = (uint32_t)(d1 - d0);
-    const uint8_t *ac, *ad;
-    uint32_t oc, od;
-    uint32_t bc = range_interior(gc, clen, ac, oc);
-    uint32_t bd = range_interior(gd, dlen, ad, od);
-    if (lane == 0) {
-        S.hc[ns] = (uint32_t)((uintptr_t)gc & 15u);
-        S.hd[ns] = (uint32_t)((uintptr_t)gd & 15u);
-        mbar_arrive_expect_tx(&S.bar[ns], bc + bd);
-        if (bc)
-            bulk_g2s(S.ctrl[ns] + oc, ac, bc, &S.bar[ns]);
-        if (bd)
-            bulk_g2s(S.data[ns] + od, ad, bd, &S.bar[ns]);
-    }
-    range_edges(gc, clen, S.ctrl[ns], lane);
-    range_edges(gd, dlen, S.data[ns], lane);
 }
 
 __device__ __forceinline__ uint32_t quad_count(uint32_t c, uint32_t nints)
@@ -266,62 +270,122 @@ __device__ __forceinline__ uint32_t value_at(const uint32_t *s32, uint32_t p, ui
     return v & (0xffffffffu >> (24u - 8u * code));
 }
 
+// Producer warp: fill stages with tiles until none is left, then post one
+// stage marked kNoTile.  Returns normally or after a bounded wait gave up.
 template <bool kDelta>
-__global__ void __launch_bounds__(kThreads, 3) decode_tiled_kernel(TiledArgs a)
+__device__ void produce(const TiledArgs &a, Pipe &P, int lane)
 {
-    __shared__ __align__(16) Stages S;
-    __shared__ __align__(16) uint16_t s_qoff[kTileQuads];
-    __shared__ uint32_t s_warp[kWarps];
-    __shared__ u64 s_etag;
-    __shared__ uint32_t s_flag, s_carry;
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) {
-        mbar_init(&S.bar[0], 1);
-        mbar_init(&S.bar[1], 1);
-        fence_mbar_init();
-        s_etag = (ld_relaxed(&a.hdr->epoch) + 1) << 2;
-        s_flag = error_raised(a.hdr) ? 1u : 0u;
+    uint32_t issued = 0;  // stage fills posted (iteration k fills stage k % kStages)
+    u64 next = 0;
+    if (kDelta) {
+        if (lane == 0)
+            next = atomicAdd(&a.hdr->tile_counter, 1ull);
+        next = __shfl_sync(0xffffffffu, next, 0);
+    } else {
+        next = blockIdx.x;
     }
-    __syncthreads();
-    if (s_flag) {  // the offsets pass failed (truncated stream)
-        finish_launch(a.hdr, a.result);
-        return;
+    u64 nd0 = 0, nd1 = 0;
+    if (next < a.ntiles) {
+        nd0 = a.offs[next];
+        nd1 = a.offs[next + 1];
     }
-    const u64 etag = s_etag;
-    const uint32_t last_nints = (uint32_t)(a.n - 4 * (a.nquads - 1));
-    if (warp == 0)
-        claim_and_issue(a, S, 0, lane);
-    __syncthreads();
-
-    // Stage s is used for iterations it = s, s + 2, ...; its k-th fill
-    // completes phase k of its barrier, so iteration it waits on parity
-    // (it >> 1) & 1.
-    int exit_reason = 0;  // 0 done, 1 a copy never completed, 2 carry look-back failed
-    uint32_t it = 0;
-    for (;; it++) {
-        const int s = it & 1;
-        const u64 tile = S.tile[s];
-        if (tile >= a.ntiles)
-            break;
-        if (warp == 0)
-            claim_and_issue(a, S, s ^ 1, lane);
-        bool ok = mbar_wait_bounded(&S.bar[s], (it >> 1) & 1u, kBarrierPolls);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0)
-                raise_error(a.hdr, kErrTimeout);
-            exit_reason = 1;
+    for (uint32_t k = 0;; k++) {
+        const int s = k % kStages;
+        if (k >= (uint32_t)kStages) {
+            bool ok = mbar_wait_bounded(&P.empty[s], ((k / kStages) - 1) & 1u, kBarrierPolls);
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0)
+                    raise_error(a.hdr, kErrTimeout);
+                break;
+            }
+        }
+        const u64 t = next;
+        const u64 d0 = nd0, d1 = nd1;
+        if (t >= a.ntiles) {
+            if (lane == 0) {
+                P.tile[s] = kNoTile;
+                mbar_arrive_expect_tx(&P.full[s], 0);
+            } else {
+                mbar_arrive(&P.full[s]);
+            }
+            issued = k + 1;
             break;
         }
+        // Claim the following tile now so its offsets load overlaps this one.
+        if (kDelta) {
+            if (lane == 0)
+                next = atomicAdd(&a.hdr->tile_counter, 1ull);
+            next = __shfl_sync(0xffffffffu, next, 0);
+        } else {
+            next = t + gridDim.x;
+        }
+        if (next < a.ntiles) {
+            nd0 = a.offs[next];
+            nd1 = a.offs[next + 1];
+        }
+        const u64 q0 = t * kTileQuads;
+        const uint32_t clen = (uint32_t)min((u64)kTileQuads, a.nquads - q0);
+        const uint8_t *gc = a.in + q0;
+        const uint8_t *gd = a.in + a.nquads + d0;
+        const uint32_t dlen = (uint32_t)(d1 - d0);
+        range_edges(gc, clen, P.ctrl[s], lane);
+        range_edges(gd, dlen, P.data[s], lane);
+        if (lane == 0) {
+            const uint8_t *ac, *ad;
+            uint32_t oc, od;
+            uint32_t bc = range_interior(gc, clen, ac, oc);
+            uint32_t bd = range_interior(gd, dlen, ad, od);
+            P.tile[s] = t;
+            P.hc[s] = (uint32_t)((uintptr_t)gc & 15u);
+            P.hd[s] = (uint32_t)((uintptr_t)gd & 15u);
+            mbar_arrive_expect_tx(&P.full[s], bc + bd);
+            if (bc)
+                bulk_g2s(P.ctrl[s] + oc, ac, bc, &P.full[s]);
+            if (bd)
+                bulk_g2s(P.data[s] + od, ad, bd, &P.full[s]);
+        } else {
+            mbar_arrive(&P.full[s]);
+        }
+        issued = k + 1;
+    }
+    // Let every copy this warp started land before the CTA can exit: stage s
+    // was filled (issued - 1 - s) / kStages + 1 times; wait for the last fill.
+    if (lane == 0) {
+        for (int s = 0; s < kStages; s++)
+            if (issued > (uint32_t)s) {
+                uint32_t fills = (issued - 1 - s) / kStages + 1;
+                mbar_wait_bounded(&P.full[s], (fills - 1) & 1u, kBarrierPolls);
+            }
+    }
+    __syncwarp();
+}
 
-        // ---- control bytes -> quad offsets inside the tile ------------------
+// Consumer warps (8, synchronised among themselves by named barrier 1).
+template <bool kDelta>
+__device__ void consume(const TiledArgs &a, Pipe &P, uint16_t *s_qoff, uint32_t *s_warp,
+                        u64 s_etag, uint32_t &s_flag, uint32_t &s_carry)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const u64 etag = s_etag;
+    const uint32_t last_nints = (uint32_t)(a.n - 4 * (a.nquads - 1));
+    for (uint32_t k = 0;; k++) {
+        const int s = k % kStages;
+        bool ok = mbar_wait_bounded(&P.full[s], (k / kStages) & 1u, kBarrierPolls);
+        if (!ok) {  // cannot happen unless a copy is lost; give up quietly
+            raise_error(a.hdr, kErrTimeout);
+            break;
+        }
+        const u64 tile = P.tile[s];
+        if (tile == kNoTile)
+            break;
+
+        // ---- control bytes -> quad offsets inside the tile ----------------
         const u64 q0 = tile * kTileQuads;
         const uint32_t nq = (uint32_t)min((u64)kTileQuads, a.nquads - q0);
-        const uint8_t *C = S.ctrl[s] + S.hc[s];
-        const uint8_t *D = S.data[s];
-        const uint32_t h = S.hd[s];
+        const uint8_t *C = P.ctrl[s] + P.hc[s];
+        const uint32_t h = P.hd[s];
         uint32_t w = 0;
-        if (S.hc[s] == 0 && 4u * tid + 4u <= nq) {
+        if (P.hc[s] == 0 && 4u * tid + 4u <= nq) {
             w = reinterpret_cast<const uint32_t *>(C)[tid];
         } else {
 #pragma unroll
@@ -345,19 +409,19 @@ __global__ void __launch_bounds__(kThreads, 3) decode_tiled_kernel(TiledArgs a)
         uint32_t incl = warp_incl_scan(tsum);
         if (lane == 31)
             s_warp[warp] = incl;
-        __syncthreads();
+        named_sync(1, kThreads);
         uint32_t wpre = 0;
 #pragma unroll
-        for (int k = 0; k < kWarps; k++)
-            wpre += k < warp ? s_warp[k] : 0u;
+        for (int j = 0; j < kWarps; j++)
+            wpre += j < warp ? s_warp[j] : 0u;
         {
             uint32_t o0 = wpre + incl - tsum, o1 = o0 + cnt[0], o2 = o1 + cnt[1], o3 = o2 + cnt[2];
             reinterpret_cast<uint2 *>(s_qoff)[tid] = make_uint2(o0 | (o1 << 16), o2 | (o3 << 16));
         }
-        __syncthreads();
+        named_sync(1, kThreads);
 
         // ---- gather: one quad per lane per round ----------------------------
-        const uint32_t *s32 = reinterpret_cast<const uint32_t *>(D);
+        const uint32_t *s32 = reinterpret_cast<const uint32_t *>(P.data[s]);
         uint32_t v[kTileRounds][4];
 #pragma unroll
         for (int r = 0; r < kTileRounds; r++) {
@@ -377,28 +441,32 @@ __global__ void __launch_bounds__(kThreads, 3) decode_tiled_kernel(TiledArgs a)
             } else {
                 uint32_t pp = p;
 #pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    uint32_t code = (c >> (2 * k)) & 3u;
-                    v[r][k] = value_at(s32, pp, code);
+                for (int j = 0; j < 4; j++) {
+                    uint32_t code = (c >> (2 * j)) & 3u;
+                    v[r][j] = value_at(s32, pp, code);
                     pp += code + 1;
                 }
             }
 #pragma unroll
-            for (int k = 0; k < 4; k++)
-                if ((uint32_t)k >= nints)
-                    v[r][k] = 0;
+            for (int j = 0; j < 4; j++)
+                if ((uint32_t)j >= nints)
+                    v[r][j] = 0;
             if (!kDelta && valid) {
                 uint32_t *dst = a.out + 4 * (q0 + lq);
                 if (nints == 4 && a.out_aligned) {
                     stg_stream128(dst, make_uint4(v[r][0], v[r][1], v[r][2], v[r][3]));
                 } else {
 #pragma unroll
-                    for (int k = 0; k < 4; k++)
-                        if ((uint32_t)k < nints)
-                            dst[k] = v[r][k];
+                    for (int j = 0; j < 4; j++)
+                        if ((uint32_t)j < nints)
+                            dst[j] = v[r][j];
                 }
             }
         }
+        // This warp no longer reads stage s.
+        __syncwarp();
+        if (lane == 0)
+            mbar_arrive(&P.empty[s]);
 
         if (kDelta) {
             // ---- running sums: quad, warp, block, then across tiles ----------
@@ -413,15 +481,15 @@ __global__ void __launch_bounds__(kThreads, 3) decode_tiled_kernel(TiledArgs a)
                 qexcl[r] = wrun + inc - qs;
                 wrun += __shfl_sync(0xffffffffu, inc, 31);
             }
-            __syncthreads();  // everyone has read s_warp (offsets) above
+            named_sync(1, kThreads);  // every warp has read s_warp (offsets) above
             if (lane == 0)
                 s_warp[warp] = wrun;
-            __syncthreads();
+            named_sync(1, kThreads);
             uint32_t bpre = 0, vagg = 0;
 #pragma unroll
-            for (int k = 0; k < kWarps; k++) {
-                uint32_t t = s_warp[k];
-                bpre += k < warp ? t : 0u;
+            for (int j = 0; j < kWarps; j++) {
+                uint32_t t = s_warp[j];
+                bpre += j < warp ? t : 0u;
                 vagg += t;
             }
             if (warp == 0) {
@@ -447,16 +515,13 @@ __global__ void __launch_bounds__(kThreads, 3) decode_tiled_kernel(TiledArgs a)
                     s_flag = lok ? 0u : 1u;
                 }
             }
-            __syncthreads();
-            if (s_flag) {
-                exit_reason = 2;
-                break;
-            }
+            named_sync(1, kThreads);
             const uint32_t base = s_carry + bpre;
+            const bool failed = s_flag != 0;
 #pragma unroll
             for (int r = 0; r < kTileRounds; r++) {
                 const uint32_t lq = warp * (32 * kTileRounds) + r * 32 + lane;
-                if (lq >= nq)
+                if (failed || lq >= nq)
                     continue;
                 const uint32_t nints = q0 + lq == a.nquads - 1 ? last_nints : 4u;
                 const uint32_t add = base + qexcl[r];
@@ -474,39 +539,82 @@ __global__ void __launch_bounds__(kThreads, 3) decode_tiled_kernel(TiledArgs a)
                         dst[3] = x.w;
                 }
             }
+            // Keep going after a failed look-back: later tiles will bail out
+            // on the raised error, and the producer must still drain.
         }
-        __syncthreads();  // stage s, s_qoff and s_warp are free again
+    }
+}
+
+template <bool kDelta>
+__global__ void __launch_bounds__(kDecBlock, 3) decode_tiled_kernel(TiledArgs a)
+{
+    extern __shared__ __align__(128) uint8_t dyn_smem[];
+    Pipe &P = *reinterpret_cast<Pipe *>(dyn_smem);
+    __shared__ __align__(16) uint16_t s_qoff[kTileQuads];
+    __shared__ uint32_t s_warp[kWarps];
+    __shared__ u64 s_etag;
+    __shared__ uint32_t s_flag, s_carry;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        for (int s = 0; s < kStages; s++) {
+            mbar_init(&P.full[s], 32);        // the 32 producer lanes arrive
+            mbar_init(&P.empty[s], kWarps);   // one arrival per consumer warp
+        }
+        fence_mbar_init();
+        s_etag = (ld_relaxed(&a.hdr->epoch) + 1) << 2;
+        s_flag = error_raised(a.hdr) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (s_flag) {  // the offsets pass failed (truncated stream)
+        finish_launch(a.hdr, a.result);
+        return;
     }
 
-    // After an early exit, let the copies still in flight land before the
-    // CTA's shared memory goes away (bounded like every other wait).
-    if (exit_reason != 0 && tid == 0) {
-        const int s = it & 1;
-        if (exit_reason == 1)
-            mbar_wait_bounded(&S.bar[s], (it >> 1) & 1u, kBarrierPolls);
-        if (S.tile[s ^ 1] < a.ntiles)
-            mbar_wait_bounded(&S.bar[s ^ 1], ((it + 1) >> 1) & 1u, kBarrierPolls);
-    }
+    if (warp == kWarps)
+        produce<kDelta>(a, P, lane);
+    else
+        consume<kDelta>(a, P, s_qoff, s_warp, s_etag, s_flag, s_carry);
     finish_launch(a.hdr, a.result);
 }
 
 // ---------------------------------------------------------------------------
 
-static int tiled_grid(bool delta)
+static int sm_count()
 {
-    static int cached[2] = {0, 0};
-    int &g = cached[delta ? 1 : 0];
-    if (!g) {
-        int dev = 0, sms = 0, occ = 0;
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (delta)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, decode_tiled_kernel<true>,
-                                                          kThreads, 0);
-        else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, decode_tiled_kernel<false>,
-                                                          kThreads, 0);
-        g = (sms > 0 ? sms : 148) * (occ > 0 ? occ : 1);
+        if (sms <= 0)
+            sms = 148;
+    }
+    return sms;
+}
+
+template <bool kDelta>
+static int tiled_grid()
+{
+    static int g = 0;
+    if (!g) {
+        cudaFuncSetAttribute(decode_tiled_kernel<kDelta>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Pipe));
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, decode_tiled_kernel<kDelta>,
+                                                      kDecBlock, sizeof(Pipe));
+        g = sm_count() * (occ > 0 ? occ : 1);
+    }
+    return g;
+}
+
+static int offsets_grid()
+{
+    static int g = 0;
+    if (!g) {
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, offsets_kernel, kThreads, 0);
+        g = sm_count() * (occ > 0 ? occ : 1);
     }
     return g;
 }
@@ -528,13 +636,16 @@ int launch_decode_tiled(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, uin
     o.n = n;
     o.nquads = nquads;
     o.ntiles = ntiles;
-    o.nctas = (ntiles + kOffTiles - 1) / kOffTiles;
+    o.groups = (ntiles + kOffGroup - 1) / kOffGroup;
+    u64 ogrid = min((u64)offsets_grid(), o.groups);
+    o.per_cta = (o.groups + ogrid - 1) / ogrid;
+    ogrid = (o.groups + o.per_cta - 1) / o.per_cta;  // no CTA without groups
     o.offs = offs;
     o.hdr = hdr;
     o.st = st;
     o.spin_limit = spin_limit;
     o.in_aligned = (((uintptr_t)in) & 15u) == 0;
-    offsets_kernel<<<(unsigned)o.nctas, kThreads, 0, stream>>>(o);
+    offsets_kernel<<<(unsigned)ogrid, kThreads, 0, stream>>>(o);
 
     TiledArgs t;
     t.in = in;
@@ -549,11 +660,13 @@ int launch_decode_tiled(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, uin
     t.spin_limit = spin_limit;
     t.prev = prev;
     t.out_aligned = (((uintptr_t)out) & 15u) == 0;
-    u64 grid = min((u64)tiled_grid(delta), ntiles);
-    if (delta)
-        decode_tiled_kernel<true><<<(unsigned)grid, kThreads, 0, stream>>>(t);
-    else
-        decode_tiled_kernel<false><<<(unsigned)grid, kThreads, 0, stream>>>(t);
+    if (delta) {
+        u64 grid = min((u64)tiled_grid<true>(), ntiles);
+        decode_tiled_kernel<true><<<(unsigned)grid, kDecBlock, sizeof(Pipe), stream>>>(t);
+    } else {
+        u64 grid = min((u64)tiled_grid<false>(), ntiles);
+        decode_tiled_kernel<false><<<(unsigned)grid, kDecBlock, sizeof(Pipe), stream>>>(t);
+    }
     return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
 

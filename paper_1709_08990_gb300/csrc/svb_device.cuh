@@ -169,7 +169,7 @@ __device__ __forceinline__ void publish(u64 *tag, u64 *slot, u64 value, u64 flag
     st_release(tag, etag | flag);
 }
 
-constexpr int kLookbackPerLane = 4;  // predecessors each lane inspects per round trip
+constexpr int kLookbackPerLane = 8;  // predecessors each lane inspects per round trip
 
 // Exclusive prefix of tile `tile` (> 0) for one scan (kVal: the delta running
 // sum, else the byte offsets), computed by one whole warp.  One round trip
@@ -178,7 +178,7 @@ constexpr int kLookbackPerLane = 4;  // predecessors each lane inspects per roun
 // tiles back); the window's values are summed up to the nearest published
 // inclusive prefix, or wholly and the next window is taken.  A window this
 // wide keeps the look-back shallow even when tiles are claimed faster than
-// one L2 round trip per 128 tiles.  Every poll is bounded: after spin_limit
+// one L2 round trip per 256 tiles.  Every poll is bounded: after spin_limit
 // polls (backing off to ~1 us each), or as soon as another tile has raised an
 // error, it returns with ok = false and the caller records the failure.
 template <bool kVal>
@@ -290,6 +290,11 @@ __device__ __forceinline__ void fence_mbar_init()
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
@@ -320,6 +325,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
             __nanosleep(64);
     }
     return false;
+}
+
+// Barrier among the first `count` threads of the CTA (named barrier `id`).
+__device__ __forceinline__ void named_sync(int id, int count)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
 // Global -> shared bulk copy completing on an mbarrier.  dst and src 16-byte
