@@ -21,9 +21,11 @@
 //                    on its "empty" mbarrier.  Plain streams never wait on
 //                    another CTA; loads for later tiles are always in flight.
 // Differential streams add one look-back over the tiles' gap sums (the carry
-// of Sec. 2's prefix sum across tiles) before a tile's values are stored; their
-// tiles are claimed from an atomic counter so that every predecessor of a
-// tile is already owned by a running CTA.
+// of Sec. 2's prefix sum across tiles) before a tile's values are stored.
+// Tiles go round-robin over the CTAs (CTA c takes c, c + G, c + 2G, ...), so
+// the tiles a look-back waits on are the ones the other CTAs decode in the
+// same round.  Differential launches are cooperative: every CTA is resident
+// at once, so each predecessor is always owned by a running CTA.
 //
 // Bytes outside the stream are never read: each tile's range is copied as its
 // 16-byte-aligned interior by the bulk engine plus a ragged head and tail of
@@ -264,10 +266,32 @@ __device__ __forceinline__ uint32_t quad_count(uint32_t c, uint32_t nints)
     return nints + __popc(c & 0x55u) + 2u * __popc(c & 0xAAu);
 }
 
-__device__ __forceinline__ uint32_t value_at(const uint32_t *s32, uint32_t p, uint32_t code)
+// The code + 1 bytes at staged position p, least significant first.  The
+// funnel shift uses only the low five bits of its count, so p << 3 selects
+// the byte within the first word.
+__device__ __forceinline__ uint32_t take(const uint8_t *d, uint32_t p, uint32_t code)
 {
-    uint32_t v = __funnelshift_r(s32[p >> 2], s32[(p >> 2) + 1], (p & 3u) * 8u);
-    return v & (0xffffffffu >> (24u - 8u * code));
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(d + (p & ~3u));
+    return __funnelshift_r(w[0], w[1], p << 3) & (0xffffffffu >> (24u - 8u * code));
+}
+
+// One quad: its four integers start at staged position p, lengths from the
+// codes of control byte c (Sec. 4: integer j takes code_j + 1 bytes).
+__device__ __forceinline__ uint4 decode_quad(const uint8_t *d, uint32_t p, uint32_t c)
+{
+    const uint32_t c0 = c & 3u, c1 = (c >> 2) & 3u, c2 = (c >> 4) & 3u, c3 = c >> 6;
+    const uint32_t p1 = p + c0 + 1, p2 = p1 + c1 + 1, p3 = p2 + c2 + 1;
+    return make_uint4(take(d, p, c0), take(d, p1, c1), take(d, p2, c2), take(d, p3, c3));
+}
+
+// A quad with control byte 0: four one-byte integers (the zero-control fast
+// path the paper also takes, Sec. 4).
+__device__ __forceinline__ uint4 widen_quad(const uint8_t *d, uint32_t p)
+{
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(d + (p & ~3u));
+    const uint32_t x = __funnelshift_r(w[0], w[1], p << 3);
+    return make_uint4(__byte_perm(x, 0, 0x4440), __byte_perm(x, 0, 0x4441),
+                      __byte_perm(x, 0, 0x4442), __byte_perm(x, 0, 0x4443));
 }
 
 // Producer warp: fill stages with tiles until none is left, then post one
@@ -276,14 +300,7 @@ template <bool kDelta>
 __device__ void produce(const TiledArgs &a, Pipe &P, int lane)
 {
     uint32_t issued = 0;  // stage fills posted (iteration k fills stage k % kStages)
-    u64 next = 0;
-    if (kDelta) {
-        if (lane == 0)
-            next = atomicAdd(&a.hdr->tile_counter, 1ull);
-        next = __shfl_sync(0xffffffffu, next, 0);
-    } else {
-        next = blockIdx.x;
-    }
+    u64 next = blockIdx.x;
     u64 nd0 = 0, nd1 = 0;
     if (next < a.ntiles) {
         nd0 = a.offs[next];
@@ -311,14 +328,9 @@ __device__ void produce(const TiledArgs &a, Pipe &P, int lane)
             issued = k + 1;
             break;
         }
-        // Claim the following tile now so its offsets load overlaps this one.
-        if (kDelta) {
-            if (lane == 0)
-                next = atomicAdd(&a.hdr->tile_counter, 1ull);
-            next = __shfl_sync(0xffffffffu, next, 0);
-        } else {
-            next = t + gridDim.x;
-        }
+        // Tiles go round-robin over the CTAs; read the next tile's offsets now
+        // so that the load overlaps this one.
+        next = t + gridDim.x;
         if (next < a.ntiles) {
             nd0 = a.offs[next];
             nd1 = a.offs[next + 1];
@@ -382,7 +394,10 @@ __device__ void consume(const TiledArgs &a, Pipe &P, uint16_t *s_qoff, uint32_t 
         // ---- control bytes -> quad offsets inside the tile ----------------
         const u64 q0 = tile * kTileQuads;
         const uint32_t nq = (uint32_t)min((u64)kTileQuads, a.nquads - q0);
+        // Every tile but possibly the last holds kTileQuads quads of four.
+        const bool full = nq == kTileQuads && (tile + 1 < a.ntiles || last_nints == 4);
         const uint8_t *C = P.ctrl[s] + P.hc[s];
+        const uint8_t *D = P.data[s];
         const uint32_t h = P.hd[s];
         uint32_t w = 0;
         if (P.hc[s] == 0 && 4u * tid + 4u <= nq) {
@@ -393,18 +408,34 @@ __device__ void consume(const TiledArgs &a, Pipe &P, uint16_t *s_qoff, uint32_t 
                 if (4u * tid + j < nq)
                     w |= (uint32_t)C[4 * tid + j] << (8 * j);
         }
-        uint32_t cnt[4], tsum = 0;
+        uint32_t o1, o2, o3, tsum;
+        if (full) {
+            // Byte j of cs = sum of the four codes of quad j; the multiply turns
+            // the four bytes into their running sums (at most 48, no carries).
+            uint32_t cs = (w & 0x33333333u) + ((w >> 2) & 0x33333333u);
+            cs = (cs & 0x0F0F0F0Fu) + ((cs >> 4) & 0x0F0F0F0Fu);
+            const uint32_t run = cs * 0x01010101u;
+            o1 = 4u + (run & 0xffu);
+            o2 = 8u + ((run >> 8) & 0xffu);
+            o3 = 12u + ((run >> 16) & 0xffu);
+            tsum = 16u + (run >> 24);
+        } else {
+            uint32_t cnt[4];
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-            uint32_t lq = 4u * tid + j;
-            uint32_t c = (w >> (8 * j)) & 0xffu;
-            uint32_t nints = 4;
-            if (q0 + lq == a.nquads - 1 && last_nints < 4) {
-                nints = last_nints;
-                c &= (1u << (2 * nints)) - 1u;
+            for (int j = 0; j < 4; j++) {
+                uint32_t lq = 4u * tid + j;
+                uint32_t c = (w >> (8 * j)) & 0xffu;
+                uint32_t nints = 4;
+                if (q0 + lq == a.nquads - 1 && last_nints < 4) {
+                    nints = last_nints;
+                    c &= (1u << (2 * nints)) - 1u;
+                }
+                cnt[j] = lq < nq ? quad_count(c, nints) : 0u;
             }
-            cnt[j] = lq < nq ? quad_count(c, nints) : 0u;
-            tsum += cnt[j];
+            o1 = cnt[0];
+            o2 = o1 + cnt[1];
+            o3 = o2 + cnt[2];
+            tsum = o3 + cnt[3];
         }
         uint32_t incl = warp_incl_scan(tsum);
         if (lane == 31)
@@ -415,51 +446,66 @@ __device__ void consume(const TiledArgs &a, Pipe &P, uint16_t *s_qoff, uint32_t 
         for (int j = 0; j < kWarps; j++)
             wpre += j < warp ? s_warp[j] : 0u;
         {
-            uint32_t o0 = wpre + incl - tsum, o1 = o0 + cnt[0], o2 = o1 + cnt[1], o3 = o2 + cnt[2];
-            reinterpret_cast<uint2 *>(s_qoff)[tid] = make_uint2(o0 | (o1 << 16), o2 | (o3 << 16));
+            const uint32_t o0 = h + wpre + incl - tsum;  // staged position of the thread's data
+            reinterpret_cast<uint2 *>(s_qoff)[tid] =
+                make_uint2(o0 | ((o0 + o1) << 16), (o0 + o2) | ((o0 + o3) << 16));
         }
         named_sync(1, kThreads);
 
         // ---- gather: one quad per lane per round ----------------------------
-        const uint32_t *s32 = reinterpret_cast<const uint32_t *>(P.data[s]);
+        const uint32_t lq0 = warp * (32 * kTileRounds) + lane;
+        const uint8_t *Cl = C + lq0;
+        const uint16_t *Ql = s_qoff + lq0;
+        uint32_t *op = a.out + 4 * (q0 + lq0);
         uint32_t v[kTileRounds][4];
+        if (full) {
 #pragma unroll
-        for (int r = 0; r < kTileRounds; r++) {
-            const uint32_t lq = warp * (32 * kTileRounds) + r * 32 + lane;
-            const bool valid = lq < nq;
-            uint32_t c = valid ? C[lq] : 0u;
-            const uint32_t nints = !valid ? 0u : (q0 + lq == a.nquads - 1 ? last_nints : 4u);
-            if (nints < 4)
-                c &= (1u << (2 * nints)) - 1u;
-            const uint32_t p = h + (valid ? s_qoff[lq] : 0u);
-            if (__all_sync(0xffffffffu, c == 0)) {
-                uint32_t d = __funnelshift_r(s32[p >> 2], s32[(p >> 2) + 1], (p & 3u) * 8u);
-                v[r][0] = __byte_perm(d, 0, 0x4440);
-                v[r][1] = __byte_perm(d, 0, 0x4441);
-                v[r][2] = __byte_perm(d, 0, 0x4442);
-                v[r][3] = __byte_perm(d, 0, 0x4443);
-            } else {
-                uint32_t pp = p;
-#pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    uint32_t code = (c >> (2 * j)) & 3u;
-                    v[r][j] = value_at(s32, pp, code);
-                    pp += code + 1;
+            for (int r = 0; r < kTileRounds; r++) {
+                const uint32_t c = Cl[32 * r];
+                const uint32_t p = Ql[32 * r];
+                uint4 x;
+                if (__all_sync(0xffffffffu, c == 0))
+                    x = widen_quad(D, p);
+                else
+                    x = decode_quad(D, p, c);
+                v[r][0] = x.x;
+                v[r][1] = x.y;
+                v[r][2] = x.z;
+                v[r][3] = x.w;
+                if (!kDelta) {
+                    if (a.out_aligned) {
+                        stg_stream128(op + 128 * r, x);
+                    } else {
+                        op[128 * r + 0] = x.x;
+                        op[128 * r + 1] = x.y;
+                        op[128 * r + 2] = x.z;
+                        op[128 * r + 3] = x.w;
+                    }
                 }
             }
+        } else {
 #pragma unroll
-            for (int j = 0; j < 4; j++)
-                if ((uint32_t)j >= nints)
-                    v[r][j] = 0;
-            if (!kDelta && valid) {
-                uint32_t *dst = a.out + 4 * (q0 + lq);
-                if (nints == 4 && a.out_aligned) {
-                    stg_stream128(dst, make_uint4(v[r][0], v[r][1], v[r][2], v[r][3]));
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 4; j++)
-                        if ((uint32_t)j < nints)
-                            dst[j] = v[r][j];
+            for (int r = 0; r < kTileRounds; r++) {
+                const uint32_t lq = lq0 + r * 32;
+                const bool valid = lq < nq;
+                uint32_t c = valid ? C[lq] : 0u;
+                const uint32_t nints = !valid ? 0u : (q0 + lq == a.nquads - 1 ? last_nints : 4u);
+                if (nints < 4)
+                    c &= (1u << (2 * nints)) - 1u;
+                const uint32_t p = valid ? s_qoff[lq] : h;
+                uint4 x = decode_quad(D, p, c);
+                v[r][0] = x.x;
+                v[r][1] = nints > 1 ? x.y : 0u;
+                v[r][2] = nints > 2 ? x.z : 0u;
+                v[r][3] = nints > 3 ? x.w : 0u;
+                if (!kDelta && valid) {
+                    op[128 * r] = x.x;
+                    if (nints > 1)
+                        op[128 * r + 1] = x.y;
+                    if (nints > 2)
+                        op[128 * r + 2] = x.z;
+                    if (nints > 3)
+                        op[128 * r + 3] = x.w;
                 }
             }
         }
@@ -520,12 +566,12 @@ __device__ void consume(const TiledArgs &a, Pipe &P, uint16_t *s_qoff, uint32_t 
             const bool failed = s_flag != 0;
 #pragma unroll
             for (int r = 0; r < kTileRounds; r++) {
-                const uint32_t lq = warp * (32 * kTileRounds) + r * 32 + lane;
+                const uint32_t lq = lq0 + r * 32;
                 if (failed || lq >= nq)
                     continue;
-                const uint32_t nints = q0 + lq == a.nquads - 1 ? last_nints : 4u;
+                const uint32_t nints = full ? 4u : (q0 + lq == a.nquads - 1 ? last_nints : 4u);
                 const uint32_t add = base + qexcl[r];
-                uint32_t *dst = a.out + 4 * (q0 + lq);
+                uint32_t *dst = op + 128 * r;
                 uint4 x = make_uint4(v[r][0] + add, v[r][1] + add, v[r][2] + add, v[r][3] + add);
                 if (nints == 4 && a.out_aligned) {
                     stg_stream128(dst, x);
@@ -662,7 +708,12 @@ int launch_decode_tiled(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, uin
     t.out_aligned = (((uintptr_t)out) & 15u) == 0;
     if (delta) {
         u64 grid = min((u64)tiled_grid<true>(), ntiles);
-        decode_tiled_kernel<true><<<(unsigned)grid, kDecBlock, sizeof(Pipe), stream>>>(t);
+        void *args[] = {&t};
+        cudaError_t e = cudaLaunchCooperativeKernel((const void *)decode_tiled_kernel<true>,
+                                                    dim3((unsigned)grid), dim3(kDecBlock), args,
+                                                    sizeof(Pipe), stream);
+        if (e != cudaSuccess)
+            return 3;
     } else {
         u64 grid = min((u64)tiled_grid<false>(), ntiles);
         decode_tiled_kernel<false><<<(unsigned)grid, kDecBlock, sizeof(Pipe), stream>>>(t);
