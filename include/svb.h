@@ -162,6 +162,34 @@ int svb_decode_async(const uint8_t *in, size_t in_len, size_t n, uint32_t *out,
                      uint32_t prev, int delta, svb_result *d_result, void *ws,
                      size_t ws_bytes, svb_stream_t stream);
 
+/* ---- decoding without allocation --------------------------------------- */
+
+/* Largest n that svb_decode_noalloc accepts. */
+#define SVB_NOALLOC_MAX_N ((size_t)1 << 24)
+
+/* Decode like svb_decode_checked, but without allocating anything: no
+ * cudaMalloc, cudaFree, pinned host buffer or allocating library call.  The
+ * paper has no counterpart; this is for callers that cannot allocate device
+ * memory while they decode, such as a custom allocator or memory pool that
+ * decodes from inside its own bookkeeping (a nested cudaMalloc would re-enter
+ * it), a process whose HBM is already reserved by a framework's caching
+ * allocator, or a latency-bound path that cannot afford cudaMalloc/cudaFree,
+ * which may synchronize the device.
+ *
+ * Scratch: a fixed device array of about 1.1 MB inside the library, enough
+ * for n <= SVB_NOALLOC_MAX_N; every GPU that loads the library holds it until
+ * the process exits.  n > SVB_NOALLOC_MAX_N returns SVB_ERROR with
+ * SVB_EINVAL.  The first call on a device looks up the array's device
+ * address (make that first call before any stream capture).  All calls share
+ * the array: calls that overlap on the GPU race, so order them on one stream
+ * or serialize them on the host.
+ *
+ * in[0..in_len) is the stream, out[0..n) receives the integers, delta and prev
+ * as in svb_decode_checked.  Runs on `stream` and waits for it.  Returns the
+ * bytes consumed, or SVB_ERROR with svb_last_error() set. */
+size_t svb_decode_noalloc(const uint8_t *in, size_t in_len, size_t n, uint32_t *out,
+                          uint32_t prev, int delta, svb_stream_t stream);
+
 /* ---- test hook ---------------------------------------------------------- */
 
 /* Failure-detection check: launches one decode tile whose predecessor is

@@ -140,6 +140,11 @@ size_t decode_sync(const uint8_t *in, u64 in_len, size_t n, uint32_t *out, uint3
 
 }  // namespace
 
+void svb::set_last_error(int code)
+{
+    t_last_error = code;
+}
+
 extern "C" {
 
 size_t svb_max_compressed_size(size_t n)

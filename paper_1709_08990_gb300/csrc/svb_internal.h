@@ -26,4 +26,7 @@ int launch_encode(const uint32_t *in, u64 n, uint8_t *out, uint32_t prev, bool d
                   DeviceResult *result, cudaStream_t stream, u64 spin_limit);
 u64 encode_tiles(u64 n);
 
+// Record the calling thread's status for svb_last_error().
+void set_last_error(int code);
+
 }  // namespace svb

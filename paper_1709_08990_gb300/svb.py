@@ -61,6 +61,7 @@ def lib() -> ctypes.CDLL:
             "svb_encode_async": ([vp, sz, vp, u32, i32, vp, vp, sz, vp], i32),
             "svb_decode_async": ([vp, sz, sz, vp, u32, i32, vp, vp, sz, vp], i32),
             "svb_testhook_lookback_timeout": ([vp, sz, vp, u64, vp, vp, sz, vp], i32),
+            "svb_decode_noalloc": ([vp, sz, sz, vp, u32, i32, vp], sz),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -180,6 +181,14 @@ def svb_encode_async(inp, n, out, prev, delta, d_result, ws, ws_bytes, stream=No
 def svb_decode_async(inp, in_len, n, out, prev, delta, d_result, ws, ws_bytes, stream=None) -> int:
     return lib().svb_decode_async(_p(inp), in_len, n, _p(out), prev & 0xFFFFFFFF, int(delta),
                                   _p(d_result), _p(ws), ws_bytes, _stream(stream))
+
+
+SVB_NOALLOC_MAX_N = 1 << 24
+
+
+def svb_decode_noalloc(inp, in_len: int, n: int, out, prev: int, delta: int, stream=None) -> int:
+    return _sized(lib().svb_decode_noalloc(_p(inp), in_len, n, _p(out), prev & 0xFFFFFFFF,
+                                           int(delta), _stream(stream)), "svb_decode_noalloc")
 
 
 def svb_testhook_lookback_timeout(stream_in, n, out, spin_limit, d_result, ws, ws_bytes,
