@@ -44,6 +44,7 @@ constexpr int kStageData = kTileData + 64;          // + 16-byte phase + 2-word 
 constexpr int kStageCtrl = kTileQuads + 32;
 constexpr int kStages = 4;
 constexpr int kDecBlock = kThreads + 32;            // 8 consumer warps + 1 producer warp
+constexpr int kDecBlockDelta = kThreads + 64;       // + 1 warp for the carry look-back
 constexpr u64 kBarrierPolls = 1ull << 24;           // bound on one mbarrier wait
 constexpr u64 kNoTile = ~0ull;
 
@@ -234,6 +235,16 @@ struct Pipe {
     uint32_t hd[kStages], hc[kStages];  // address phase (mod 16) of the data / control range
 };
 
+// Hand-off between the consumers and the carry warp of a differential decode:
+// per tile parity, the tile's gap sum (consumers -> carry warp) and its
+// carry-in (carry warp -> consumers), each announced on an mbarrier.
+struct CarrySync {
+    uint64_t agg_full[2];
+    uint64_t carry_full[2];
+    uint32_t agg[2];
+    uint32_t carry[2];
+};
+
 // Interior of global [g, g + len): the 16-byte-aligned part, copied by the
 // bulk engine to smem base + off0 (base + (g mod 16) holds byte g).
 __device__ __forceinline__ uint32_t range_interior(const uint8_t *g, uint32_t len,
@@ -372,15 +383,82 @@ __device__ void produce(const TiledArgs &a, Pipe &P, int lane)
     __syncwarp();
 }
 
+// Store tile k of this CTA (running sums in x, carry-in from the carry warp).
+__device__ __forceinline__ void store_delta_tile(const TiledArgs &a, CarrySync &cs, uint32_t k,
+                                                 const uint32_t (&x)[kTileRounds][4],
+                                                 uint32_t *op, uint32_t nq, u64 q0, bool full,
+                                                 uint32_t last_nints, int lane)
+{
+    const int warp = threadIdx.x >> 5;
+    mbar_wait_bounded(&cs.carry_full[k & 1], (k >> 1) & 1u, kBarrierPolls);
+    const uint32_t carry = cs.carry[k & 1];
+    const uint32_t lq0 = warp * (32 * kTileRounds) + lane;
+#pragma unroll
+    for (int r = 0; r < kTileRounds; r++) {
+        const uint32_t lq = lq0 + r * 32;
+        if (lq >= nq)
+            continue;
+        const uint32_t nints = full ? 4u : (q0 + lq == a.nquads - 1 ? last_nints : 4u);
+        uint32_t *dst = op + 128 * r;
+        uint4 y = make_uint4(x[r][0] + carry, x[r][1] + carry, x[r][2] + carry, x[r][3] + carry);
+        if (nints == 4 && a.out_aligned) {
+            stg_stream128(dst, y);
+        } else {
+            dst[0] = y.x;
+            if (nints > 1)
+                dst[1] = y.y;
+            if (nints > 2)
+                dst[2] = y.z;
+            if (nints > 3)
+                dst[3] = y.w;
+        }
+    }
+}
+
+// Carry warp of a differential decode: for each of this CTA's tiles, in
+// order, wait for the consumers' gap sum, find the tile's carry-in by
+// look-back, publish the tile's inclusive prefix and hand the carry back.
+__device__ void carry_warp(const TiledArgs &a, CarrySync &cs, u64 etag, int lane)
+{
+    uint32_t k = 0;
+    for (u64 tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, k++) {
+        bool ok = mbar_wait_bounded(&cs.agg_full[k & 1], (k >> 1) & 1u, kBarrierPolls);
+        const uint32_t vagg = cs.agg[k & 1];
+        TileStatus *me = &a.st[tile];
+        u64 carry = a.prev;
+        if (ok && tile != 0)
+            carry = lookback<true>(a.st, tile, etag, a.spin_limit, a.hdr, ok);
+        if (lane == 0) {
+            if (ok)
+                publish(&me->val_tag, &me->val_pre, (uint32_t)(carry + vagg), kFlagPrefix, etag);
+            else
+                raise_error(a.hdr, kErrTimeout);
+            cs.carry[k & 1] = (uint32_t)carry;
+            mbar_arrive(&cs.carry_full[k & 1]);
+        }
+        __syncwarp();
+        if (!ok)
+            break;
+    }
+}
+
 // Consumer warps (8, synchronised among themselves by named barrier 1).
 template <bool kDelta>
 __device__ void consume(const TiledArgs &a, Pipe &P, uint16_t *s_qoff, uint32_t *s_warp,
-                        u64 s_etag, uint32_t &s_flag, uint32_t &s_carry)
+                        u64 s_etag, CarrySync &cs)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const u64 etag = s_etag;
     const uint32_t last_nints = (uint32_t)(a.n - 4 * (a.nquads - 1));
-    for (uint32_t k = 0;; k++) {
+    // Differential: tile k's running sums wait in x_prev until its carry-in
+    // arrives; they are stored while tile k + 1 is being decoded.
+    uint32_t x_prev[kTileRounds][4];
+    uint32_t *op_prev = nullptr;
+    uint32_t nq_prev = 0;
+    u64 q0_prev = 0;
+    bool full_prev = true, has_prev = false;
+    uint32_t k = 0;
+    for (;; k++) {
         const int s = k % kStages;
         bool ok = mbar_wait_bounded(&P.full[s], (k / kStages) & 1u, kBarrierPolls);
         if (!ok) {  // cannot happen unless a copy is lost; give up quietly
@@ -515,7 +593,7 @@ __device__ void consume(const TiledArgs &a, Pipe &P, uint16_t *s_qoff, uint32_t 
             mbar_arrive(&P.empty[s]);
 
         if (kDelta) {
-            // ---- running sums: quad, warp, block, then across tiles ----------
+            // ---- running sums: quad, warp, block; the carry comes later ------
             uint32_t qexcl[kTileRounds], wrun = 0;
 #pragma unroll
             for (int r = 0; r < kTileRounds; r++) {
@@ -538,74 +616,55 @@ __device__ void consume(const TiledArgs &a, Pipe &P, uint16_t *s_qoff, uint32_t 
                 bpre += j < warp ? t : 0u;
                 vagg += t;
             }
-            if (warp == 0) {
-                TileStatus *me = &a.st[tile];
-                u64 carry = a.prev;
-                bool lok = true;
-                if (tile == 0) {
-                    if (lane == 0)
-                        publish(&me->val_tag, &me->val_pre, (uint32_t)(a.prev + vagg),
-                                kFlagPrefix, etag);
-                } else {
-                    if (lane == 0)
-                        publish(&me->val_tag, &me->val_agg, vagg, kFlagAgg, etag);
-                    carry = lookback<true>(a.st, tile, etag, a.spin_limit, a.hdr, lok);
-                    if (lok && lane == 0)
-                        publish(&me->val_tag, &me->val_pre, (uint32_t)(carry + vagg),
-                                kFlagPrefix, etag);
-                }
-                if (lane == 0) {
-                    if (!lok)
-                        raise_error(a.hdr, kErrTimeout);
-                    s_carry = (uint32_t)carry;
-                    s_flag = lok ? 0u : 1u;
-                }
+            if (tid == 0) {
+                // Other CTAs may look back at this tile right away.
+                if (tile != 0)
+                    publish(&a.st[tile].val_tag, &a.st[tile].val_agg, vagg, kFlagAgg, etag);
+                cs.agg[k & 1] = vagg;
+                mbar_arrive(&cs.agg_full[k & 1]);
             }
-            named_sync(1, kThreads);
-            const uint32_t base = s_carry + bpre;
-            const bool failed = s_flag != 0;
+            // Store the previous tile now that its carry has had a tile's time.
+            if (has_prev)
+                store_delta_tile(a, cs, k - 1, x_prev, op_prev, nq_prev, q0_prev, full_prev,
+                                 last_nints, lane);
 #pragma unroll
-            for (int r = 0; r < kTileRounds; r++) {
-                const uint32_t lq = lq0 + r * 32;
-                if (failed || lq >= nq)
-                    continue;
-                const uint32_t nints = full ? 4u : (q0 + lq == a.nquads - 1 ? last_nints : 4u);
-                const uint32_t add = base + qexcl[r];
-                uint32_t *dst = op + 128 * r;
-                uint4 x = make_uint4(v[r][0] + add, v[r][1] + add, v[r][2] + add, v[r][3] + add);
-                if (nints == 4 && a.out_aligned) {
-                    stg_stream128(dst, x);
-                } else {
-                    dst[0] = x.x;
-                    if (nints > 1)
-                        dst[1] = x.y;
-                    if (nints > 2)
-                        dst[2] = x.z;
-                    if (nints > 3)
-                        dst[3] = x.w;
-                }
-            }
-            // Keep going after a failed look-back: later tiles will bail out
-            // on the raised error, and the producer must still drain.
+            for (int r = 0; r < kTileRounds; r++)
+#pragma unroll
+                for (int j = 0; j < 4; j++)
+                    x_prev[r][j] = v[r][j] + qexcl[r] + bpre;
+            op_prev = op;
+            nq_prev = nq;
+            q0_prev = q0;
+            full_prev = full;
+            has_prev = true;
         }
     }
+    if (kDelta && has_prev)
+        store_delta_tile(a, cs, k - 1, x_prev, op_prev, nq_prev, q0_prev, full_prev, last_nints,
+                         lane);
 }
 
 template <bool kDelta>
-__global__ void __launch_bounds__(kDecBlock, 3) decode_tiled_kernel(TiledArgs a)
+__global__ void __launch_bounds__(kDelta ? kDecBlockDelta : kDecBlock, kDelta ? 2 : 3)
+    decode_tiled_kernel(TiledArgs a)
 {
     extern __shared__ __align__(128) uint8_t dyn_smem[];
     Pipe &P = *reinterpret_cast<Pipe *>(dyn_smem);
     __shared__ __align__(16) uint16_t s_qoff[kTileQuads];
     __shared__ uint32_t s_warp[kWarps];
     __shared__ u64 s_etag;
-    __shared__ uint32_t s_flag, s_carry;
+    __shared__ uint32_t s_flag;
+    __shared__ __align__(8) CarrySync cs;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
         for (int s = 0; s < kStages; s++) {
             mbar_init(&P.full[s], 32);        // the 32 producer lanes arrive
             mbar_init(&P.empty[s], kWarps);   // one arrival per consumer warp
+        }
+        for (int i = 0; i < 2; i++) {
+            mbar_init(&cs.agg_full[i], 1);
+            mbar_init(&cs.carry_full[i], 1);
         }
         fence_mbar_init();
         s_etag = (ld_relaxed(&a.hdr->epoch) + 1) << 2;
@@ -619,8 +678,10 @@ __global__ void __launch_bounds__(kDecBlock, 3) decode_tiled_kernel(TiledArgs a)
 
     if (warp == kWarps)
         produce<kDelta>(a, P, lane);
+    else if (warp == kWarps + 1)
+        carry_warp(a, cs, s_etag, lane);
     else
-        consume<kDelta>(a, P, s_qoff, s_warp, s_etag, s_flag, s_carry);
+        consume<kDelta>(a, P, s_qoff, s_warp, s_etag, cs);
     finish_launch(a.hdr, a.result);
 }
 
@@ -648,7 +709,8 @@ static int tiled_grid()
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Pipe));
         int occ = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, decode_tiled_kernel<kDelta>,
-                                                      kDecBlock, sizeof(Pipe));
+                                                      kDelta ? kDecBlockDelta : kDecBlock,
+                                                      sizeof(Pipe));
         g = sm_count() * (occ > 0 ? occ : 1);
     }
     return g;
@@ -710,7 +772,7 @@ int launch_decode_tiled(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, uin
         u64 grid = min((u64)tiled_grid<true>(), ntiles);
         void *args[] = {&t};
         cudaError_t e = cudaLaunchCooperativeKernel((const void *)decode_tiled_kernel<true>,
-                                                    dim3((unsigned)grid), dim3(kDecBlock), args,
+                                                    dim3((unsigned)grid), dim3(kDecBlockDelta), args,
                                                     sizeof(Pipe), stream);
         if (e != cudaSuccess)
             return 3;

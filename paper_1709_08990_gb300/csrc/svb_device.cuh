@@ -171,15 +171,22 @@ __device__ __forceinline__ void publish(u64 *tag, u64 *slot, u64 value, u64 flag
 
 constexpr int kLookbackPerLane = 8;  // predecessors each lane inspects per round trip
 
+__device__ __forceinline__ void fence_acq_rel_gpu()
+{
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+
 // Exclusive prefix of tile `tile` (> 0) for one scan (kVal: the delta running
 // sum, else the byte offsets), computed by one whole warp.  One round trip
 // inspects a window of 32 * kLookbackPerLane predecessors (lane l owns the
-// kLookbackPerLane nearest-to-farthest run starting l * kLookbackPerLane
-// tiles back); the window's values are summed up to the nearest published
-// inclusive prefix, or wholly and the next window is taken.  A window this
-// wide keeps the look-back shallow even when tiles are claimed faster than
-// one L2 round trip per 256 tiles.  Every poll is bounded: after spin_limit
-// polls (backing off to ~1 us each), or as soon as another tile has raised an
+// run of kLookbackPerLane tiles starting l * kLookbackPerLane tiles back,
+// nearest first); the window is summed up to its nearest published inclusive
+// prefix, or wholly, and then the next window is taken.  The tag loads of a
+// window are relaxed and independent, so they are in flight together; one
+// acquire fence after the window's tags are valid orders the value loads
+// after them (a release store of the tag, a relaxed load that sees it and an
+// acquire fence synchronise).  Every poll is bounded: after spin_limit polls
+// (backing off to ~0.25 us each), or as soon as another tile has raised an
 // error, it returns with ok = false and the caller records the failure.
 template <bool kVal>
 __device__ u64 lookback(TileStatus *st, u64 tile, u64 etag, u64 spin_limit, WsHeader *hdr,
@@ -195,7 +202,7 @@ __device__ u64 lookback(TileStatus *st, u64 tile, u64 etag, u64 spin_limit, WsHe
 #pragma unroll
         for (int j = 0; j < K; j++) {
             long long p = base - (lane * K + j);
-            tags[j] = p >= 0 ? ld_acquire(kVal ? &st[p].val_tag : &st[p].off_tag)
+            tags[j] = p >= 0 ? ld_relaxed(kVal ? &st[p].val_tag : &st[p].off_tag)
                              : (etag | kFlagPrefix);
         }
         bool failed = false;
@@ -203,16 +210,14 @@ __device__ u64 lookback(TileStatus *st, u64 tile, u64 etag, u64 spin_limit, WsHe
         for (int j = 0; j < K; j++) {
             long long p = base - (lane * K + j);
             u64 spins = 0;
-            unsigned ns = 32;
             while (!failed && p >= 0 &&
                    ((tags[j] & ~3ull) != etag || (tags[j] & 3ull) == kFlagNone)) {
                 if (++spins > spin_limit || ((spins & 31) == 0 && error_raised(hdr))) {
                     failed = true;
                 } else {
-                    __nanosleep(ns);
-                    if (ns < 512)
-                        ns <<= 1;
-                    tags[j] = ld_acquire(kVal ? &st[p].val_tag : &st[p].off_tag);
+                    if (spins > 4)
+                        __nanosleep(spins < 64 ? 32 : 256);
+                    tags[j] = ld_relaxed(kVal ? &st[p].val_tag : &st[p].off_tag);
                 }
             }
         }
@@ -220,26 +225,32 @@ __device__ u64 lookback(TileStatus *st, u64 tile, u64 etag, u64 spin_limit, WsHe
             ok = false;
             return 0;
         }
+        fence_acq_rel_gpu();
         // Lane-local: sum up to and including this lane's nearest prefix.
-        u64 sum = 0;
-        bool has_prefix = false;
+        u64 vals[K];
+        int stop = K;  // index of this lane's nearest prefix, K if none
+#pragma unroll
+        for (int j = K - 1; j >= 0; j--) {
+            long long p = base - (lane * K + j);
+            bool pre = p < 0 || (tags[j] & 3ull) == kFlagPrefix;
+            if (pre)
+                stop = j;
+        }
 #pragma unroll
         for (int j = 0; j < K; j++) {
             long long p = base - (lane * K + j);
-            if (!has_prefix) {
-                u64 v = 0;
-                if (p >= 0) {
-                    bool pre = (tags[j] & 3ull) == kFlagPrefix;
-                    v = ld_relaxed(kVal ? (pre ? &st[p].val_pre : &st[p].val_agg)
-                                        : (pre ? &st[p].off_pre : &st[p].off_agg));
-                    has_prefix = pre;
-                } else {
-                    has_prefix = true;
-                }
-                sum += v;
+            vals[j] = 0;
+            if (j <= stop && p >= 0) {
+                bool pre = (tags[j] & 3ull) == kFlagPrefix;
+                vals[j] = ld_relaxed(kVal ? (pre ? &st[p].val_pre : &st[p].val_agg)
+                                          : (pre ? &st[p].off_pre : &st[p].off_agg));
             }
         }
-        unsigned pm = __ballot_sync(0xffffffffu, has_prefix);
+        u64 sum = 0;
+#pragma unroll
+        for (int j = 0; j < K; j++)
+            sum += vals[j];
+        unsigned pm = __ballot_sync(0xffffffffu, stop < K);
         int k = pm ? __ffs(pm) - 1 : 31;
         excl += warp_sum64(lane <= k ? sum : 0ull);
         if (pm)
