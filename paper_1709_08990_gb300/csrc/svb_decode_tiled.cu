@@ -20,12 +20,13 @@
 //                    mbarrier); consumers decode a full stage and release it
 //                    on its "empty" mbarrier.  Plain streams never wait on
 //                    another CTA; loads for later tiles are always in flight.
-// Differential streams add one look-back over the tiles' gap sums (the carry
-// of Sec. 2's prefix sum across tiles) before a tile's values are stored.
-// Tiles go round-robin over the CTAs (CTA c takes c, c + G, c + 2G, ...), so
-// the tiles a look-back waits on are the ones the other CTAs decode in the
-// same round.  Differential launches are cooperative: every CTA is resident
-// at once, so each predecessor is always owned by a running CTA.
+// Differential streams need each tile's carry-in, prev plus the sum of all
+// earlier gaps (Sec. 2's prefix sum continued across tiles).  A sums pass runs
+// the same pipeline without stores: persistent CTAs take contiguous tile
+// ranges, sum each tile's gaps, and chain the range totals with one look-back
+// per CTA into per-tile carries.  The decode pass then adds a known carry and
+// never waits on another CTA.  For streams that fit in L2 (129 MB) the second
+// read of the stream is served by L2.
 //
 // Bytes outside the stream are never read: each tile's range is copied as its
 // 16-byte-aligned interior by the bulk engine plus a ragged head and tail of
@@ -44,7 +45,6 @@ constexpr int kStageData = kTileData + 64;          // + 16-byte phase + 2-word 
 constexpr int kStageCtrl = kTileQuads + 32;
 constexpr int kStages = 4;
 constexpr int kDecBlock = kThreads + 32;            // 8 consumer warps + 1 producer warp
-constexpr int kDecBlockDelta = kThreads + 64;       // + 1 warp for the carry look-back
 constexpr u64 kBarrierPolls = 1ull << 24;           // bound on one mbarrier wait
 constexpr u64 kNoTile = ~0ull;
 
@@ -213,15 +213,23 @@ __global__ void __launch_bounds__(kThreads) offsets_kernel(OffsetsArgs a)
 // ---------------------------------------------------------------------------
 // Pass 2: persistent decode, producer warp + consumer warps.
 
+enum TiledMode : int {
+    kPlain = 0,  // decode and store
+    kDelta = 1,  // decode, running sums plus the tile's precomputed carry, store
+    kSums = 2,   // decode, sum the tile's gaps; write per-tile carries (no stores)
+};
+
 struct TiledArgs {
     const uint8_t *in;
     u64 n, nquads, ntiles;
     uint32_t *out;
     const u64 *offs;
+    uint32_t *carries;  // per tile: written by kSums, read by kDelta
     WsHeader *hdr;
     TileStatus *st;
     DeviceResult *result;
     u64 spin_limit;
+    u64 per_cta;        // kSums: tiles per CTA (contiguous ranges)
     uint32_t prev;
     uint32_t out_aligned;
 };
@@ -233,16 +241,7 @@ struct Pipe {
     uint64_t empty[kStages];
     u64 tile[kStages];
     uint32_t hd[kStages], hc[kStages];  // address phase (mod 16) of the data / control range
-};
-
-// Hand-off between the consumers and the carry warp of a differential decode:
-// per tile parity, the tile's gap sum (consumers -> carry warp) and its
-// carry-in (carry warp -> consumers), each announced on an mbarrier.
-struct CarrySync {
-    uint64_t agg_full[2];
-    uint64_t carry_full[2];
-    uint32_t agg[2];
-    uint32_t carry[2];
+    uint32_t carry[kStages];            // kDelta: the tile's carry-in
 };
 
 // Interior of global [g, g + len): the 16-byte-aligned part, copied by the
@@ -305,13 +304,25 @@ __device__ __forceinline__ uint4 widen_quad(const uint8_t *d, uint32_t p)
                       __byte_perm(x, 0, 0x4442), __byte_perm(x, 0, 0x4443));
 }
 
+// The k-th tile this CTA handles: round-robin for decoding, a contiguous
+// range for the sums pass (whose look-back chains ranges in order).
+template <int kMode>
+__device__ __forceinline__ u64 tile_of(const TiledArgs &a, u64 first, uint32_t k)
+{
+    if (kMode == kSums) {
+        const u64 end = min(first + a.per_cta, a.ntiles);
+        return first + k < end ? first + k : a.ntiles;
+    }
+    return first + (u64)k * gridDim.x;
+}
+
 // Producer warp: fill stages with tiles until none is left, then post one
 // stage marked kNoTile.  Returns normally or after a bounded wait gave up.
-template <bool kDelta>
-__device__ void produce(const TiledArgs &a, Pipe &P, int lane)
+template <int kMode>
+__device__ void produce(const TiledArgs &a, Pipe &P, u64 first, int lane)
 {
     uint32_t issued = 0;  // stage fills posted (iteration k fills stage k % kStages)
-    u64 next = blockIdx.x;
+    u64 next = tile_of<kMode>(a, first, 0);
     u64 nd0 = 0, nd1 = 0;
     if (next < a.ntiles) {
         nd0 = a.offs[next];
@@ -339,9 +350,8 @@ __device__ void produce(const TiledArgs &a, Pipe &P, int lane)
             issued = k + 1;
             break;
         }
-        // Tiles go round-robin over the CTAs; read the next tile's offsets now
-        // so that the load overlaps this one.
-        next = t + gridDim.x;
+        // Read the next tile's offsets now so that the load overlaps this one.
+        next = tile_of<kMode>(a, first, k + 1);
         if (next < a.ntiles) {
             nd0 = a.offs[next];
             nd1 = a.offs[next + 1];
@@ -361,6 +371,8 @@ __device__ void produce(const TiledArgs &a, Pipe &P, int lane)
             P.tile[s] = t;
             P.hc[s] = (uint32_t)((uintptr_t)gc & 15u);
             P.hd[s] = (uint32_t)((uintptr_t)gd & 15u);
+            if (kMode == kDelta)
+                P.carry[s] = a.carries[t];
             mbar_arrive_expect_tx(&P.full[s], bc + bd);
             if (bc)
                 bulk_g2s(P.ctrl[s] + oc, ac, bc, &P.full[s]);
@@ -383,82 +395,15 @@ __device__ void produce(const TiledArgs &a, Pipe &P, int lane)
     __syncwarp();
 }
 
-// Store tile k of this CTA (running sums in x, carry-in from the carry warp).
-__device__ __forceinline__ void store_delta_tile(const TiledArgs &a, CarrySync &cs, uint32_t k,
-                                                 const uint32_t (&x)[kTileRounds][4],
-                                                 uint32_t *op, uint32_t nq, u64 q0, bool full,
-                                                 uint32_t last_nints, int lane)
-{
-    const int warp = threadIdx.x >> 5;
-    mbar_wait_bounded(&cs.carry_full[k & 1], (k >> 1) & 1u, kBarrierPolls);
-    const uint32_t carry = cs.carry[k & 1];
-    const uint32_t lq0 = warp * (32 * kTileRounds) + lane;
-#pragma unroll
-    for (int r = 0; r < kTileRounds; r++) {
-        const uint32_t lq = lq0 + r * 32;
-        if (lq >= nq)
-            continue;
-        const uint32_t nints = full ? 4u : (q0 + lq == a.nquads - 1 ? last_nints : 4u);
-        uint32_t *dst = op + 128 * r;
-        uint4 y = make_uint4(x[r][0] + carry, x[r][1] + carry, x[r][2] + carry, x[r][3] + carry);
-        if (nints == 4 && a.out_aligned) {
-            stg_stream128(dst, y);
-        } else {
-            dst[0] = y.x;
-            if (nints > 1)
-                dst[1] = y.y;
-            if (nints > 2)
-                dst[2] = y.z;
-            if (nints > 3)
-                dst[3] = y.w;
-        }
-    }
-}
-
-// Carry warp of a differential decode: for each of this CTA's tiles, in
-// order, wait for the consumers' gap sum, find the tile's carry-in by
-// look-back, publish the tile's inclusive prefix and hand the carry back.
-__device__ void carry_warp(const TiledArgs &a, CarrySync &cs, u64 etag, int lane)
-{
-    uint32_t k = 0;
-    for (u64 tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, k++) {
-        bool ok = mbar_wait_bounded(&cs.agg_full[k & 1], (k >> 1) & 1u, kBarrierPolls);
-        const uint32_t vagg = cs.agg[k & 1];
-        TileStatus *me = &a.st[tile];
-        u64 carry = a.prev;
-        if (ok && tile != 0)
-            carry = lookback<true>(a.st, tile, etag, a.spin_limit, a.hdr, ok);
-        if (lane == 0) {
-            if (ok)
-                publish(&me->val_tag, &me->val_pre, (uint32_t)(carry + vagg), kFlagPrefix, etag);
-            else
-                raise_error(a.hdr, kErrTimeout);
-            cs.carry[k & 1] = (uint32_t)carry;
-            mbar_arrive(&cs.carry_full[k & 1]);
-        }
-        __syncwarp();
-        if (!ok)
-            break;
-    }
-}
-
 // Consumer warps (8, synchronised among themselves by named barrier 1).
-template <bool kDelta>
+template <int kMode>
 __device__ void consume(const TiledArgs &a, Pipe &P, uint16_t *s_qoff, uint32_t *s_warp,
-                        u64 s_etag, CarrySync &cs)
+                        u64 first, u64 etag)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const u64 etag = s_etag;
     const uint32_t last_nints = (uint32_t)(a.n - 4 * (a.nquads - 1));
-    // Differential: tile k's running sums wait in x_prev until its carry-in
-    // arrives; they are stored while tile k + 1 is being decoded.
-    uint32_t x_prev[kTileRounds][4];
-    uint32_t *op_prev = nullptr;
-    uint32_t nq_prev = 0;
-    u64 q0_prev = 0;
-    bool full_prev = true, has_prev = false;
-    uint32_t k = 0;
-    for (;; k++) {
+    uint32_t running = 0;  // kSums: gap sum of this CTA's tiles so far (thread 0)
+    for (uint32_t k = 0;; k++) {
         const int s = k % kStages;
         bool ok = mbar_wait_bounded(&P.full[s], (k / kStages) & 1u, kBarrierPolls);
         if (!ok) {  // cannot happen unless a copy is lost; give up quietly
@@ -469,7 +414,7 @@ __device__ void consume(const TiledArgs &a, Pipe &P, uint16_t *s_qoff, uint32_t 
         if (tile == kNoTile)
             break;
 
-        // ---- control bytes -> quad offsets inside the tile ----------------
+        // ---- control bytes -> staged position of every quad -----------------
         const u64 q0 = tile * kTileQuads;
         const uint32_t nq = (uint32_t)min((u64)kTileQuads, a.nquads - q0);
         // Every tile but possibly the last holds kTileQuads quads of four.
@@ -477,6 +422,7 @@ __device__ void consume(const TiledArgs &a, Pipe &P, uint16_t *s_qoff, uint32_t 
         const uint8_t *C = P.ctrl[s] + P.hc[s];
         const uint8_t *D = P.data[s];
         const uint32_t h = P.hd[s];
+        const uint32_t carry_in = kMode == kDelta ? P.carry[s] : 0u;
         uint32_t w = 0;
         if (P.hc[s] == 0 && 4u * tid + 4u <= nq) {
             w = reinterpret_cast<const uint32_t *>(C)[tid];
@@ -550,7 +496,7 @@ __device__ void consume(const TiledArgs &a, Pipe &P, uint16_t *s_qoff, uint32_t 
                 v[r][1] = x.y;
                 v[r][2] = x.z;
                 v[r][3] = x.w;
-                if (!kDelta) {
+                if (kMode == kPlain) {
                     if (a.out_aligned) {
                         stg_stream128(op + 128 * r, x);
                     } else {
@@ -572,11 +518,11 @@ __device__ void consume(const TiledArgs &a, Pipe &P, uint16_t *s_qoff, uint32_t 
                     c &= (1u << (2 * nints)) - 1u;
                 const uint32_t p = valid ? s_qoff[lq] : h;
                 uint4 x = decode_quad(D, p, c);
-                v[r][0] = x.x;
+                v[r][0] = nints > 0 ? x.x : 0u;
                 v[r][1] = nints > 1 ? x.y : 0u;
                 v[r][2] = nints > 2 ? x.z : 0u;
                 v[r][3] = nints > 3 ? x.w : 0u;
-                if (!kDelta && valid) {
+                if (kMode == kPlain && valid) {
                     op[128 * r] = x.x;
                     if (nints > 1)
                         op[128 * r + 1] = x.y;
@@ -592,8 +538,30 @@ __device__ void consume(const TiledArgs &a, Pipe &P, uint16_t *s_qoff, uint32_t 
         if (lane == 0)
             mbar_arrive(&P.empty[s]);
 
-        if (kDelta) {
-            // ---- running sums: quad, warp, block; the carry comes later ------
+        if (kMode == kSums) {
+            // ---- the tile's gap sum; thread 0 keeps the CTA's running total --
+            uint32_t t = 0;
+#pragma unroll
+            for (int r = 0; r < kTileRounds; r++)
+                t += v[r][0] + v[r][1] + v[r][2] + v[r][3];
+#pragma unroll
+            for (int d = 16; d >= 1; d >>= 1)
+                t += __shfl_xor_sync(0xffffffffu, t, d);
+            named_sync(1, kThreads);  // every warp has read s_warp (offsets) above
+            if (lane == 0)
+                s_warp[warp] = t;
+            named_sync(1, kThreads);
+            if (tid == 0) {
+                uint32_t vagg = 0;
+#pragma unroll
+                for (int j = 0; j < kWarps; j++)
+                    vagg += s_warp[j];
+                a.carries[tile] = running;  // carry relative to the CTA's first tile
+                running += vagg;
+            }
+        }
+        if (kMode == kDelta) {
+            // ---- running sums: quad, warp, block, plus the carry-in -----------
             uint32_t qexcl[kTileRounds], wrun = 0;
 #pragma unroll
             for (int r = 0; r < kTileRounds; r++) {
@@ -609,52 +577,79 @@ __device__ void consume(const TiledArgs &a, Pipe &P, uint16_t *s_qoff, uint32_t 
             if (lane == 0)
                 s_warp[warp] = wrun;
             named_sync(1, kThreads);
-            uint32_t bpre = 0, vagg = 0;
+            uint32_t bpre = carry_in;
 #pragma unroll
-            for (int j = 0; j < kWarps; j++) {
-                uint32_t t = s_warp[j];
-                bpre += j < warp ? t : 0u;
-                vagg += t;
+            for (int j = 0; j < kWarps; j++)
+                bpre += j < warp ? s_warp[j] : 0u;
+#pragma unroll
+            for (int r = 0; r < kTileRounds; r++) {
+                const uint32_t lq = lq0 + r * 32;
+                if (lq >= nq)
+                    continue;
+                const uint32_t nints = full ? 4u : (q0 + lq == a.nquads - 1 ? last_nints : 4u);
+                const uint32_t add = bpre + qexcl[r];
+                uint32_t *dst = op + 128 * r;
+                uint4 y = make_uint4(v[r][0] + add, v[r][1] + add, v[r][2] + add, v[r][3] + add);
+                if (nints == 4 && a.out_aligned) {
+                    stg_stream128(dst, y);
+                } else {
+                    dst[0] = y.x;
+                    if (nints > 1)
+                        dst[1] = y.y;
+                    if (nints > 2)
+                        dst[2] = y.z;
+                    if (nints > 3)
+                        dst[3] = y.w;
+                }
             }
-            if (tid == 0) {
-                // Other CTAs may look back at this tile right away.
-                if (tile != 0)
-                    publish(&a.st[tile].val_tag, &a.st[tile].val_agg, vagg, kFlagAgg, etag);
-                cs.agg[k & 1] = vagg;
-                mbar_arrive(&cs.agg_full[k & 1]);
-            }
-            // Store the previous tile now that its carry has had a tile's time.
-            if (has_prev)
-                store_delta_tile(a, cs, k - 1, x_prev, op_prev, nq_prev, q0_prev, full_prev,
-                                 last_nints, lane);
-#pragma unroll
-            for (int r = 0; r < kTileRounds; r++)
-#pragma unroll
-                for (int j = 0; j < 4; j++)
-                    x_prev[r][j] = v[r][j] + qexcl[r] + bpre;
-            op_prev = op;
-            nq_prev = nq;
-            q0_prev = q0;
-            full_prev = full;
-            has_prev = true;
         }
     }
-    if (kDelta && has_prev)
-        store_delta_tile(a, cs, k - 1, x_prev, op_prev, nq_prev, q0_prev, full_prev, last_nints,
-                         lane);
+
+    if (kMode == kSums) {
+        // Chain this CTA's range total with the ranges before it, then turn
+        // the range-relative carries into absolute ones (prev included).
+        __shared__ uint32_t s_base;
+        if (warp == 0) {
+            u64 range_total = __shfl_sync(0xffffffffu, running, 0);
+            TileStatus *me = &a.st[first / (a.per_cta ? a.per_cta : 1)];
+            const u64 cta = first / (a.per_cta ? a.per_cta : 1);
+            u64 base = a.prev;
+            bool ok = true;
+            if (cta == 0) {
+                if (lane == 0)
+                    publish(&me->val_tag, &me->val_pre, (uint32_t)(a.prev + range_total),
+                            kFlagPrefix, etag);
+            } else {
+                if (lane == 0)
+                    publish(&me->val_tag, &me->val_agg, (uint32_t)range_total, kFlagAgg, etag);
+                base = lookback<true>(a.st, cta, etag, a.spin_limit, a.hdr, ok);
+                if (ok && lane == 0)
+                    publish(&me->val_tag, &me->val_pre, (uint32_t)(base + range_total),
+                            kFlagPrefix, etag);
+            }
+            if (lane == 0) {
+                if (!ok)
+                    raise_error(a.hdr, kErrTimeout);
+                s_base = (uint32_t)base;
+            }
+        }
+        named_sync(1, kThreads);
+        const uint32_t base = s_base;
+        const u64 end = min(first + a.per_cta, a.ntiles);
+        for (u64 t = first + tid; t < end; t += kThreads)
+            a.carries[t] += base;
+    }
 }
 
-template <bool kDelta>
-__global__ void __launch_bounds__(kDelta ? kDecBlockDelta : kDecBlock, kDelta ? 2 : 3)
-    decode_tiled_kernel(TiledArgs a)
+template <int kMode>
+__global__ void __launch_bounds__(kDecBlock, 3) decode_tiled_kernel(TiledArgs a)
 {
     extern __shared__ __align__(128) uint8_t dyn_smem[];
     Pipe &P = *reinterpret_cast<Pipe *>(dyn_smem);
     __shared__ __align__(16) uint16_t s_qoff[kTileQuads];
     __shared__ uint32_t s_warp[kWarps];
-    __shared__ u64 s_etag;
+    __shared__ u64 s_etag, s_first;
     __shared__ uint32_t s_flag;
-    __shared__ __align__(8) CarrySync cs;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
@@ -662,27 +657,36 @@ __global__ void __launch_bounds__(kDelta ? kDecBlockDelta : kDecBlock, kDelta ? 
             mbar_init(&P.full[s], 32);        // the 32 producer lanes arrive
             mbar_init(&P.empty[s], kWarps);   // one arrival per consumer warp
         }
-        for (int i = 0; i < 2; i++) {
-            mbar_init(&cs.agg_full[i], 1);
-            mbar_init(&cs.carry_full[i], 1);
-        }
         fence_mbar_init();
         s_etag = (ld_relaxed(&a.hdr->epoch) + 1) << 2;
         s_flag = error_raised(a.hdr) ? 1u : 0u;
+        // The sums pass takes ranges in claim order, so every range before
+        // this one belongs to a CTA that is running or done.
+        s_first = kMode == kSums ? atomicAdd(&a.hdr->tile_counter, 1ull) * a.per_cta
+                                 : (u64)blockIdx.x;
     }
     __syncthreads();
-    if (s_flag) {  // the offsets pass failed (truncated stream)
-        finish_launch(a.hdr, a.result);
-        return;
+    if (!s_flag) {  // else the offsets pass failed (truncated stream)
+        if (warp == kWarps)
+            produce<kMode>(a, P, s_first, lane);
+        else
+            consume<kMode>(a, P, s_qoff, s_warp, s_first, s_etag);
     }
-
-    if (warp == kWarps)
-        produce<kDelta>(a, P, lane);
-    else if (warp == kWarps + 1)
-        carry_warp(a, cs, s_etag, lane);
-    else
-        consume<kDelta>(a, P, s_qoff, s_warp, s_etag, cs);
-    finish_launch(a.hdr, a.result);
+    if (kMode == kSums) {
+        // The decode pass that follows owns the result and the counters; only
+        // reset the claim counter for it.
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            u64 done = atomicAdd(&a.hdr->done_counter, 1ull);
+            if (done == (u64)gridDim.x - 1) {
+                st_relaxed(&a.hdr->tile_counter, 0);
+                st_relaxed(&a.hdr->done_counter, 0);
+            }
+        }
+    } else {
+        finish_launch(a.hdr, a.result);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -700,16 +704,15 @@ static int sm_count()
     return sms;
 }
 
-template <bool kDelta>
+template <int kMode>
 static int tiled_grid()
 {
     static int g = 0;
     if (!g) {
-        cudaFuncSetAttribute(decode_tiled_kernel<kDelta>,
+        cudaFuncSetAttribute(decode_tiled_kernel<kMode>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Pipe));
         int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, decode_tiled_kernel<kDelta>,
-                                                      kDelta ? kDecBlockDelta : kDecBlock,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, decode_tiled_kernel<kMode>, kDecBlock,
                                                       sizeof(Pipe));
         g = sm_count() * (occ > 0 ? occ : 1);
     }
@@ -736,6 +739,7 @@ int launch_decode_tiled(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, uin
     const u64 ntiles = (nquads + kTileQuads - 1) / kTileQuads;
     WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
     u64 *offs = reinterpret_cast<u64 *>(static_cast<char *>(ws) + L.offs);
+    uint32_t *carries = reinterpret_cast<uint32_t *>(static_cast<char *>(ws) + L.carries);
     TileStatus *st = reinterpret_cast<TileStatus *>(static_cast<char *>(ws) + L.status);
 
     OffsetsArgs o;
@@ -762,23 +766,26 @@ int launch_decode_tiled(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, uin
     t.ntiles = ntiles;
     t.out = out;
     t.offs = offs;
+    t.carries = carries;
     t.hdr = hdr;
     t.st = st;
     t.result = result;
     t.spin_limit = spin_limit;
+    t.per_cta = 0;
     t.prev = prev;
     t.out_aligned = (((uintptr_t)out) & 15u) == 0;
     if (delta) {
-        u64 grid = min((u64)tiled_grid<true>(), ntiles);
-        void *args[] = {&t};
-        cudaError_t e = cudaLaunchCooperativeKernel((const void *)decode_tiled_kernel<true>,
-                                                    dim3((unsigned)grid), dim3(kDecBlockDelta), args,
-                                                    sizeof(Pipe), stream);
-        if (e != cudaSuccess)
-            return 3;
+        // Sums pass over contiguous ranges, then the decode with carries.
+        u64 sgrid = min((u64)tiled_grid<kSums>(), ntiles);
+        t.per_cta = (ntiles + sgrid - 1) / sgrid;
+        sgrid = (ntiles + t.per_cta - 1) / t.per_cta;
+        decode_tiled_kernel<kSums><<<(unsigned)sgrid, kDecBlock, sizeof(Pipe), stream>>>(t);
+        t.per_cta = 0;
+        u64 grid = min((u64)tiled_grid<kDelta>(), ntiles);
+        decode_tiled_kernel<kDelta><<<(unsigned)grid, kDecBlock, sizeof(Pipe), stream>>>(t);
     } else {
-        u64 grid = min((u64)tiled_grid<false>(), ntiles);
-        decode_tiled_kernel<false><<<(unsigned)grid, kDecBlock, sizeof(Pipe), stream>>>(t);
+        u64 grid = min((u64)tiled_grid<kPlain>(), ntiles);
+        decode_tiled_kernel<kPlain><<<(unsigned)grid, kDecBlock, sizeof(Pipe), stream>>>(t);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }

@@ -57,7 +57,8 @@ constexpr size_t kResultOffset = 128;
 constexpr size_t kOffsetsOffset = 256;
 
 struct WsLayout {
-    size_t offs;     // byte offset of the tile-offset array
+    size_t offs;     // byte offset of the tile-offset array (u64 x tiles + 1)
+    size_t carries;  // byte offset of the per-tile carry array (u32 x tiles)
     size_t status;   // byte offset of the TileStatus array
     size_t total;    // workspace bytes
 };
@@ -67,8 +68,8 @@ inline WsLayout ws_layout_for_tiles(u64 tiles)
 {
     WsLayout l;
     l.offs = kOffsetsOffset;
-    size_t st = l.offs + 8 * (tiles + 1);
-    l.status = (st + 63) & ~(size_t)63;
+    l.carries = (l.offs + 8 * (tiles + 1) + 63) & ~(size_t)63;
+    l.status = (l.carries + 4 * (tiles ? tiles : 1) + 63) & ~(size_t)63;
     l.total = l.status + sizeof(TileStatus) * (tiles ? tiles : 1);
     return l;
 }
