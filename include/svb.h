@@ -162,6 +162,51 @@ int svb_decode_async(const uint8_t *in, size_t in_len, size_t n, uint32_t *out,
                      uint32_t prev, int delta, svb_result *d_result, void *ws,
                      size_t ws_bytes, svb_stream_t stream);
 
+/* ---- batched codec: many independent lists in one launch --------------- */
+
+/* One list of a batch.  Decode: in_off / in_len locate the list's stream in
+ * the batch's input bytes (in_len = bytes available, at least the stream's
+ * size), out_off is the index of its first integer in the output.  Encode:
+ * in_off is the index of its first integer in the input, out_off the byte
+ * offset of its stream in the output, which must have room for
+ * svb_max_compressed_size(n) bytes; in_len is ignored.  prev is the list's
+ * start value for differential coding (Sec. 5 starts every list from 0). */
+typedef struct svb_list {
+    uint64_t in_off;
+    uint64_t in_len;
+    uint64_t out_off;
+    uint32_t n;
+    uint32_t prev;
+} svb_list;
+
+/* Device bytes of the plan of a batch of num_lists lists. */
+size_t svb_batch_plan_bytes(size_t num_lists);
+
+/* Build a batch's work plan on the host from the list lengths in h_lists
+ * (HOST memory) and copy it to d_plan (DEVICE, svb_batch_plan_bytes bytes)
+ * on stream.  Lists with n >= big_threshold (0: the default, 8192) are each
+ * decoded by one CTA, longest first; shorter ones by one warp each.  A plan
+ * stays valid for any batch with the same list lengths. */
+int svb_batch_plan(const svb_list *h_lists, size_t num_lists, uint32_t big_threshold,
+                   void *d_plan, size_t plan_bytes, svb_stream_t stream);
+
+/* Workspace bytes of a batched call (its counters; zero it once with
+ * svb_workspace_init, like the single-stream workspace). */
+size_t svb_batch_workspace_size(void);
+
+/* Decode / encode every list of the plan in one persistent launch enqueued on
+ * stream.  d_lists is the DEVICE copy of the list table.  d_result receives
+ * the total bytes consumed / written and the status (SVB_ETRUNCATED when
+ * some list's stream is longer than its in_len).  Encode also writes each
+ * list's stream size to d_sizes[list] (DEVICE, one uint64_t per list).
+ * grid: 0 for one CTA per resident slot, else the number of CTAs. */
+int svb_batch_decode(const void *d_plan, const svb_list *d_lists, const uint8_t *in_base,
+                     uint32_t *out_base, int delta, svb_result *d_result, void *ws,
+                     size_t ws_bytes, int grid, svb_stream_t stream);
+int svb_batch_encode(const void *d_plan, const svb_list *d_lists, const uint32_t *in_base,
+                     uint8_t *out_base, int delta, uint64_t *d_sizes, svb_result *d_result,
+                     void *ws, size_t ws_bytes, int grid, svb_stream_t stream);
+
 /* ---- decoding without allocation --------------------------------------- */
 
 /* Largest n that svb_decode_noalloc accepts. */

@@ -327,6 +327,51 @@ int svb_decode_async(const uint8_t *in, size_t in_len, size_t n, uint32_t *out,
                            reinterpret_cast<svb::DeviceResult *>(d_result), s);
 }
 
+size_t svb_batch_plan_bytes(size_t num_lists)
+{
+    return svb::batch_plan_bytes(num_lists);
+}
+
+int svb_batch_plan(const svb_list *h_lists, size_t num_lists, uint32_t big_threshold,
+                   void *d_plan, size_t plan_bytes, svb_stream_t stream)
+{
+    if ((!h_lists && num_lists) || !d_plan || plan_bytes < svb::batch_plan_bytes(num_lists) ||
+        num_lists > 0xffffffffull)
+        return SVB_EINVAL;
+    return svb::build_batch_plan(h_lists, num_lists, big_threshold, d_plan,
+                                 reinterpret_cast<cudaStream_t>(stream));
+}
+
+size_t svb_batch_workspace_size(void)
+{
+    return svb::kOffsetsOffset;
+}
+
+int svb_batch_decode(const void *d_plan, const svb_list *d_lists, const uint8_t *in_base,
+                     uint32_t *out_base, int delta, svb_result *d_result, void *ws,
+                     size_t ws_bytes, int grid, svb_stream_t stream)
+{
+    if (!d_plan || !d_lists || !in_base || !out_base || !d_result || !ws ||
+        ws_bytes < svb::kOffsetsOffset || grid < 0)
+        return SVB_EINVAL;
+    return svb::launch_batch_decode(d_plan, d_lists, in_base, out_base, delta != 0, ws,
+                                    reinterpret_cast<svb::DeviceResult *>(d_result),
+                                    reinterpret_cast<cudaStream_t>(stream), grid);
+}
+
+int svb_batch_encode(const void *d_plan, const svb_list *d_lists, const uint32_t *in_base,
+                     uint8_t *out_base, int delta, uint64_t *d_sizes, svb_result *d_result,
+                     void *ws, size_t ws_bytes, int grid, svb_stream_t stream)
+{
+    if (!d_plan || !d_lists || !in_base || !out_base || !d_sizes || !d_result || !ws ||
+        ws_bytes < svb::kOffsetsOffset || grid < 0)
+        return SVB_EINVAL;
+    return svb::launch_batch_encode(d_plan, d_lists, in_base, out_base,
+                                    reinterpret_cast<u64 *>(d_sizes), delta != 0, ws,
+                                    reinterpret_cast<svb::DeviceResult *>(d_result),
+                                    reinterpret_cast<cudaStream_t>(stream), grid);
+}
+
 int svb_testhook_lookback_timeout(const uint8_t *stream_in, size_t n, uint32_t *out,
                                   uint64_t spin_limit_, svb_result *d_result, void *ws,
                                   size_t ws_bytes, svb_stream_t stream)

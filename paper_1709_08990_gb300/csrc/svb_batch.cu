@@ -1,0 +1,901 @@
+// Batched Stream VByte codec: many independent streams (posting lists, the
+// paper's use case in Sec. 5) of very uneven lengths in one persistent launch.
+//
+// Each list is its own stream (ceil(n/4) control bytes, then data, Sec. 4)
+// with its own start value for differential coding (Sec. 2, Sec. 5).  Lists
+// are independent, so no list ever waits on another:
+//   * big lists (n >= the plan's threshold, longest first) are each taken by
+//     one CTA and processed tile by tile through the same producer/consumer
+//     pipeline as the single-stream decoder.  The producer sums each tile's
+//     control bytes to find where the next tile's data starts, so it needs no
+//     separate offsets pass; consumers carry the running differential sum of
+//     the list from tile to tile in registers.
+//   * small lists are taken one at a time by single warps once the big lists
+//     are handed out; every warp of the CTA (the producer included) takes
+//     part, which also evens out the end of the launch.
+// The plan (built on the host from the list lengths) holds the two id lists.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "svb.h"
+#include "svb_device.cuh"
+#include "svb_internal.h"
+#include "svb_quad.cuh"
+
+namespace svb {
+
+constexpr int kBQuads = 1024;                // quads per tile
+constexpr int kBRounds = kBQuads / kThreads;
+constexpr int kBStages = 4;
+constexpr int kBStageData = 16 * kBQuads + 64;
+constexpr int kBStageCtrl = kBQuads + 32;
+constexpr int kBBlock = kThreads + 32;       // 8 consumer warps + 1 producer warp
+constexpr u64 kBPolls = 1ull << 24;
+constexpr uint32_t kNoList = 0xffffffffu;
+constexpr uint32_t kDefaultBigThreshold = 8192;
+
+// Plan layout in device memory: header, then big ids, then small ids.
+struct PlanHeader {
+    uint32_t nbig, nsmall, threshold, pad;
+};
+
+// ---------------------------------------------------------------------------
+// Decode
+
+struct BatchDecArgs {
+    const svb_list *lists;
+    const PlanHeader *plan;
+    const uint8_t *in;
+    uint32_t *out;
+    WsHeader *hdr;
+    DeviceResult *result;
+    uint32_t delta;
+};
+
+struct BPipe {
+    uint8_t data[kBStages][kBStageData];
+    uint8_t ctrl[kBStages][kBStageCtrl];
+    uint64_t full[kBStages];   // control and data landed (consumers wait)
+    uint64_t cfull[kBStages];  // control landed (the producer waits)
+    uint64_t empty[kBStages];  // consumers done with the stage
+    uint32_t list[kBStages];   // list id, or kNoList
+    uint32_t tile[kBStages];   // tile index within the list
+    uint32_t skip[kBStages];   // the list is truncated: decode nothing
+    uint32_t hd[kBStages], hc[kBStages];
+};
+
+__device__ __forceinline__ const uint32_t *plan_big(const PlanHeader *p)
+{
+    return reinterpret_cast<const uint32_t *>(p + 1);
+}
+
+__device__ __forceinline__ const uint32_t *plan_small(const PlanHeader *p)
+{
+    return plan_big(p) + p->nbig;
+}
+
+// Data bytes of the quads of one tile, from its staged control bytes
+// (pad fields of the list's last quad count nothing).
+__device__ __forceinline__ uint32_t tile_data_bytes(const uint8_t *C, uint32_t nq, bool last_tile,
+                                                    uint32_t last_nints, int lane)
+{
+    uint32_t t = 0;
+    for (uint32_t q = lane; q < nq; q += 32) {
+        uint32_t c = C[q];
+        uint32_t k = (last_tile && q == nq - 1) ? last_nints : 4u;
+        if (k < 4)
+            c &= (1u << (2 * k)) - 1u;
+        t += quad_count(c, k);
+    }
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1)
+        t += __shfl_xor_sync(0xffffffffu, t, d);
+    return t;
+}
+
+// Producer warp of the big-list phase.
+__device__ void bdec_produce(const BatchDecArgs &a, BPipe &P, int lane)
+{
+    const PlanHeader *plan = a.plan;
+    const uint32_t *big = plan_big(plan);
+    uint32_t issued = 0;
+
+    // Current list and tile.
+    uint32_t li = kNoList, k = 0, ntl = 0, nql = 0, last_nints = 4;
+    u64 running = 0;
+    svb_list L = {};
+    auto claim = [&]() -> bool {
+        uint32_t j = 0;
+        if (lane == 0)
+            j = (uint32_t)atomicAdd(&a.hdr->tile_counter, 1ull);
+        j = __shfl_sync(0xffffffffu, j, 0);
+        if (j >= plan->nbig)
+            return false;
+        li = big[j];
+        L = a.lists[li];
+        nql = (L.n + 3) / 4;
+        ntl = (nql + kBQuads - 1) / kBQuads;
+        last_nints = L.n - 4 * (nql - 1);
+        k = 0;
+        running = 0;
+        return true;
+    };
+    auto issue_ctrl = [&](int s) {
+        const uint8_t *gc = a.in + L.in_off + (u64)k * kBQuads;
+        const uint32_t clen = min((uint32_t)kBQuads, nql - k * kBQuads);
+        range_edges(gc, clen, P.ctrl[s], lane);
+        if (lane == 0) {
+            const uint8_t *ac;
+            uint32_t oc;
+            uint32_t bc = range_interior(gc, clen, ac, oc);
+            P.list[s] = li;
+            P.tile[s] = k;
+            P.hc[s] = (uint32_t)((uintptr_t)gc & 15u);
+            mbar_arrive_expect_tx(&P.cfull[s], bc);
+            if (bc)
+                bulk_g2s(P.ctrl[s] + oc, ac, bc, &P.cfull[s]);
+        } else {
+            mbar_arrive(&P.cfull[s]);
+        }
+    };
+    auto post_none = [&](int s) {
+        if (lane == 0) {
+            P.list[s] = kNoList;
+            mbar_arrive_expect_tx(&P.full[s], 0);
+        } else {
+            mbar_arrive(&P.full[s]);
+        }
+    };
+    auto wait_empty = [&](uint32_t g) -> bool {
+        if (g < (uint32_t)kBStages)
+            return true;
+        bool ok = mbar_wait_bounded(&P.empty[g % kBStages], ((g / kBStages) - 1) & 1u, kBPolls);
+        return __all_sync(0xffffffffu, ok);
+    };
+
+    bool have = claim();
+    if (!have) {
+        post_none(0);
+        issued = 1;
+    } else {
+        // A list whose control bytes do not fit is reported and skipped.
+        while (have && nql > L.in_len) {
+            if (lane == 0)
+                raise_error(a.hdr, kErrTruncated);
+            have = claim();
+        }
+        if (!have) {
+            post_none(0);
+            issued = 1;
+        } else {
+            issue_ctrl(0);
+        }
+    }
+    for (uint32_t g = 0; have; g++) {
+        const int s = g % kBStages;
+        if (!mbar_wait_bounded(&P.cfull[s], (g / kBStages) & 1u, kBPolls)) {
+            if (lane == 0)
+                raise_error(a.hdr, kErrTimeout);
+        }
+        __syncwarp();
+        const bool last_tile = k + 1 == ntl;
+        const uint32_t nq = min((uint32_t)kBQuads, nql - k * kBQuads);
+        const uint32_t dsize =
+            tile_data_bytes(P.ctrl[s] + P.hc[s], nq, last_tile, last_nints, lane);
+        const bool trunc = nql + running + dsize > L.in_len;
+        const uint8_t *gd = a.in + L.in_off + nql + running;
+        const uint32_t dlen = trunc ? 0u : dsize;
+        range_edges(gd, dlen, P.data[s], lane);
+        if (lane == 0) {
+            const uint8_t *ad;
+            uint32_t od;
+            uint32_t bd = range_interior(gd, dlen, ad, od);
+            P.hd[s] = (uint32_t)((uintptr_t)gd & 15u);
+            P.skip[s] = trunc ? 1u : 0u;
+            if (trunc)
+                raise_error(a.hdr, kErrTruncated);
+            mbar_arrive_expect_tx(&P.full[s], bd);
+            if (bd)
+                bulk_g2s(P.data[s] + od, ad, bd, &P.full[s]);
+        } else {
+            mbar_arrive(&P.full[s]);
+        }
+        running += dsize;
+        if (last_tile && lane == 0)
+            atomicAdd(&a.hdr->total, (u64)nql + running);
+
+        // Next tile: the rest of this list, or the next big list.
+        if (last_tile || trunc) {
+            have = claim();
+            while (have && nql > L.in_len) {
+                if (lane == 0)
+                    raise_error(a.hdr, kErrTruncated);
+                have = claim();
+            }
+        } else {
+            k++;
+        }
+        if (!wait_empty(g + 1)) {
+            if (lane == 0)
+                raise_error(a.hdr, kErrTimeout);
+            issued = g + 1;
+            break;
+        }
+        if (have)
+            issue_ctrl((g + 1) % kBStages);
+        else
+            post_none((g + 1) % kBStages);
+        issued = g + 2;
+    }
+    // Let every copy this warp started land before the CTA can exit.
+    if (lane == 0) {
+        for (int s = 0; s < kBStages; s++)
+            if (issued > (uint32_t)s) {
+                uint32_t fills = (issued - 1 - s) / kBStages + 1;
+                mbar_wait_bounded(&P.full[s], (fills - 1) & 1u, kBPolls);
+            }
+    }
+    __syncwarp();
+}
+
+// Consumer warps of the big-list phase.
+__device__ void bdec_consume(const BatchDecArgs &a, BPipe &P, uint16_t *s_qoff,
+                             uint32_t *s_warp)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t carry = 0;  // running differential sum of the current list
+    for (uint32_t g = 0;; g++) {
+        const int s = g % kBStages;
+        if (!mbar_wait_bounded(&P.full[s], (g / kBStages) & 1u, kBPolls)) {
+            raise_error(a.hdr, kErrTimeout);
+            break;
+        }
+        const uint32_t li = P.list[s];
+        if (li == kNoList)
+            break;
+        const svb_list L = a.lists[li];
+        const uint32_t k = P.tile[s];
+        const uint32_t nql = (L.n + 3) / 4;
+        const uint32_t last_nints = L.n - 4 * (nql - 1);
+        const uint32_t q0 = k * kBQuads;
+        const uint32_t nq = min((uint32_t)kBQuads, nql - q0);
+        const bool full = nq == kBQuads && (q0 + kBQuads < nql || last_nints == 4);
+        const bool skip = P.skip[s] != 0;
+        if (k == 0)
+            carry = L.prev;
+        const uint8_t *C = P.ctrl[s] + P.hc[s];
+        const uint8_t *D = P.data[s];
+        const uint32_t h = P.hd[s];
+
+        uint32_t w = 0;
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            if (4u * tid + j < nq)
+                w |= (uint32_t)C[4 * tid + j] << (8 * j);
+        uint32_t cnt[4], tsum = 0;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            uint32_t lq = 4u * tid + j;
+            uint32_t c = (w >> (8 * j)) & 0xffu;
+            uint32_t nints = 4;
+            if (q0 + lq == nql - 1 && last_nints < 4) {
+                nints = last_nints;
+                c &= (1u << (2 * nints)) - 1u;
+            }
+            cnt[j] = lq < nq ? quad_count(c, nints) : 0u;
+            tsum += cnt[j];
+        }
+        uint32_t incl = warp_incl_scan(tsum);
+        if (lane == 31)
+            s_warp[warp] = incl;
+        named_sync(1, kThreads);
+        uint32_t wpre = 0;
+#pragma unroll
+        for (int j = 0; j < kWarps; j++)
+            wpre += j < warp ? s_warp[j] : 0u;
+        {
+            const uint32_t o0 = h + wpre + incl - tsum;
+            const uint32_t o1 = o0 + cnt[0], o2 = o1 + cnt[1], o3 = o2 + cnt[2];
+            reinterpret_cast<uint2 *>(s_qoff)[tid] = make_uint2(o0 | (o1 << 16), o2 | (o3 << 16));
+        }
+        named_sync(1, kThreads);
+
+        const uint32_t lq0 = warp * (32 * kBRounds) + lane;
+        uint32_t *op = a.out + L.out_off + 4 * (u64)(q0 + lq0);
+        const bool aligned = ((uintptr_t)(a.out + L.out_off) & 15u) == 0;
+        uint32_t v[kBRounds][4];
+#pragma unroll
+        for (int r = 0; r < kBRounds; r++) {
+            const uint32_t lq = lq0 + r * 32;
+            const bool valid = lq < nq;
+            uint32_t c = valid ? C[lq] : 0u;
+            const uint32_t nints = !valid ? 0u : (q0 + lq == nql - 1 ? last_nints : 4u);
+            if (nints < 4)
+                c &= (1u << (2 * nints)) - 1u;
+            const uint32_t p = valid ? s_qoff[lq] : h;
+            uint4 x;
+            if (full && __all_sync(0xffffffffu, c == 0))
+                x = widen_quad(D, p);
+            else
+                x = decode_quad(D, p, c);
+            v[r][0] = nints > 0 ? x.x : 0u;
+            v[r][1] = nints > 1 ? x.y : 0u;
+            v[r][2] = nints > 2 ? x.z : 0u;
+            v[r][3] = nints > 3 ? x.w : 0u;
+        }
+        __syncwarp();
+        if (lane == 0)
+            mbar_arrive(&P.empty[s]);
+
+        if (a.delta) {
+            uint32_t qexcl[kBRounds], wrun = 0;
+#pragma unroll
+            for (int r = 0; r < kBRounds; r++) {
+                v[r][1] += v[r][0];
+                v[r][2] += v[r][1];
+                v[r][3] += v[r][2];
+                uint32_t qs = v[r][3];
+                uint32_t inc = warp_incl_scan(qs);
+                qexcl[r] = wrun + inc - qs;
+                wrun += __shfl_sync(0xffffffffu, inc, 31);
+            }
+            named_sync(1, kThreads);
+            if (lane == 0)
+                s_warp[warp] = wrun;
+            named_sync(1, kThreads);
+            uint32_t bpre = carry, vagg = 0;
+#pragma unroll
+            for (int j = 0; j < kWarps; j++) {
+                uint32_t t = s_warp[j];
+                bpre += j < warp ? t : 0u;
+                vagg += t;
+            }
+            carry += vagg;
+#pragma unroll
+            for (int r = 0; r < kBRounds; r++) {
+                const uint32_t add = bpre + qexcl[r];
+#pragma unroll
+                for (int j = 0; j < 4; j++)
+                    v[r][j] += add;
+            }
+        }
+        if (skip)
+            continue;
+#pragma unroll
+        for (int r = 0; r < kBRounds; r++) {
+            const uint32_t lq = lq0 + r * 32;
+            if (lq >= nq)
+                continue;
+            const uint32_t nints = q0 + lq == nql - 1 ? last_nints : 4u;
+            uint32_t *dst = op + 128 * r;
+            if (nints == 4 && aligned) {
+                stg_stream128(dst, make_uint4(v[r][0], v[r][1], v[r][2], v[r][3]));
+            } else {
+                dst[0] = v[r][0];
+                if (nints > 1)
+                    dst[1] = v[r][1];
+                if (nints > 2)
+                    dst[2] = v[r][2];
+                if (nints > 3)
+                    dst[3] = v[r][3];
+            }
+        }
+    }
+}
+
+// One small list, decoded by one warp straight from global memory.
+__device__ void bdec_small(const BatchDecArgs &a, uint32_t li, int lane)
+{
+    const svb_list L = a.lists[li];
+    const uint32_t n = L.n, nq = (n + 3) / 4;
+    const uint8_t *base = a.in + L.in_off;
+    if (nq > L.in_len) {
+        if (lane == 0)
+            raise_error(a.hdr, kErrTruncated);
+        return;
+    }
+    const uint8_t *data = base + nq;
+    const u64 dcap = L.in_len - nq;  // data bytes the stream may use
+    u64 running = 0;
+    uint32_t carry = L.prev;
+    for (uint32_t q0 = 0; q0 < nq; q0 += 32) {
+        const uint32_t q = q0 + lane;
+        const bool valid = q < nq;
+        uint32_t c = valid ? __ldg(base + q) : 0u;
+        const uint32_t nints = !valid ? 0u : (q == nq - 1 ? n - 4 * q : 4u);
+        if (nints < 4)
+            c &= (1u << (2 * nints)) - 1u;
+        const uint32_t C = valid ? quad_count(c, nints) : 0u;
+        const uint32_t incl = warp_incl_scan(C);
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        if (running + total > dcap) {
+            if (lane == 0)
+                raise_error(a.hdr, kErrTruncated);
+            return;
+        }
+        const uint8_t *p = data + running + (incl - C);
+        uint32_t x[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            if ((uint32_t)j < nints) {
+                const uint32_t code = (c >> (2 * j)) & 3u;
+                uint32_t val = 0;
+#pragma unroll
+                for (uint32_t b = 0; b < 4; b++)
+                    if (b <= code)
+                        val |= (uint32_t)__ldg(p + b) << (8 * b);
+                x[j] = val;
+                p += code + 1;
+            }
+        }
+        if (a.delta) {
+            x[1] += x[0];
+            x[2] += x[1];
+            x[3] += x[2];
+            const uint32_t qi = warp_incl_scan(x[3]);
+            const uint32_t add = carry + qi - x[3];
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                x[j] += add;
+            carry += __shfl_sync(0xffffffffu, qi, 31);
+        }
+        uint32_t *dst = a.out + L.out_off + 4 * (u64)q;
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            if ((uint32_t)j < nints)
+                dst[j] = x[j];
+        running += total;
+    }
+    if (lane == 0)
+        atomicAdd(&a.hdr->total, (u64)nq + running);
+}
+
+__global__ void __launch_bounds__(kBBlock, 3) batch_decode_kernel(BatchDecArgs a)
+{
+    extern __shared__ __align__(128) uint8_t dyn_smem[];
+    BPipe &P = *reinterpret_cast<BPipe *>(dyn_smem);
+    __shared__ __align__(16) uint16_t s_qoff[kBQuads];
+    __shared__ uint32_t s_warp[kWarps];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        for (int s = 0; s < kBStages; s++) {
+            mbar_init(&P.full[s], 32);
+            mbar_init(&P.cfull[s], 32);
+            mbar_init(&P.empty[s], kWarps);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (warp == kWarps)
+        bdec_produce(a, P, lane);
+    else
+        bdec_consume(a, P, s_qoff, s_warp);
+
+    // Small lists: every warp takes them one by one.
+    const uint32_t *small = plan_small(a.plan);
+    const uint32_t nsmall = a.plan->nsmall;
+    for (;;) {
+        uint32_t j = 0;
+        if (lane == 0)
+            j = (uint32_t)atomicAdd(&a.hdr->a_counter, 1ull);
+        j = __shfl_sync(0xffffffffu, j, 0);
+        if (j >= nsmall)
+            break;
+        bdec_small(a, small[j], lane);
+    }
+    finish_launch(a.hdr, a.result);
+}
+
+// ---------------------------------------------------------------------------
+// Encode
+
+struct BatchEncArgs {
+    const svb_list *lists;
+    const PlanHeader *plan;
+    const uint32_t *in;
+    uint8_t *out;
+    u64 *sizes;
+    WsHeader *hdr;
+    DeviceResult *result;
+    uint32_t delta;
+};
+
+constexpr int kEStages = 3;
+constexpr int kEStageBytes = 16 * kBQuads + 16;  // 4096 values + 16-byte phase
+constexpr int kEOutBytes = 16 * kBQuads + 32;
+
+struct EPipe {
+    uint8_t vals[kEStages][kEStageBytes];
+    uint8_t outb[kEOutBytes];
+    uint64_t full[kEStages];
+    uint64_t empty[kEStages];
+    uint32_t list[kEStages];
+    uint32_t tile[kEStages];
+    uint32_t hv[kEStages];  // phase (mod 16) of the staged values
+};
+
+__device__ void benc_produce(const BatchEncArgs &a, EPipe &P, int lane)
+{
+    const PlanHeader *plan = a.plan;
+    const uint32_t *big = plan_big(plan);
+    uint32_t issued = 0, li = kNoList, k = 0, ntl = 0;
+    svb_list L = {};
+    auto claim = [&]() -> bool {
+        uint32_t j = 0;
+        if (lane == 0)
+            j = (uint32_t)atomicAdd(&a.hdr->tile_counter, 1ull);
+        j = __shfl_sync(0xffffffffu, j, 0);
+        if (j >= plan->nbig)
+            return false;
+        li = big[j];
+        L = a.lists[li];
+        ntl = (L.n + 4 * kBQuads - 1) / (4 * kBQuads);
+        k = 0;
+        return true;
+    };
+    bool have = claim();
+    for (uint32_t g = 0;; g++) {
+        const int s = g % kEStages;
+        if (g >= (uint32_t)kEStages) {
+            bool ok = mbar_wait_bounded(&P.empty[s], ((g / kEStages) - 1) & 1u, kBPolls);
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0)
+                    raise_error(a.hdr, kErrTimeout);
+                issued = g;
+                break;
+            }
+        }
+        if (!have) {
+            if (lane == 0) {
+                P.list[s] = kNoList;
+                mbar_arrive_expect_tx(&P.full[s], 0);
+            } else {
+                mbar_arrive(&P.full[s]);
+            }
+            issued = g + 1;
+            break;
+        }
+        const u64 i0 = (u64)k * 4 * kBQuads;
+        const uint32_t cnt = (uint32_t)min((u64)4 * kBQuads, (u64)L.n - i0);
+        const uint8_t *gv = reinterpret_cast<const uint8_t *>(a.in + L.in_off + i0);
+        range_edges(gv, 4 * cnt, P.vals[s], lane);
+        if (lane == 0) {
+            const uint8_t *av;
+            uint32_t ov;
+            uint32_t bv = range_interior(gv, 4 * cnt, av, ov);
+            P.list[s] = li;
+            P.tile[s] = k;
+            P.hv[s] = (uint32_t)((uintptr_t)gv & 15u);
+            mbar_arrive_expect_tx(&P.full[s], bv);
+            if (bv)
+                bulk_g2s(P.vals[s] + ov, av, bv, &P.full[s]);
+        } else {
+            mbar_arrive(&P.full[s]);
+        }
+        if (++k == ntl)
+            have = claim();
+        issued = g + 1;
+    }
+    if (lane == 0) {
+        for (int s = 0; s < kEStages; s++)
+            if (issued > (uint32_t)s) {
+                uint32_t fills = (issued - 1 - s) / kEStages + 1;
+                mbar_wait_bounded(&P.full[s], (fills - 1) & 1u, kBPolls);
+            }
+    }
+    __syncwarp();
+}
+
+__device__ void benc_consume(const BatchEncArgs &a, EPipe &P, uint32_t *s_warp, uint32_t *s_last)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    u64 run = 0;          // data bytes of the current list written so far
+    uint32_t before = 0;  // last value of the previous tile (differential)
+    for (uint32_t g = 0;; g++) {
+        const int s = g % kEStages;
+        if (!mbar_wait_bounded(&P.full[s], (g / kEStages) & 1u, kBPolls)) {
+            raise_error(a.hdr, kErrTimeout);
+            break;
+        }
+        const uint32_t li = P.list[s];
+        if (li == kNoList)
+            break;
+        const svb_list L = a.lists[li];
+        const uint32_t k = P.tile[s];
+        const uint32_t nql = (L.n + 3) / 4;
+        const uint32_t last_nints = L.n - 4 * (nql - 1);
+        const uint32_t q0 = k * kBQuads;
+        const uint32_t nq = min((uint32_t)kBQuads, nql - q0);
+        if (k == 0) {
+            run = 0;
+            before = L.prev;
+        }
+        const uint32_t *V = reinterpret_cast<const uint32_t *>(P.vals[s] + P.hv[s]);
+
+        // Values -> gaps -> lengths -> control bytes, one quad per lane per round.
+        uint32_t d[kBRounds][4], ctrl[kBRounds], qexcl[kBRounds], wrun = 0;
+        const uint32_t lq0 = warp * (32 * kBRounds) + lane;
+#pragma unroll
+        for (int r = 0; r < kBRounds; r++) {
+            const uint32_t lq = lq0 + r * 32;
+            const uint32_t nints = lq >= nq ? 0u : (q0 + lq == nql - 1 ? last_nints : 4u);
+            uint32_t x[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                x[j] = (uint32_t)j < nints ? V[4 * lq + j] : 0u;
+            if (a.delta) {
+                const uint32_t pv = lq == 0 ? before : (nints ? V[4 * lq - 1] : 0u);
+                d[r][0] = x[0] - pv;
+                d[r][1] = x[1] - x[0];
+                d[r][2] = x[2] - x[1];
+                d[r][3] = x[3] - x[2];
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; j++)
+                    d[r][j] = x[j];
+            }
+            uint32_t c = 0, C = 0;
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                if ((uint32_t)j < nints) {
+                    const uint32_t Lb = byte_len(d[r][j]);
+                    c |= (Lb - 1) << (2 * j);
+                    C += Lb;
+                }
+            ctrl[r] = c;
+            if (nints)
+                a.out[L.out_off + q0 + lq] = (uint8_t)c;
+            const uint32_t inc = warp_incl_scan(C);
+            qexcl[r] = wrun + inc - C;
+            wrun += __shfl_sync(0xffffffffu, inc, 31);
+        }
+        if (tid == kThreads - 1)
+            *s_last = nq ? V[4 * nq - 1 - (q0 + nq == nql ? 4 - last_nints : 0)] : before;
+        if (lane == 0)
+            s_warp[warp] = wrun;
+        named_sync(1, kThreads);
+        uint32_t bpre = 0, agg = 0;
+#pragma unroll
+        for (int j = 0; j < kWarps; j++) {
+            const uint32_t t = s_warp[j];
+            bpre += j < warp ? t : 0u;
+            agg += t;
+        }
+        before = *s_last;
+        __syncwarp();
+        if (lane == 0)
+            mbar_arrive(&P.empty[s]);
+
+        // Assemble the tile's data bytes aligned like their destination.
+        uint8_t *dst = a.out + L.out_off + nql + run;
+        const uint32_t h = (uint32_t)((uintptr_t)dst & 15u);
+#pragma unroll
+        for (int r = 0; r < kBRounds; r++) {
+            const uint32_t lq = lq0 + r * 32;
+            const uint32_t nints = lq >= nq ? 0u : (q0 + lq == nql - 1 ? last_nints : 4u);
+            uint32_t p = h + bpre + qexcl[r];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                if ((uint32_t)j < nints) {
+                    const uint32_t code = (ctrl[r] >> (2 * j)) & 3u;
+#pragma unroll
+                    for (uint32_t b = 0; b < 4; b++)
+                        if (b <= code)
+                            P.outb[p + b] = (uint8_t)(d[r][j] >> (8 * b));
+                    p += code + 1;
+                }
+            }
+        }
+        named_sync(1, kThreads);
+        uint8_t *adst = dst - h;
+        const uint32_t nchunks = (h + agg + 15u) >> 4;
+        for (uint32_t c = tid; c < nchunks; c += kThreads) {
+            if (16u * c >= h && 16u * c + 16u <= h + agg) {
+                stg_stream128(adst + 16u * c, *reinterpret_cast<const uint4 *>(P.outb + 16u * c));
+            } else {
+                for (uint32_t b = 0; b < 16; b++) {
+                    const uint32_t idx = 16u * c + b;
+                    if (idx >= h && idx < h + agg)
+                        adst[idx] = P.outb[idx];
+                }
+            }
+        }
+        run += agg;
+        if (q0 + nq == nql && tid == 0) {
+            a.sizes[li] = nql + run;
+            atomicAdd(&a.hdr->total, (u64)nql + run);
+        }
+        named_sync(1, kThreads);  // P.outb and s_warp free again
+    }
+}
+
+// One small list, encoded by one warp straight from global memory.
+__device__ void benc_small(const BatchEncArgs &a, uint32_t li, int lane)
+{
+    const svb_list L = a.lists[li];
+    const uint32_t n = L.n, nq = (n + 3) / 4;
+    const uint32_t *src = a.in + L.in_off;
+    uint8_t *ctrl = a.out + L.out_off;
+    uint8_t *data = ctrl + nq;
+    u64 running = 0;
+    uint32_t before = L.prev;
+    for (uint32_t q0 = 0; q0 < nq; q0 += 32) {
+        const uint32_t q = q0 + lane;
+        const uint32_t nints = q >= nq ? 0u : (q == nq - 1 ? n - 4 * q : 4u);
+        uint32_t x[4] = {0, 0, 0, 0}, d[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            if ((uint32_t)j < nints)
+                x[j] = __ldg(src + 4 * q + j);
+        if (a.delta) {
+            uint32_t pv = __shfl_up_sync(0xffffffffu, x[3], 1);
+            if (lane == 0)
+                pv = before;
+            d[0] = x[0] - pv;
+            d[1] = x[1] - x[0];
+            d[2] = x[2] - x[1];
+            d[3] = x[3] - x[2];
+            before = __shfl_sync(0xffffffffu, x[3], 31);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                d[j] = x[j];
+        }
+        uint32_t c = 0, C = 0;
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            if ((uint32_t)j < nints) {
+                const uint32_t Lb = byte_len(d[j]);
+                c |= (Lb - 1) << (2 * j);
+                C += Lb;
+            }
+        if (nints)
+            ctrl[q] = (uint8_t)c;
+        const uint32_t incl = warp_incl_scan(C);
+        uint8_t *p = data + running + (incl - C);
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            if ((uint32_t)j < nints) {
+                const uint32_t code = (c >> (2 * j)) & 3u;
+#pragma unroll
+                for (uint32_t b = 0; b < 4; b++)
+                    if (b <= code)
+                        p[b] = (uint8_t)(d[j] >> (8 * b));
+                p += code + 1;
+            }
+        }
+        running += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (lane == 0) {
+        a.sizes[li] = nq + running;
+        atomicAdd(&a.hdr->total, (u64)nq + running);
+    }
+}
+
+__global__ void __launch_bounds__(kBBlock, 3) batch_encode_kernel(BatchEncArgs a)
+{
+    extern __shared__ __align__(128) uint8_t dyn_smem[];
+    EPipe &P = *reinterpret_cast<EPipe *>(dyn_smem);
+    __shared__ uint32_t s_warp[kWarps];
+    __shared__ uint32_t s_last;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        for (int s = 0; s < kEStages; s++) {
+            mbar_init(&P.full[s], 32);
+            mbar_init(&P.empty[s], kWarps);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (warp == kWarps)
+        benc_produce(a, P, lane);
+    else
+        benc_consume(a, P, s_warp, &s_last);
+
+    const uint32_t *small = plan_small(a.plan);
+    const uint32_t nsmall = a.plan->nsmall;
+    for (;;) {
+        uint32_t j = 0;
+        if (lane == 0)
+            j = (uint32_t)atomicAdd(&a.hdr->a_counter, 1ull);
+        j = __shfl_sync(0xffffffffu, j, 0);
+        if (j >= nsmall)
+            break;
+        benc_small(a, small[j], lane);
+    }
+    finish_launch(a.hdr, a.result);
+}
+
+// ---------------------------------------------------------------------------
+
+template <class K>
+static int persistent_grid(K kernel, size_t smem)
+{
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kBBlock, smem);
+    return (sms > 0 ? sms : 148) * (occ > 0 ? occ : 1);
+}
+
+int launch_batch_decode(const void *d_plan, const svb_list *d_lists, const uint8_t *in,
+                        uint32_t *out, bool delta, void *ws, DeviceResult *result,
+                        cudaStream_t stream, int grid)
+{
+    static int g = 0;
+    if (!g)
+        g = persistent_grid(batch_decode_kernel, sizeof(BPipe));
+    BatchDecArgs a;
+    a.lists = d_lists;
+    a.plan = static_cast<const PlanHeader *>(d_plan);
+    a.in = in;
+    a.out = out;
+    a.hdr = static_cast<WsHeader *>(ws);
+    a.result = result;
+    a.delta = delta ? 1u : 0u;
+    batch_decode_kernel<<<grid > 0 ? grid : g, kBBlock, sizeof(BPipe), stream>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+int launch_batch_encode(const void *d_plan, const svb_list *d_lists, const uint32_t *in,
+                        uint8_t *out, u64 *sizes, bool delta, void *ws, DeviceResult *result,
+                        cudaStream_t stream, int grid)
+{
+    static int g = 0;
+    if (!g)
+        g = persistent_grid(batch_encode_kernel, sizeof(EPipe));
+    BatchEncArgs a;
+    a.lists = d_lists;
+    a.plan = static_cast<const PlanHeader *>(d_plan);
+    a.in = in;
+    a.out = out;
+    a.sizes = sizes;
+    a.hdr = static_cast<WsHeader *>(ws);
+    a.result = result;
+    a.delta = delta ? 1u : 0u;
+    batch_encode_kernel<<<grid > 0 ? grid : g, kBBlock, sizeof(EPipe), stream>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+size_t batch_plan_bytes(size_t num_lists)
+{
+    return sizeof(PlanHeader) + 4 * num_lists;
+}
+
+int build_batch_plan(const svb_list *h_lists, size_t num_lists, uint32_t threshold, void *d_plan,
+                     cudaStream_t stream)
+{
+    if (threshold == 0)
+        threshold = kDefaultBigThreshold;
+    std::vector<uint32_t> big, small;
+    for (size_t j = 0; j < num_lists; j++) {
+        if (h_lists[j].n == 0)
+            continue;
+        (h_lists[j].n >= threshold ? big : small).push_back((uint32_t)j);
+    }
+    // Longest first, so that the last lists handed out are the shortest.
+    auto longer = [&](uint32_t x, uint32_t y) {
+        return h_lists[x].n != h_lists[y].n ? h_lists[x].n > h_lists[y].n : x < y;
+    };
+    std::sort(big.begin(), big.end(), longer);
+    std::sort(small.begin(), small.end(), longer);
+    std::vector<uint32_t> buf(4 + big.size() + small.size());
+    buf[0] = (uint32_t)big.size();
+    buf[1] = (uint32_t)small.size();
+    buf[2] = threshold;
+    buf[3] = 0;
+    std::copy(big.begin(), big.end(), buf.begin() + 4);
+    std::copy(small.begin(), small.end(), buf.begin() + 4 + big.size());
+    // Pageable source: the copy is staged before this call returns.
+    return cudaMemcpyAsync(d_plan, buf.data(), buf.size() * 4, cudaMemcpyHostToDevice, stream) ==
+                   cudaSuccess
+               ? 0
+               : 3;
+}
+
+}  // namespace svb

@@ -279,6 +279,8 @@ __device__ __forceinline__ void finish_launch(WsHeader *hdr, DeviceResult *resul
             st_relaxed(&hdr->total, 0);
             st_relaxed(&hdr->tile_counter, 0);
             st_relaxed(&hdr->done_counter, 0);
+            st_relaxed(&hdr->a_counter, 0);
+            st_relaxed(&hdr->a_done, 0);
             st_relaxed(&hdr->epoch, ld_relaxed(&hdr->epoch) + 1);
         }
     }

@@ -5,6 +5,8 @@
 
 #include <cstdint>
 
+#include "svb.h"
+
 namespace svb {
 
 typedef unsigned long long u64;
@@ -25,6 +27,17 @@ int launch_decode_tiled(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, uin
 int launch_encode(const uint32_t *in, u64 n, uint8_t *out, uint32_t prev, bool delta, void *ws,
                   DeviceResult *result, cudaStream_t stream, u64 spin_limit);
 u64 encode_tiles(u64 n);
+
+// Batched codec (svb_batch.cu).
+int launch_batch_decode(const void *d_plan, const svb_list *d_lists, const uint8_t *in,
+                        uint32_t *out, bool delta, void *ws, DeviceResult *result,
+                        cudaStream_t stream, int grid);
+int launch_batch_encode(const void *d_plan, const svb_list *d_lists, const uint32_t *in,
+                        uint8_t *out, u64 *sizes, bool delta, void *ws, DeviceResult *result,
+                        cudaStream_t stream, int grid);
+size_t batch_plan_bytes(size_t num_lists);
+int build_batch_plan(const svb_list *h_lists, size_t num_lists, uint32_t threshold, void *d_plan,
+                     cudaStream_t stream);
 
 // Record the calling thread's status for svb_last_error().
 void set_last_error(int code);

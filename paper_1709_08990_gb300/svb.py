@@ -62,6 +62,11 @@ def lib() -> ctypes.CDLL:
             "svb_decode_async": ([vp, sz, sz, vp, u32, i32, vp, vp, sz, vp], i32),
             "svb_testhook_lookback_timeout": ([vp, sz, vp, u64, vp, vp, sz, vp], i32),
             "svb_decode_noalloc": ([vp, sz, sz, vp, u32, i32, vp], sz),
+            "svb_batch_plan_bytes": ([sz], sz),
+            "svb_batch_plan": ([vp, sz, u32, vp, sz, vp], i32),
+            "svb_batch_workspace_size": ([], sz),
+            "svb_batch_decode": ([vp, vp, vp, vp, i32, vp, vp, sz, i32, vp], i32),
+            "svb_batch_encode": ([vp, vp, vp, vp, i32, vp, vp, vp, sz, i32, vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -181,6 +186,40 @@ def svb_encode_async(inp, n, out, prev, delta, d_result, ws, ws_bytes, stream=No
 def svb_decode_async(inp, in_len, n, out, prev, delta, d_result, ws, ws_bytes, stream=None) -> int:
     return lib().svb_decode_async(_p(inp), in_len, n, _p(out), prev & 0xFFFFFFFF, int(delta),
                                   _p(d_result), _p(ws), ws_bytes, _stream(stream))
+
+
+# numpy layout of struct svb_list (32 bytes)
+def list_dtype():
+    import numpy as np
+    return np.dtype([("in_off", "<u8"), ("in_len", "<u8"), ("out_off", "<u8"),
+                     ("n", "<u4"), ("prev", "<u4")])
+
+
+def svb_batch_plan_bytes(num_lists: int) -> int:
+    return lib().svb_batch_plan_bytes(num_lists)
+
+
+def svb_batch_plan(h_lists, num_lists: int, big_threshold: int, d_plan, plan_bytes: int,
+                   stream=None) -> int:
+    return lib().svb_batch_plan(_p(h_lists), num_lists, big_threshold, _p(d_plan), plan_bytes,
+                                _stream(stream))
+
+
+def svb_batch_workspace_size() -> int:
+    return lib().svb_batch_workspace_size()
+
+
+def svb_batch_decode(d_plan, d_lists, in_base, out_base, delta, d_result, ws, ws_bytes,
+                     grid: int = 0, stream=None) -> int:
+    return lib().svb_batch_decode(_p(d_plan), _p(d_lists), _p(in_base), _p(out_base), int(delta),
+                                  _p(d_result), _p(ws), ws_bytes, grid, _stream(stream))
+
+
+def svb_batch_encode(d_plan, d_lists, in_base, out_base, delta, d_sizes, d_result, ws, ws_bytes,
+                     grid: int = 0, stream=None) -> int:
+    return lib().svb_batch_encode(_p(d_plan), _p(d_lists), _p(in_base), _p(out_base), int(delta),
+                                  _p(d_sizes), _p(d_result), _p(ws), ws_bytes, grid,
+                                  _stream(stream))
 
 
 SVB_NOALLOC_MAX_N = 1 << 24

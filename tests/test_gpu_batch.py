@@ -1,0 +1,193 @@
+"""Batched codec against the oracle, list by list, bit for bit.
+
+Lists of very uneven lengths (1 .. ~10^5 integers, most not multiples of 4)
+go through one persistent launch; each list is checked against the oracle's
+stream or values for that list alone.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1709_08990_gb300 import svb
+from paper_1709_08990_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def to_dev(a: np.ndarray):
+    if a.dtype == np.uint32:
+        a = a.view(np.int32)
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+class Batch:
+    """Values, oracle streams and list tables of one batch."""
+
+    def __init__(self, lengths, delta: bool, seed: int = 7, prevs=None, gap_bytes: int = 0):
+        self.delta = delta
+        self.lengths = np.asarray(lengths, dtype=np.uint32)
+        k = self.lengths.size
+        rng = np.random.default_rng(seed)
+        self.prevs = (np.zeros(k, dtype=np.uint32) if prevs is None
+                      else np.asarray(prevs, dtype=np.uint32))
+        self.values = []
+        for j, m in enumerate(self.lengths):
+            if delta:
+                v = W.posting_list(seed, 1000 * j, int(m)) if m else np.zeros(0, np.uint32)
+            else:
+                v = W.uniform_lengths(seed * 1000 + j, int(m))
+            self.values.append(v)
+        self.streams = [oracle.encode(v, prev=int(p), delta=delta)
+                        for v, p in zip(self.values, self.prevs)]
+        # Streams back to back (with optional junk bytes between them).
+        dt = svb.list_dtype()
+        self.dec_lists = np.zeros(k, dtype=dt)
+        self.enc_lists = np.zeros(k, dtype=dt)
+        pos, opos, ipos = 0, 0, 0
+        chunks = []
+        for j in range(k):
+            s = self.streams[j]
+            self.dec_lists[j] = (pos, s.size, opos, self.lengths[j], self.prevs[j])
+            self.enc_lists[j] = (ipos, 0, opos_enc(j, self.lengths), self.lengths[j], self.prevs[j])
+            chunks.append(s)
+            pad = rng.integers(0, 256, gap_bytes, dtype=np.uint8)
+            chunks.append(pad)
+            pos += s.size + gap_bytes
+            opos += int(self.lengths[j])
+            ipos += int(self.lengths[j])
+        self.pool = np.concatenate(chunks) if chunks else np.zeros(0, np.uint8)
+        self.total_ints = int(self.lengths.sum())
+        self.all_values = (np.concatenate(self.values) if self.values
+                           else np.zeros(0, np.uint32))
+
+
+def opos_enc(j, lengths):
+    return int(sum(svb.svb_max_compressed_size(int(m)) for m in lengths[:j]))
+
+
+def run_plan(h_lists, threshold):
+    nbytes = svb.svb_batch_plan_bytes(len(h_lists))
+    d_plan = torch.empty(nbytes, dtype=torch.uint8, device=DEV)
+    assert svb.svb_batch_plan(h_lists, len(h_lists), threshold, d_plan, nbytes) == 0
+    return d_plan
+
+
+def workspace():
+    nb = svb.svb_batch_workspace_size()
+    ws = torch.empty(nb, dtype=torch.uint8, device=DEV)
+    assert svb.svb_workspace_init(ws, nb) == 0
+    return ws, nb
+
+
+def batch_decode(b: Batch, threshold=0, grid=0):
+    d_plan = run_plan(b.dec_lists, threshold)
+    d_lists = to_dev(b.dec_lists.view(np.uint8))
+    d_in = to_dev(b.pool) if b.pool.size else torch.zeros(1, dtype=torch.uint8, device=DEV)
+    d_out = torch.full((max(1, b.total_ints),), -7, dtype=torch.int32, device=DEV)
+    ws, nb = workspace()
+    res = torch.zeros(2, dtype=torch.int64, device=DEV)
+    assert svb.svb_batch_decode(d_plan, d_lists, d_in, d_out, int(b.delta), res, ws, nb, grid) == 0
+    r = res.cpu().numpy()
+    return d_out[: b.total_ints].cpu().numpy().view(np.uint32), r
+
+
+def batch_encode(b: Batch, threshold=0, grid=0):
+    d_plan = run_plan(b.enc_lists, threshold)
+    d_lists = to_dev(b.enc_lists.view(np.uint8))
+    d_in = to_dev(b.all_values) if b.total_ints else torch.zeros(1, dtype=torch.int32, device=DEV)
+    cap = opos_enc(len(b.lengths), b.lengths)
+    d_out = torch.zeros(max(1, cap), dtype=torch.uint8, device=DEV)
+    d_sizes = torch.zeros(max(1, len(b.lengths)), dtype=torch.int64, device=DEV)
+    ws, nb = workspace()
+    res = torch.zeros(2, dtype=torch.int64, device=DEV)
+    assert svb.svb_batch_encode(d_plan, d_lists, d_in, d_out, int(b.delta), d_sizes, res, ws, nb,
+                                grid) == 0
+    return d_out.cpu().numpy(), d_sizes.cpu().numpy(), res.cpu().numpy()
+
+
+LENGTHS = [1, 2, 3, 4, 5, 7, 8, 9, 31, 100, 127, 128, 129, 1000, 2047, 4095, 4096, 4097,
+           8191, 8192, 8193, 12289, 20000, 50001, 0, 6]
+
+
+@pytest.mark.parametrize("delta", [False, True])
+@pytest.mark.parametrize("threshold", [0, 16, 1 << 30])
+def test_batch_decode_matches_oracle(delta, threshold):
+    b = Batch(LENGTHS, delta, seed=3, prevs=[(97 * j) & 0xFFFF for j in range(len(LENGTHS))],
+              gap_bytes=5)
+    got, r = batch_decode(b, threshold)
+    assert r[1] == 0
+    assert r[0] == sum(s.size for s in b.streams)
+    assert np.array_equal(got, b.all_values)
+
+
+@pytest.mark.parametrize("delta", [False, True])
+@pytest.mark.parametrize("threshold", [0, 16, 1 << 30])
+def test_batch_encode_matches_oracle(delta, threshold):
+    b = Batch(LENGTHS, delta, seed=4, prevs=[(31 * j) & 0xFFFF for j in range(len(LENGTHS))])
+    out, sizes, r = batch_encode(b, threshold)
+    assert r[1] == 0
+    assert r[0] == sum(s.size for s in b.streams)
+    for j, s in enumerate(b.streams):
+        off = int(b.enc_lists[j]["out_off"])
+        assert sizes[j] == s.size or (s.size == 0 and b.lengths[j] == 0)
+        assert np.array_equal(out[off:off + s.size], s), f"list {j} (n={b.lengths[j]})"
+
+
+@pytest.mark.parametrize("grid", [1, 3])
+def test_batch_small_grids(grid):
+    b = Batch([5000, 9000, 17, 40000, 3], True, seed=9)
+    got, r = batch_decode(b, 1024, grid)
+    assert r[1] == 0 and np.array_equal(got, b.all_values)
+    out, sizes, r = batch_encode(b, 1024, grid)
+    assert r[1] == 0
+    for j, s in enumerate(b.streams):
+        off = int(b.enc_lists[j]["out_off"])
+        assert np.array_equal(out[off:off + s.size], s)
+
+
+def test_batch_truncated_list_is_reported():
+    b = Batch([10000, 50, 9000], False, seed=5)
+    for j in (0, 1):
+        lists = b.dec_lists.copy()
+        lists[j]["in_len"] = b.streams[j].size - 1
+        b2 = b
+        saved = b2.dec_lists
+        b2.dec_lists = lists
+        got, r = batch_decode(b2, 1024)
+        b2.dec_lists = saved
+        assert r[1] == svb.SVB_ETRUNCATED
+        assert r[0] == -1
+    got, r = batch_decode(b, 1024)  # the workspace of a fresh call is fine
+    assert r[1] == 0 and np.array_equal(got, b.all_values)
+
+
+def test_batch_of_posting_lists_from_the_workload():
+    """2,000 lists of the lists_100k workload (lengths as drawn, start 0)."""
+    L = W.lists_lengths()[:2000]
+    b = Batch(L, True, seed=4)
+    got, r = batch_decode(b)
+    assert r[1] == 0 and np.array_equal(got, b.all_values)
+    out, sizes, r = batch_encode(b)
+    assert r[1] == 0
+    for j in range(0, 2000, 7):
+        off = int(b.enc_lists[j]["out_off"])
+        assert np.array_equal(out[off:off + b.streams[j].size], b.streams[j])
+
+
+def test_batch_is_repeatable_on_one_workspace():
+    b = Batch([3000, 70000, 12, 8192], True, seed=11)
+    d_plan = run_plan(b.dec_lists, 0)
+    d_lists = to_dev(b.dec_lists.view(np.uint8))
+    d_in = to_dev(b.pool)
+    ws, nb = workspace()
+    res = torch.zeros(2, dtype=torch.int64, device=DEV)
+    for _ in range(3):
+        d_out = torch.zeros(b.total_ints, dtype=torch.int32, device=DEV)
+        assert svb.svb_batch_decode(d_plan, d_lists, d_in, d_out, 1, res, ws, nb) == 0
+        assert res[1].item() == 0
+        assert np.array_equal(d_out.cpu().numpy().view(np.uint32), b.all_values)
