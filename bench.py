@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-lists", action="store_true", help="skip the batched-lists workload")
+    ap.add_argument("--list-count", type=int, default=100_000)
     return ap.parse_args()
 
 
@@ -344,6 +346,9 @@ def main():
         del h_x
         sec["delta_64m"] = time_codec(svb, W, "delta_64m", dev, peaks)
         sec["uniform_1m"] = time_codec(svb, W, "uniform_1m", dev, peaks)
+        if not args.no_lists:
+            torch.cuda.empty_cache()
+            sec["lists_100k"] = time_lists(svb, W, dev, peaks, args.list_count)
         line["secondary"] = sec
 
     if rank == 0:
@@ -416,6 +421,68 @@ def time_codec(svb, W, name, dev, peaks):
                        "frac": alg / (ms_d / 1e3) / 1e9 / hb},
             "encode": {"gints_per_s": n / ms_e / 1e6, "us": ms_e * 1e3,
                        "frac": alg / (ms_e / 1e3) / 1e9 / hb}}
+
+
+def time_lists(svb, W, dev, peaks, count: int):
+    """Batched delta decode/encode of the lists_100k workload (one persistent
+    launch, replayed from a CUDA graph) against one launch per list."""
+    import torch
+    from paper_1709_08990_gb300 import autotune
+    from paper_1709_08990_gb300.batch import ListPool
+    L = W.lists_lengths(count, cap=(1 << 30) * count // 100_000)
+    h_vals = torch.empty(int(L.sum()), dtype=torch.int32, pin_memory=True)
+    W.posting_lists(W.WORKLOADS["lists_100k"].seed, L, out=h_vals.numpy().view(np.uint32))
+    d_vals = h_vals.to(dev)
+    pool = ListPool(L, d_vals, delta=True, device=dev)
+    total = pool.total
+    d_out = torch.empty(total, dtype=torch.int32, device=dev)
+    tuned = autotune.tune_batch(pool, f"lists_{count}", d_out)
+    stream = torch.cuda.current_stream()
+    g = pool.graph(lambda: pool.decode(d_out))
+    ms_graph = _time(lambda: g.replay(), 20, stream)
+    ms_batch = _time(lambda: pool.decode(d_out), 20, stream)
+    r = pool.result()
+    ok = bool(r[1] == 0 and torch.equal(d_out, d_vals))
+    # One launch per list, every list once.
+    d_out2 = torch.zeros_like(d_out)
+    ws = pool.decode_per_list(d_out2, lists=range(min(64, pool.k)))
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    pool.decode_per_list(d_out2, ws=ws)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_per_list = a.elapsed_time(b)
+    ok_per_list = bool(torch.equal(d_out2, d_vals))
+    # Encode: batched vs per list.
+    d_enc = torch.empty(pool.pool_bytes, dtype=torch.uint8, device=dev)
+    ms_benc = _time(lambda: pool.encode(d_enc), 10, stream)
+    ok_enc = bool(torch.equal(d_enc, pool.pool))
+    a.record(stream)
+    pool.encode_per_list(d_enc, ws=ws)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_enc_per_list = a.elapsed_time(b)
+    alg = pool.pool_bytes + 4 * total
+    hb = peaks["hbm_gbs"]
+    out = {"lists": pool.k, "ints": total, "stream_bytes": pool.pool_bytes,
+           "min_len": int(L.min()), "max_len": int(L.max()),
+           "not_multiple_of_4": int((L % 4 != 0).sum()), "verified": ok and ok_per_list and ok_enc,
+           "tuned": {"threshold": tuned["threshold"], "grid": tuned["grid"],
+                     "cached": tuned["cached"]},
+           "decode_batched_graph": {"gints_per_s": total / ms_graph / 1e6, "ms": ms_graph,
+                                    "frac": alg / (ms_graph / 1e3) / 1e9 / hb},
+           "decode_batched_launch": {"gints_per_s": total / ms_batch / 1e6, "ms": ms_batch},
+           "decode_per_list": {"gints_per_s": total / ms_per_list / 1e6, "ms": ms_per_list},
+           "decode_speedup_vs_per_list": ms_per_list / ms_graph,
+           "encode_batched": {"gints_per_s": total / ms_benc / 1e6, "ms": ms_benc,
+                              "frac": alg / (ms_benc / 1e3) / 1e9 / hb},
+           "encode_per_list": {"gints_per_s": total / ms_enc_per_list / 1e6,
+                               "ms": ms_enc_per_list},
+           "encode_speedup_vs_per_list": ms_enc_per_list / ms_benc}
+    del pool, d_out, d_out2, d_enc, d_vals
+    torch.cuda.empty_cache()
+    return out
 
 
 if __name__ == "__main__":

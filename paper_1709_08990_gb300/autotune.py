@@ -1,0 +1,84 @@
+"""Autotuner for the batched codec's launch parameters.
+
+The batched kernels take two run-time choices: the list length from which a
+list gets a whole CTA instead of one warp (the plan's threshold), and the
+number of persistent CTAs.  tune_batch() times the batched decode of a
+ListPool over a small grid of both (CUDA events, best of a few runs) and
+caches the winner in a JSON file keyed by GPU name and workload, so later
+runs reuse it.  The cache path is SVB_AUTOTUNE_CACHE, else autotune_cache.json
+next to this file.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import torch
+
+CACHE = os.environ.get("SVB_AUTOTUNE_CACHE",
+                       os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                                    "autotune_cache.json"))
+
+
+def _key(op: str, workload: str) -> str:
+    name = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
+    return f"{name}|{workload}|{op}"
+
+
+def _load() -> dict:
+    try:
+        with open(CACHE) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def lookup(op: str, workload: str) -> dict | None:
+    return _load().get(_key(op, workload))
+
+
+def store(op: str, workload: str, entry: dict) -> None:
+    d = _load()
+    d[_key(op, workload)] = entry
+    tmp = CACHE + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(d, f, indent=1, sort_keys=True)
+    os.replace(tmp, CACHE)
+
+
+def _time_ms(fn, reps: int) -> float:
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(reps)]
+    fn()
+    torch.cuda.synchronize()
+    for a, b in ev:
+        a.record()
+        fn()
+        b.record()
+    torch.cuda.synchronize()
+    return min(a.elapsed_time(b) for a, b in ev)
+
+
+def tune_batch(pool, workload: str, d_out: torch.Tensor,
+               thresholds=(2048, 4096, 8192, 16384, 65536), grids=None, reps: int = 3,
+               force: bool = False) -> dict:
+    """Pick (threshold, grid) for pool.decode; returns the cache entry."""
+    hit = None if force else lookup("batch_decode", workload)
+    if hit is not None:
+        pool.replan(hit["threshold"], hit["grid"])
+        return dict(hit, cached=True)
+    if grids is None:
+        sms = torch.cuda.get_device_properties(pool.device).multi_processor_count
+        grids = (0, 2 * sms, sms)
+    trials = []
+    for thr in thresholds:
+        for grid in grids:
+            pool.replan(thr, grid)
+            trials.append({"threshold": thr, "grid": grid,
+                           "ms": _time_ms(lambda: pool.decode(d_out), reps)})
+    best = min(trials, key=lambda t: t["ms"])
+    entry = {"threshold": best["threshold"], "grid": best["grid"], "ms": best["ms"],
+             "trials": trials}
+    store("batch_decode", workload, entry)
+    pool.replan(best["threshold"], best["grid"])
+    return dict(entry, cached=False)

@@ -191,3 +191,35 @@ def test_batch_is_repeatable_on_one_workspace():
         assert svb.svb_batch_decode(d_plan, d_lists, d_in, d_out, 1, res, ws, nb) == 0
         assert res[1].item() == 0
         assert np.array_equal(d_out.cpu().numpy().view(np.uint32), b.all_values)
+
+
+def test_list_pool_graph_and_per_list_agree():
+    """ListPool: packed pool equals the oracle streams; batched decode (eager and
+    from a CUDA graph) and one-launch-per-list decode all restore the lists."""
+    from paper_1709_08990_gb300.batch import ListPool
+    L = W.lists_lengths(300, cap=3_000_000)
+    vals, first = W.posting_lists(4, L)
+    pool = ListPool(L, vals, delta=True, threshold=4096)
+    host_pool = pool.pool.cpu().numpy()
+    for j in range(0, 300, 13):
+        s = oracle.encode(vals[int(first[j]):int(first[j]) + int(L[j])], delta=True)
+        off = int(pool.pool_off[j])
+        assert pool.sizes[j] == s.size and np.array_equal(host_pool[off:off + s.size], s)
+    d_vals = to_dev(vals)
+    out = torch.zeros(pool.total, dtype=torch.int32, device=DEV)
+    pool.decode(out)
+    assert pool.result()[1] == 0 and torch.equal(out, d_vals)
+    out.zero_()
+    g = pool.graph(lambda: pool.decode(out))
+    out.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, d_vals)
+    out2 = torch.zeros_like(out)
+    pool.decode_per_list(out2)
+    torch.cuda.synchronize()
+    assert torch.equal(out2, d_vals)
+    enc = torch.zeros(pool.pool_bytes, dtype=torch.uint8, device=DEV)
+    pool.encode_per_list(enc)
+    torch.cuda.synchronize()
+    assert torch.equal(enc, pool.pool)
