@@ -164,3 +164,59 @@ def array_values(name: str, n: int | None = None, out=None, threads: int = 0) ->
 
 def lists_lengths(num_lists: int = 100_000, cap: int = 1 << 30) -> np.ndarray:
     return list_lengths(WORKLOADS["lists_100k"].seed, num_lists, 8, 4194304, cap)
+
+
+# ---------------------------------------------------------------------------
+# Serving workload: requests over a pool of lists (seeded, reproducible).
+
+@dataclass
+class RequestStream:
+    arrival: np.ndarray      # seconds from the start, non-decreasing
+    is_encode: np.ndarray    # bool
+    list_id: np.ndarray      # decode: pool list id; encode: -1
+    n: np.ndarray            # integers of the request
+    enc_first: np.ndarray    # encode: index of the fresh list in enc_values; else -1
+    enc_values: np.ndarray   # fresh lists for the encode requests, back to back
+
+
+def zipf_ranks(rng, count: int, num_ranks: int, s: float = 1.1) -> np.ndarray:
+    """Ranks 0..num_ranks-1 drawn with P(rank r) proportional to (r+1)^-s."""
+    w = np.arange(1, num_ranks + 1, dtype=np.float64) ** (-s)
+    cdf = np.cumsum(w)
+    cdf /= cdf[-1]
+    return np.minimum(np.searchsorted(cdf, rng.random(count), side="right"), num_ranks - 1)
+
+
+def serve_requests(pool_lengths: np.ndarray, count: int, rate: float | None,
+                   seed: int = 5, encode_fraction: float = 0.05, s: float = 1.1,
+                   fresh_threads: int = 0) -> RequestStream:
+    """count requests over a pool of lists.  rate = mean arrivals per second
+    (Poisson; None puts every arrival at time 0).  Decode requests pick a
+    list by Zipf(s) over popularity ranks mapped to list ids by a seeded
+    permutation; encode requests carry a fresh sorted list whose length is
+    that of a uniformly drawn pool list, drawn like the pool's lists."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    k = pool_lengths.size
+    perm = rng.permutation(k)
+    if rate is None:
+        arrival = np.zeros(count)
+    else:
+        arrival = np.cumsum(rng.exponential(1.0 / rate, count))
+    is_enc = rng.random(count) < encode_fraction
+    list_id = perm[zipf_ranks(rng, count, k, s)]
+    n = pool_lengths[list_id].astype(np.int64)
+    enc_len = pool_lengths[rng.integers(0, k, count)].astype(np.int64)
+    n = np.where(is_enc, enc_len, n)
+    list_id = np.where(is_enc, -1, list_id)
+    enc_idx = np.flatnonzero(is_enc)
+    enc_first = np.full(count, -1, dtype=np.int64)
+    lens = n[enc_idx].astype(np.uint32)
+    if enc_idx.size:
+        firsts = np.zeros(enc_idx.size, dtype=np.int64)
+        firsts[1:] = np.cumsum(lens[:-1], dtype=np.int64)
+        enc_first[enc_idx] = firsts
+        # A fresh stream of the list generator (seed of this workload).
+        vals, _ = posting_lists(seed, lens, threads=fresh_threads)
+    else:
+        vals = np.zeros(0, dtype=np.uint32)
+    return RequestStream(arrival, is_enc, list_id, n, enc_first, vals)
