@@ -423,6 +423,33 @@ def time_codec(svb, W, name, dev, peaks):
                        "frac": alg / (ms_e / 1e3) / 1e9 / hb}}
 
 
+def time_serve(pool, W, seconds: float = 1.0):
+    """Serving loop over the pool: peak throughput with every request queued
+    at once, then Poisson arrivals at 10%..90% of that peak."""
+    from paper_1709_08990_gb300.serve import Server, summarize
+    srv = Server(pool, budget=16 << 30)
+    warm = W.serve_requests(pool.lengths, 2000, None, seed=105)
+    srv.run(warm)
+    req = W.serve_requests(pool.lengths, 30000, None, seed=5)
+    peak = summarize(req, srv.run(req))
+    mean_n = float(req.n.mean())
+    peak_rate = peak["gints_per_s"] * 1e9 / mean_n
+    levels = []
+    for i, f in enumerate([0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9]):
+        rate = f * peak_rate
+        count = max(500, int(rate * seconds))
+        r = W.serve_requests(pool.lengths, count, rate, seed=5 + 1000 * (i + 1))
+        s = summarize(r, srv.run(r))
+        s["load"] = f
+        s["offered_gints_per_s"] = rate * float(r.n.mean()) / 1e9
+        levels.append(s)
+    return {"budget_bytes": 16 << 30, "slots": len(srv.slots), "mean_request_ints": mean_n,
+            "peak": peak, "levels": levels}
+
+
+serve_levels = True
+
+
 def time_lists(svb, W, dev, peaks, count: int):
     """Batched delta decode/encode of the lists_100k workload (one persistent
     launch, replayed from a CUDA graph) against one launch per list."""
@@ -465,6 +492,7 @@ def time_lists(svb, W, dev, peaks, count: int):
     ms_enc_per_list = a.elapsed_time(b)
     alg = pool.pool_bytes + 4 * total
     hb = peaks["hbm_gbs"]
+    serve = time_serve(pool, W) if serve_levels else None
     out = {"lists": pool.k, "ints": total, "stream_bytes": pool.pool_bytes,
            "min_len": int(L.min()), "max_len": int(L.max()),
            "not_multiple_of_4": int((L % 4 != 0).sum()), "verified": ok and ok_per_list and ok_enc,
@@ -479,7 +507,8 @@ def time_lists(svb, W, dev, peaks, count: int):
                               "frac": alg / (ms_benc / 1e3) / 1e9 / hb},
            "encode_per_list": {"gints_per_s": total / ms_enc_per_list / 1e6,
                                "ms": ms_enc_per_list},
-           "encode_speedup_vs_per_list": ms_enc_per_list / ms_benc}
+           "encode_speedup_vs_per_list": ms_enc_per_list / ms_benc,
+           "serve": serve}
     del pool, d_out, d_out2, d_enc, d_vals
     torch.cuda.empty_cache()
     return out
