@@ -64,15 +64,18 @@ def measured_peaks() -> dict:
 
 
 def kernel_source_hash() -> str:
+    """Hash of the sources the decode kernels are built from."""
     h = hashlib.sha256()
-    for f in ("svb_decode.cu", "svb_device.cuh"):
+    for f in ("svb_decode_tiled.cu", "svb_quad.cuh", "svb_device.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1709_08990_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel: str, workload: str) -> int | None:
-    """DRAM bytes per launch from the committed ncu summary, when it was taken
-    on the current kernel source (else None)."""
+    """DRAM bytes (read + write) per launch of `kernel` on `workload`, from
+    the committed ncu summary profiles/traffic.txt, when the summary was taken
+    on the current kernel sources (else None).  Line format:
+    kernel workload bytes_per_launch source_hash"""
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
@@ -275,15 +278,27 @@ def main():
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    kernel_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    step_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
     value = n * args.steps * world / (total_ms / 1e3) / 1e9
     alg_bytes = in_len + 4 * n  # control + data read, 4n written
-    achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
+
+    # Per-kernel times, live: a second pass of the same K steps with the
+    # library's CUDA-event bracketing on (each launch timed on its stream).
+    svb.svb_profile_begin()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    kernels = svb.profile_end()
+    top = max(kernels, key=lambda k: kernels[k][1])
+    top_ms = kernels[top][1] / kernels[top][0]
+    achieved = alg_bytes / (top_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["source"],
-                "kernel": "decode_kernel<false>" if not w.delta else "decode_kernel<true>",
-                "alg_bytes_per_launch": alg_bytes,
-                "traffic": ncu_traffic("decode_kernel", args.workload)}
+                "kernel": top, "kernel_ms": top_ms, "alg_bytes_per_launch": alg_bytes,
+                "alg_bytes_note": "control + data bytes read + 4n bytes written per decode",
+                "step_ms": step_ms,
+                "step_frac": alg_bytes / (step_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+                "traffic": ncu_traffic(top, args.workload)}
 
     line = {
         "metric": "decode_gints_per_s", "value": value, "unit": "Gints/s", "n_gpus": world,
@@ -294,8 +309,9 @@ def main():
                    "bits_per_int": 8.0 * in_len / n, "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
         "roofline": roofline,
+        "kernels": {k: {"launches": c, "ms_per_launch": t / c} for k, (c, t) in kernels.items()},
         "clocks": clocks.summary(),
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * sum(c for c, _ in kernels.values()) // max(1, args.steps),
     }
 
     # ---- e2e: through the host-buffer C entry point ----------------------

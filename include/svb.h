@@ -143,6 +143,17 @@ enum svb_decode_variant {
 };
 int svb_set_decode_variant(int variant);
 
+/* ---- per-kernel timing --------------------------------------------------- */
+
+/* Start recording a CUDA event pair around every kernel the library launches
+ * (on the kernel's own stream).  Do not profile while capturing a CUDA graph. */
+int svb_profile_begin(void);
+
+/* Stop recording, wait for the recorded events and write one line per kernel,
+ * "name launches total_ms", longest total first, into buf (NUL-terminated,
+ * truncated to len).  Returns the bytes the full report needs. */
+size_t svb_profile_end(char *buf, size_t len);
+
 /* ---- async forms with a caller-owned workspace ------------------------- */
 
 /* Bytes of workspace one async call over n integers needs. */

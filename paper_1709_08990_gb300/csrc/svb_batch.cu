@@ -838,7 +838,9 @@ int launch_batch_decode(const void *d_plan, const svb_list *d_lists, const uint8
     a.hdr = static_cast<WsHeader *>(ws);
     a.result = result;
     a.delta = delta ? 1u : 0u;
+    prof_begin("batch_decode_kernel", stream);
     batch_decode_kernel<<<grid > 0 ? grid : g, kBBlock, sizeof(BPipe), stream>>>(a);
+    prof_end(stream);
     return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
 
@@ -858,7 +860,9 @@ int launch_batch_encode(const void *d_plan, const svb_list *d_lists, const uint3
     a.hdr = static_cast<WsHeader *>(ws);
     a.result = result;
     a.delta = delta ? 1u : 0u;
+    prof_begin("batch_encode_kernel", stream);
     batch_encode_kernel<<<grid > 0 ? grid : g, kBBlock, sizeof(EPipe), stream>>>(a);
+    prof_end(stream);
     return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
 

@@ -344,10 +344,12 @@ int launch_decode(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, uint32_t 
     a.prev = prev;
     a.out_aligned = (((uintptr_t)out) & 15u) == 0;
     dim3 grid((unsigned)(grid_override ? grid_override : a.ntiles));
+    prof_begin(delta ? "decode_kernel<delta>" : "decode_kernel<plain>", stream);
     if (delta)
         decode_kernel<true><<<grid, kThreads, 0, stream>>>(a);
     else
         decode_kernel<false><<<grid, kThreads, 0, stream>>>(a);
+    prof_end(stream);
     return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
 

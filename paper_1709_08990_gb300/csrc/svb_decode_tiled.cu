@@ -698,7 +698,9 @@ int launch_decode_tiled(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, uin
     o.st = st;
     o.spin_limit = spin_limit;
     o.in_aligned = (((uintptr_t)in) & 15u) == 0;
+    prof_begin("offsets_kernel", stream);
     offsets_kernel<<<(unsigned)ogrid, kThreads, 0, stream>>>(o);
+    prof_end(stream);
 
     TiledArgs t;
     t.in = in;
@@ -720,13 +722,19 @@ int launch_decode_tiled(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, uin
         u64 sgrid = min((u64)tiled_grid<kSums>(), ntiles);
         t.per_cta = (ntiles + sgrid - 1) / sgrid;
         sgrid = (ntiles + t.per_cta - 1) / t.per_cta;
+        prof_begin("decode_tiled_kernel<sums>", stream);
         decode_tiled_kernel<kSums><<<(unsigned)sgrid, kDecBlock, sizeof(Pipe), stream>>>(t);
+        prof_end(stream);
         t.per_cta = 0;
         u64 grid = min((u64)tiled_grid<kDelta>(), ntiles);
+        prof_begin("decode_tiled_kernel<delta>", stream);
         decode_tiled_kernel<kDelta><<<(unsigned)grid, kDecBlock, sizeof(Pipe), stream>>>(t);
+        prof_end(stream);
     } else {
         u64 grid = min((u64)tiled_grid<kPlain>(), ntiles);
+        prof_begin("decode_tiled_kernel<plain>", stream);
         decode_tiled_kernel<kPlain><<<(unsigned)grid, kDecBlock, sizeof(Pipe), stream>>>(t);
+        prof_end(stream);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }

@@ -233,10 +233,12 @@ int launch_encode(const uint32_t *in, u64 n, uint8_t *out, uint32_t prev, bool d
     a.in_aligned = (((uintptr_t)in) & 15u) == 0;
     a.delta = delta;
     dim3 grid((unsigned)a.ntiles);
+    prof_begin(delta ? "encode_kernel<delta>" : "encode_kernel<plain>", stream);
     if (delta)
         encode_kernel<true><<<grid, kThreads, 0, stream>>>(a);
     else
         encode_kernel<false><<<grid, kThreads, 0, stream>>>(a);
+    prof_end(stream);
     return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
 

@@ -39,6 +39,10 @@ size_t batch_plan_bytes(size_t num_lists);
 int build_batch_plan(const svb_list *h_lists, size_t num_lists, uint32_t threshold, void *d_plan,
                      cudaStream_t stream);
 
+// Per-kernel CUDA-event timing (svb_profile.cu); no-ops unless profiling is on.
+void prof_begin(const char *name, cudaStream_t s);
+void prof_end(cudaStream_t s);
+
 // Record the calling thread's status for svb_last_error().
 void set_last_error(int code);
 

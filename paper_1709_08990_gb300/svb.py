@@ -63,6 +63,8 @@ def lib() -> ctypes.CDLL:
             "svb_testhook_lookback_timeout": ([vp, sz, vp, u64, vp, vp, sz, vp], i32),
             "svb_decode_noalloc": ([vp, sz, sz, vp, u32, i32, vp], sz),
             "svb_batch_plan_bytes": ([sz], sz),
+            "svb_profile_begin": ([], i32),
+            "svb_profile_end": ([ctypes.c_char_p, sz], sz),
             "svb_batch_plan": ([vp, sz, u32, vp, sz, vp], i32),
             "svb_batch_workspace_size": ([], sz),
             "svb_batch_decode": ([vp, vp, vp, vp, i32, vp, vp, sz, i32, vp], i32),
@@ -220,6 +222,26 @@ def svb_batch_encode(d_plan, d_lists, in_base, out_base, delta, d_sizes, d_resul
     return lib().svb_batch_encode(_p(d_plan), _p(d_lists), _p(in_base), _p(out_base), int(delta),
                                   _p(d_sizes), _p(d_result), _p(ws), ws_bytes, grid,
                                   _stream(stream))
+
+
+def svb_profile_begin() -> int:
+    return lib().svb_profile_begin()
+
+
+def svb_profile_end(buf=None, size: int = 0) -> int:
+    return lib().svb_profile_end(buf, size)
+
+
+def profile_end() -> dict:
+    """Stop per-kernel timing: {kernel: (launches, total_ms)}."""
+    need = lib().svb_profile_end(None, 0)
+    buf = ctypes.create_string_buffer(max(need, 4096))
+    lib().svb_profile_end(buf, len(buf))
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, count, ms = line.rsplit(" ", 2)
+        out[name] = (int(count), float(ms))
+    return out
 
 
 SVB_NOALLOC_MAX_N = 1 << 24
