@@ -234,8 +234,7 @@ def svb_profile_end(buf=None, size: int = 0) -> int:
 
 def profile_end() -> dict:
     """Stop per-kernel timing: {kernel: (launches, total_ms)}."""
-    need = lib().svb_profile_end(None, 0)
-    buf = ctypes.create_string_buffer(max(need, 4096))
+    buf = ctypes.create_string_buffer(1 << 16)  # one call: it consumes the records
     lib().svb_profile_end(buf, len(buf))
     out = {}
     for line in buf.value.decode().splitlines():
