@@ -143,6 +143,23 @@ enum svb_decode_variant {
 };
 int svb_set_decode_variant(int variant);
 
+/* Encoder variant used by every encode call of this process:
+ *   SVB_ENCODE_AUTO (0)           the default, currently SVB_ENCODE_CHUNKED;
+ *   SVB_ENCODE_TILE_LOOKBACK (1)  one CTA per tile of 4096 integers, which
+ *                                 finds its data offset by a look-back over
+ *                                 its predecessors' byte totals;
+ *   SVB_ENCODE_CHUNKED (2)        persistent CTAs over chunks of 32768
+ *                                 integers: a sizing pass, one look-back per
+ *                                 chunk, then a writing pass whose second
+ *                                 read of the values is served by L2.
+ * Both give identical streams.  Returns SVB_EINVAL for an unknown variant. */
+enum svb_encode_variant {
+    SVB_ENCODE_AUTO = 0,
+    SVB_ENCODE_TILE_LOOKBACK = 1,
+    SVB_ENCODE_CHUNKED = 2
+};
+int svb_set_encode_variant(int variant);
+
 /* ---- per-kernel timing --------------------------------------------------- */
 
 /* Start recording a CUDA event pair around every kernel the library launches

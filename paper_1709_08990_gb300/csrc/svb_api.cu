@@ -21,6 +21,7 @@ thread_local int t_last_error = SVB_OK;
 thread_local cudaStream_t t_stream = nullptr;
 std::atomic<u64> g_spin_limit{0};
 std::atomic<int> g_decode_variant{SVB_DECODE_AUTO};
+std::atomic<int> g_encode_variant{SVB_ENCODE_AUTO};
 
 constexpr u64 kDefaultSpinLimit = 1ull << 21;  // ~2 s of polling at most
 
@@ -47,6 +48,14 @@ int decode_dispatch(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, uint32_
     if (g_decode_variant.load(std::memory_order_relaxed) == SVB_DECODE_SINGLE_PASS)
         return svb::launch_decode(in, in_len, n, out, prev, delta, ws, r, s, spin_limit());
     return svb::launch_decode_tiled(in, in_len, n, out, prev, delta, ws, r, s, spin_limit());
+}
+
+int encode_dispatch(const uint32_t *in, u64 n, uint8_t *out, uint32_t prev, bool delta,
+                    void *ws, svb::DeviceResult *r, cudaStream_t s)
+{
+    if (g_encode_variant.load(std::memory_order_relaxed) == SVB_ENCODE_TILE_LOOKBACK)
+        return svb::launch_encode(in, n, out, prev, delta, ws, r, s, spin_limit());
+    return svb::launch_encode_tiled(in, n, out, prev, delta, ws, r, s, spin_limit());
 }
 
 size_t set_error(int code)
@@ -120,7 +129,7 @@ size_t encode_sync(const uint32_t *in, size_t n, uint8_t *out, uint32_t prev, bo
     if (!in || !out)
         return set_error(SVB_EINVAL);
     return run_sync(n, [&](void *ws, svb::DeviceResult *r, cudaStream_t s) {
-        return svb::launch_encode(in, n, out, prev, delta, ws, r, s, spin_limit());
+        return encode_dispatch(in, n, out, prev, delta, ws, r, s);
     });
 }
 
@@ -274,6 +283,14 @@ int svb_set_decode_variant(int variant)
     return SVB_OK;
 }
 
+int svb_set_encode_variant(int variant)
+{
+    if (variant < SVB_ENCODE_AUTO || variant > SVB_ENCODE_CHUNKED)
+        return SVB_EINVAL;
+    g_encode_variant.store(variant, std::memory_order_relaxed);
+    return SVB_OK;
+}
+
 void svb_set_spin_limit(uint64_t iterations)
 {
     g_spin_limit.store(iterations, std::memory_order_relaxed);
@@ -305,8 +322,8 @@ int svb_encode_async(const uint32_t *in, size_t n, uint8_t *out, uint32_t prev, 
                                                                                  : SVB_ECUDA;
     if (!in || !out || !ws || ws_bytes < svb_workspace_size(n))
         return SVB_EINVAL;
-    return svb::launch_encode(in, n, out, prev, delta != 0, ws,
-                              reinterpret_cast<svb::DeviceResult *>(d_result), s, spin_limit());
+    return encode_dispatch(in, n, out, prev, delta != 0, ws,
+                           reinterpret_cast<svb::DeviceResult *>(d_result), s);
 }
 
 int svb_decode_async(const uint8_t *in, size_t in_len, size_t n, uint32_t *out,

@@ -28,6 +28,10 @@ int launch_encode(const uint32_t *in, u64 n, uint8_t *out, uint32_t prev, bool d
                   DeviceResult *result, cudaStream_t stream, u64 spin_limit);
 u64 encode_tiles(u64 n);
 
+// Chunked single-pass encoder (svb_encode_tiled.cu).
+int launch_encode_tiled(const uint32_t *in, u64 n, uint8_t *out, uint32_t prev, bool delta,
+                        void *ws, DeviceResult *result, cudaStream_t stream, u64 spin_limit);
+
 // Batched codec (svb_batch.cu).
 int launch_batch_decode(const void *d_plan, const svb_list *d_lists, const uint8_t *in,
                         uint32_t *out, bool delta, void *ws, DeviceResult *result,

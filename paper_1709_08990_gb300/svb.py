@@ -56,6 +56,7 @@ def lib() -> ctypes.CDLL:
             "svb_error_string": ([i32], ctypes.c_char_p),
             "svb_set_spin_limit": ([u64], None),
             "svb_set_decode_variant": ([i32], i32),
+            "svb_set_encode_variant": ([i32], i32),
             "svb_workspace_size": ([sz], sz),
             "svb_workspace_init": ([vp, sz, vp], i32),
             "svb_encode_async": ([vp, sz, vp, u32, i32, vp, vp, sz, vp], i32),
@@ -166,6 +167,13 @@ SVB_DECODE_AUTO, SVB_DECODE_SINGLE_PASS, SVB_DECODE_TWO_PASS = 0, 1, 2
 
 def svb_set_decode_variant(variant: int) -> int:
     return lib().svb_set_decode_variant(variant)
+
+
+SVB_ENCODE_AUTO, SVB_ENCODE_TILE_LOOKBACK, SVB_ENCODE_CHUNKED = 0, 1, 2
+
+
+def svb_set_encode_variant(variant: int) -> int:
+    return lib().svb_set_encode_variant(variant)
 
 
 def svb_last_error() -> int:

@@ -20,10 +20,14 @@ DEV = "cuda:0"
 
 @pytest.fixture(params=[1, 2], ids=["single_pass", "two_pass"])
 def variant(request):
-    """Run a decode test under each decoder variant."""
+    """Run a test under each decoder variant and, alongside, each encoder
+    variant (tile look-back with the single-pass decoder, chunked with the
+    two-pass decoder)."""
     assert svb.svb_set_decode_variant(request.param) == 0
+    assert svb.svb_set_encode_variant(request.param) == 0
     yield request.param
     svb.svb_set_decode_variant(0)
+    svb.svb_set_encode_variant(0)
 
 
 def to_dev(a: np.ndarray):
