@@ -249,7 +249,7 @@ int svb_batch_encode(const void *d_plan, const svb_list *d_lists, const uint32_t
  * allocator, or a latency-bound path that cannot afford cudaMalloc/cudaFree,
  * which may synchronize the device.
  *
- * Scratch: a fixed device array of about 1.2 MB inside the library, enough
+ * Scratch: a fixed device array of about 1.4 MB inside the library, enough
  * for n <= SVB_NOALLOC_MAX_N; every GPU that loads the library holds it until
  * the process exits.  n > SVB_NOALLOC_MAX_N returns SVB_ERROR with
  * SVB_EINVAL.  The first call on a device looks up the array's device

@@ -1,5 +1,4 @@
-// Stream VByte decoding, reduce-then-decode form: two kernels, no waits for
-// plain streams.
+// Stream VByte decoding of one array, reduce-then-decode form.
 //
 // The decoder's only serial dependency is where each quad's data bytes start:
 // the data pointer advances by C in [4,16] per control byte (Sec. 4, Fig. 4),
@@ -7,26 +6,27 @@
 // With the control stream apart, those positions depend on the control bytes
 // alone, so:
 //   offsets_kernel   reads only the control stream (2 bits per integer) and
-//                    writes, for every tile of kTileQuads quads, its byte
-//                    offset in the data stream.  Persistent CTAs each sum a
-//                    contiguous range of tiles, chain the range totals with
-//                    one decoupled look-back, then add their base.  It also
-//                    writes the stream's size and checks it against in_len.
+//                    writes the data-stream offset of every sub-tile of
+//                    kSubQuads quads (512 integers).  Persistent CTAs each sum
+//                    a contiguous range, chain the range totals with one
+//                    decoupled look-back, then add their base.  It also writes
+//                    the stream's size and checks it against in_len.
 //   decode_tiled     persistent CTAs with one producer warp and eight
-//                    consumer warps.  The producer claims tiles, reads their
-//                    offsets and has the TMA engine copy each tile's control
-//                    and data bytes into one of kStages shared-memory stages
-//                    (cp.async.bulk completing on the stage's "full"
-//                    mbarrier); consumers decode a full stage and release it
-//                    on its "empty" mbarrier.  Plain streams never wait on
-//                    another CTA; loads for later tiles are always in flight.
-// Differential streams need each tile's carry-in, prev plus the sum of all
-// earlier gaps (Sec. 2's prefix sum continued across tiles).  A sums pass runs
-// the same pipeline without stores: persistent CTAs take contiguous tile
-// ranges, sum each tile's gaps, and chain the range totals with one look-back
-// per CTA into per-tile carries.  The decode pass then adds a known carry and
-// never waits on another CTA.  For streams that fit in L2 (129 MB) the second
-// read of the stream is served by L2.
+//                    consumer warps.  The producer takes tiles of eight
+//                    sub-tiles round-robin, reads their offsets and has the TMA
+//                    engine copy each tile's control and data bytes into one of
+//                    kStages shared-memory stages (cp.async.bulk completing on
+//                    the stage's "full" mbarrier).  Each consumer warp decodes
+//                    one sub-tile on its own - warp scans only, no barrier with
+//                    the other warps - and releases it on the stage's "empty"
+//                    mbarrier.  Nothing waits on another CTA.
+// Differential streams need each sub-tile's carry-in: prev plus the sum of all
+// earlier gaps (Sec. 2's prefix sum continued across sub-tiles).  A sums pass
+// runs the same pipeline without stores: persistent CTAs take contiguous tile
+// ranges, each warp sums its sub-tile's gaps, and one look-back per CTA
+// chains the range totals into per-sub-tile carries.  The decode pass then adds
+// a known carry.  For streams that fit in L2 (129 MB) the second read of the
+// stream is served by L2.
 //
 // Bytes outside the stream are never read: each tile's range is copied as its
 // 16-byte-aligned interior by the bulk engine plus a ragged head and tail of
@@ -39,28 +39,32 @@
 
 namespace svb {
 
-constexpr int kTileQuads = 1024;                    // quads per tile (4096 integers)
-constexpr int kTileRounds = kTileQuads / kThreads;  // quads per lane per tile
-constexpr int kTileData = 16 * kTileQuads;          // data bytes per tile, at most
-constexpr int kStageData = kTileData + 64;          // + 16-byte phase + 2-word read slack
+constexpr int kTileQuads = 1024;                      // quads per tile (4096 integers)
+constexpr int kSubs = kTileQuads / kSubQuads;         // sub-tiles per tile = consumer warps
+constexpr int kSubRounds = kSubQuads / 32;            // quads per lane per sub-tile
+constexpr int kTileData = 16 * kTileQuads;            // data bytes per tile, at most
+constexpr int kStageData = kTileData + 64;            // + 16-byte phase + 2-word read slack
 constexpr int kStageCtrl = kTileQuads + 32;
 constexpr int kStages = 4;
-constexpr int kDecBlock = kThreads + 32;            // 8 consumer warps + 1 producer warp
-constexpr u64 kBarrierPolls = 1ull << 24;           // bound on one mbarrier wait
+constexpr int kDecBlock = kThreads + 32;              // 8 consumer warps + 1 producer warp
+constexpr u64 kBarrierPolls = 1ull << 24;             // bound on one mbarrier wait
 constexpr u64 kNoTile = ~0ull;
 
-// ---------------------------------------------------------------------------
-// Pass 1: tile offsets from the control stream.
+static_assert(kSubs == kWarps, "one consumer warp per sub-tile");
 
-constexpr int kOffGroup = 16;                       // tiles summed per CTA iteration
+// ---------------------------------------------------------------------------
+// Pass 1: sub-tile offsets from the control stream.
+
+constexpr int kOffGroupQuads = 64 * kThreads;         // quads per CTA iteration (64 per thread)
+constexpr int kOffGroupSubs = kOffGroupQuads / kSubQuads;
 
 struct OffsetsArgs {
     const uint8_t *in;
     u64 in_len;
-    u64 n, nquads, ntiles;
-    u64 groups;      // ceil(ntiles / kOffGroup)
+    u64 n, nquads, nsubs;
+    u64 groups;      // ceil(nquads / kOffGroupQuads)
     u64 per_cta;     // groups per CTA
-    u64 *offs;       // ntiles + 1 entries
+    u64 *offs;       // nsubs + 1 entries
     WsHeader *hdr;
     TileStatus *st;
     u64 spin_limit;
@@ -126,7 +130,7 @@ __device__ __forceinline__ uint32_t sum64(const OffsetsArgs &a, u64 q, uint32_t 
 
 __global__ void __launch_bounds__(kThreads) offsets_kernel(OffsetsArgs a)
 {
-    __shared__ uint32_t s_tsum[2][kOffGroup];
+    __shared__ uint32_t s_w[2][kWarps];
     __shared__ u64 s_cta, s_etag, s_base;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -140,32 +144,34 @@ __global__ void __launch_bounds__(kThreads) offsets_kernel(OffsetsArgs a)
     const u64 g0 = cta * a.per_cta;
     const u64 g1 = min(g0 + a.per_cta, a.groups);
 
-    // Local offsets: each group of 16 tiles is 16 KB of control bytes, 64 per
-    // thread and 16 threads per tile; warp 0 keeps the running total.
-    u64 running = 0;  // meaningful in warp 0
+    // Each iteration: 64 quads per thread, two threads per sub-tile.
+    u64 running = 0;  // this CTA's data bytes so far (every thread)
     int buf = 0;
     for (u64 g = g0; g < g1; g++, buf ^= 1) {
-        const u64 q = g * (u64)(kOffGroup * kTileQuads) + 64u * tid;
+        const u64 q = g * (u64)kOffGroupQuads + 64u * tid;
         uint32_t sum = sum64(a, q, last_nints);
-#pragma unroll
-        for (int d = 8; d >= 1; d >>= 1)
-            sum += __shfl_xor_sync(0xffffffffu, sum, d);
-        if ((tid & 15) == 0)
-            s_tsum[buf][tid >> 4] = sum;
+        sum += __shfl_xor_sync(0xffffffffu, sum, 1);   // the sub-tile's bytes
+        const uint32_t v = (lane & 1) ? 0u : sum;
+        const uint32_t inc = warp_incl_scan(v);
+        if (lane == 31)
+            s_w[buf][warp] = inc;
         __syncthreads();
-        if (warp == 0) {
-            uint32_t ts = lane < kOffGroup ? s_tsum[buf][lane] : 0u;
-            uint32_t inc = warp_incl_scan(ts);
-            u64 tile = g * kOffGroup + lane;
-            if (lane < kOffGroup && tile < a.ntiles)
-                a.offs[tile] = running + (inc - ts);
-            running += __shfl_sync(0xffffffffu, inc, 31);
+        uint32_t wpre = 0, tot = 0;
+#pragma unroll
+        for (int j = 0; j < kWarps; j++) {
+            const uint32_t t = s_w[buf][j];
+            wpre += j < warp ? t : 0u;
+            tot += t;
         }
-        // s_tsum is double-buffered: the next iteration writes the other half,
+        const u64 sub = g * kOffGroupSubs + (tid >> 1);
+        if (!(lane & 1) && sub < a.nsubs)
+            a.offs[sub] = running + wpre + inc - v;
+        running += tot;
+        // s_w is double-buffered: the next iteration writes the other half,
         // and the barrier of that iteration orders this read before reuse.
     }
 
-    // Chain the CTA totals, then add this CTA's base to its tiles.
+    // Chain the CTA totals, then add this CTA's base to its sub-tiles.
     if (warp == 0) {
         TileStatus *me = &a.st[cta];
         u64 base = 0;
@@ -183,9 +189,9 @@ __global__ void __launch_bounds__(kThreads) offsets_kernel(OffsetsArgs a)
         if (lane == 0) {
             if (!ok)
                 raise_error(a.hdr, kErrTimeout);
-            if (ok && g1 == a.groups && g0 < g1) {  // the CTA holding the last tile
+            if (ok && g1 == a.groups && g0 < g1) {  // the CTA holding the last sub-tile
                 u64 stream = a.nquads + base + running;
-                a.offs[a.ntiles] = base + running;
+                a.offs[a.nsubs] = base + running;
                 st_relaxed(&a.hdr->total, stream);
                 if (stream > a.in_len)
                     raise_error(a.hdr, kErrTruncated);
@@ -196,9 +202,9 @@ __global__ void __launch_bounds__(kThreads) offsets_kernel(OffsetsArgs a)
     __syncthreads();
     const u64 base = s_base;
     if (base) {
-        const u64 t0 = g0 * kOffGroup, t1 = min(g1 * kOffGroup, a.ntiles);
-        for (u64 t = t0 + tid; t < t1; t += kThreads)
-            a.offs[t] += base;
+        const u64 s0 = g0 * kOffGroupSubs, s1 = min(g1 * kOffGroupSubs, a.nsubs);
+        for (u64 s = s0 + tid; s < s1; s += kThreads)
+            a.offs[s] += base;
     }
     __syncthreads();
     if (tid == 0) {
@@ -216,16 +222,16 @@ __global__ void __launch_bounds__(kThreads) offsets_kernel(OffsetsArgs a)
 
 enum TiledMode : int {
     kPlain = 0,  // decode and store
-    kDelta = 1,  // decode, running sums plus the tile's precomputed carry, store
-    kSums = 2,   // decode, sum the tile's gaps; write per-tile carries (no stores)
+    kDelta = 1,  // decode, running sums plus each sub-tile's carry-in, store
+    kSums = 2,   // decode, sum each sub-tile's gaps; write per-sub-tile carries
 };
 
 struct TiledArgs {
     const uint8_t *in;
-    u64 n, nquads, ntiles;
+    u64 n, nquads, ntiles, nsubs;
     uint32_t *out;
     const u64 *offs;
-    uint32_t *carries;  // per tile: written by kSums, read by kDelta
+    uint32_t *carries;  // per sub-tile: written by kSums, read by kDelta
     WsHeader *hdr;
     TileStatus *st;
     DeviceResult *result;
@@ -241,8 +247,9 @@ struct Pipe {
     uint64_t full[kStages];
     uint64_t empty[kStages];
     u64 tile[kStages];
-    uint32_t hd[kStages], hc[kStages];  // address phase (mod 16) of the data / control range
-    uint32_t carry[kStages];            // kDelta: the tile's carry-in
+    uint32_t hd[kStages], hc[kStages];   // address phase (mod 16) of the data / control range
+    uint32_t soff[kStages][kSubs];       // each sub-tile's data offset inside the tile
+    uint32_t carry[kStages][kSubs];      // kDelta: each sub-tile's carry-in
 };
 
 // The k-th tile this CTA handles: round-robin for decoding, a contiguous
@@ -258,17 +265,24 @@ __device__ __forceinline__ u64 tile_of(const TiledArgs &a, u64 first, uint32_t k
 }
 
 // Producer warp: fill stages with tiles until none is left, then post one
-// stage marked kNoTile.  Returns normally or after a bounded wait gave up.
+// stage marked kNoTile.  Lane j < 9 carries the offset of sub-tile j of the
+// next tile (the ninth is where the tile ends); lane j < 8 its carry.
 template <int kMode>
 __device__ void produce(const TiledArgs &a, Pipe &P, u64 first, int lane)
 {
     uint32_t issued = 0;  // stage fills posted (iteration k fills stage k % kStages)
+    auto fetch = [&](u64 t, u64 &off, uint32_t &car) {
+        if (t < a.ntiles && lane <= kSubs) {
+            const u64 sb = min(t * kSubs + lane, a.nsubs);
+            off = a.offs[sb];
+            if (kMode == kDelta && lane < kSubs && sb < a.nsubs)
+                car = a.carries[sb];
+        }
+    };
     u64 next = tile_of<kMode>(a, first, 0);
-    u64 nd0 = 0, nd1 = 0;
-    if (next < a.ntiles) {
-        nd0 = a.offs[next];
-        nd1 = a.offs[next + 1];
-    }
+    u64 noff = 0;
+    uint32_t ncar = 0;
+    fetch(next, noff, ncar);
     for (uint32_t k = 0;; k++) {
         const int s = k % kStages;
         if (k >= (uint32_t)kStages) {
@@ -280,7 +294,8 @@ __device__ void produce(const TiledArgs &a, Pipe &P, u64 first, int lane)
             }
         }
         const u64 t = next;
-        const u64 d0 = nd0, d1 = nd1;
+        const u64 off = noff;
+        const uint32_t car = ncar;
         if (t >= a.ntiles) {
             if (lane == 0) {
                 P.tile[s] = kNoTile;
@@ -291,11 +306,15 @@ __device__ void produce(const TiledArgs &a, Pipe &P, u64 first, int lane)
             issued = k + 1;
             break;
         }
-        // Read the next tile's offsets now so that the load overlaps this one.
+        // Read the next tile's offsets now so that the loads overlap this one.
         next = tile_of<kMode>(a, first, k + 1);
-        if (next < a.ntiles) {
-            nd0 = a.offs[next];
-            nd1 = a.offs[next + 1];
+        fetch(next, noff, ncar);
+        const u64 d0 = __shfl_sync(0xffffffffu, off, 0);
+        const u64 d1 = __shfl_sync(0xffffffffu, off, kSubs);
+        if (lane < kSubs) {
+            P.soff[s][lane] = (uint32_t)(off - d0);
+            if (kMode == kDelta)
+                P.carry[s][lane] = car;
         }
         const u64 q0 = t * kTileQuads;
         const uint32_t clen = (uint32_t)min((u64)kTileQuads, a.nquads - q0);
@@ -312,8 +331,6 @@ __device__ void produce(const TiledArgs &a, Pipe &P, u64 first, int lane)
             P.tile[s] = t;
             P.hc[s] = (uint32_t)((uintptr_t)gc & 15u);
             P.hd[s] = (uint32_t)((uintptr_t)gd & 15u);
-            if (kMode == kDelta)
-                P.carry[s] = a.carries[t];
             mbar_arrive_expect_tx(&P.full[s], bc + bd);
             if (bc)
                 bulk_g2s(P.ctrl[s] + oc, ac, bc, &P.full[s]);
@@ -336,42 +353,46 @@ __device__ void produce(const TiledArgs &a, Pipe &P, u64 first, int lane)
     __syncwarp();
 }
 
-// Consumer warps (8, synchronised among themselves by named barrier 1).
+// Consumer warp `warp`: decodes sub-tile `warp` of every tile, alone.
 template <int kMode>
-__device__ void consume(const TiledArgs &a, Pipe &P, uint16_t *s_qoff, uint32_t *s_warp,
-                        u64 first, u64 etag)
+__device__ void consume(const TiledArgs &a, Pipe &P, uint16_t *s_pos)
 {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t last_nints = (uint32_t)(a.n - 4 * (a.nquads - 1));
-    uint32_t running = 0;  // kSums: gap sum of this CTA's tiles so far (thread 0)
+    uint16_t *pos = s_pos + warp * kSubQuads;   // this warp's staged positions
     for (uint32_t k = 0;; k++) {
         const int s = k % kStages;
-        bool ok = mbar_wait_bounded(&P.full[s], (k / kStages) & 1u, kBarrierPolls);
-        if (!ok) {  // cannot happen unless a copy is lost; give up quietly
-            raise_error(a.hdr, kErrTimeout);
+        if (!mbar_wait_bounded(&P.full[s], (k / kStages) & 1u, kBarrierPolls)) {
+            raise_error(a.hdr, kErrTimeout);  // cannot happen unless a copy is lost
             break;
         }
         const u64 tile = P.tile[s];
         if (tile == kNoTile)
             break;
-
-        // ---- control bytes -> staged position of every quad -----------------
-        const u64 q0 = tile * kTileQuads;
-        const uint32_t nq = (uint32_t)min((u64)kTileQuads, a.nquads - q0);
-        // Every tile but possibly the last holds kTileQuads quads of four.
-        const bool full = nq == kTileQuads && (tile + 1 < a.ntiles || last_nints == 4);
-        const uint8_t *C = P.ctrl[s] + P.hc[s];
+        const u64 q0 = tile * kTileQuads + (u64)warp * kSubQuads;  // first quad of the sub-tile
+        const u64 sb = tile * kSubs + warp;
+        if (q0 >= a.nquads) {  // the last tile may have fewer sub-tiles
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(&P.empty[s]);
+            continue;
+        }
+        const uint32_t nq = (uint32_t)min((u64)kSubQuads, a.nquads - q0);
+        const bool full = nq == kSubQuads && (q0 + kSubQuads < a.nquads || last_nints == 4);
+        const uint8_t *C = P.ctrl[s] + P.hc[s] + warp * kSubQuads;
         const uint8_t *D = P.data[s];
-        const uint32_t h = P.hd[s];
-        const uint32_t carry_in = kMode == kDelta ? P.carry[s] : 0u;
+        const uint32_t base = P.hd[s] + P.soff[s][warp];
+        const uint32_t carry_in = kMode == kDelta ? P.carry[s][warp] : 0u;
+
+        // ---- control bytes -> staged position of each of the warp's quads ----
         uint32_t w = 0;
-        if (P.hc[s] == 0 && 4u * tid + 4u <= nq) {
-            w = reinterpret_cast<const uint32_t *>(C)[tid];
+        if (((uintptr_t)C & 3u) == 0 && 4u * lane + 4u <= nq) {
+            w = reinterpret_cast<const uint32_t *>(C)[lane];
         } else {
 #pragma unroll
             for (int j = 0; j < 4; j++)
-                if (4u * tid + j < nq)
-                    w |= (uint32_t)C[4 * tid + j] << (8 * j);
+                if (4u * lane + j < nq)
+                    w |= (uint32_t)C[4 * lane + j] << (8 * j);
         }
         uint32_t o1, o2, o3, tsum;
         if (full) {
@@ -388,7 +409,7 @@ __device__ void consume(const TiledArgs &a, Pipe &P, uint16_t *s_qoff, uint32_t 
             uint32_t cnt[4];
 #pragma unroll
             for (int j = 0; j < 4; j++) {
-                uint32_t lq = 4u * tid + j;
+                const uint32_t lq = 4u * lane + j;
                 uint32_t c = (w >> (8 * j)) & 0xffu;
                 uint32_t nints = 4;
                 if (q0 + lq == a.nquads - 1 && last_nints < 4) {
@@ -402,77 +423,44 @@ __device__ void consume(const TiledArgs &a, Pipe &P, uint16_t *s_qoff, uint32_t 
             o3 = o2 + cnt[2];
             tsum = o3 + cnt[3];
         }
-        uint32_t incl = warp_incl_scan(tsum);
-        if (lane == 31)
-            s_warp[warp] = incl;
-        named_sync(1, kThreads);
-        uint32_t wpre = 0;
-#pragma unroll
-        for (int j = 0; j < kWarps; j++)
-            wpre += j < warp ? s_warp[j] : 0u;
+        const uint32_t incl = warp_incl_scan(tsum);
         {
-            const uint32_t o0 = h + wpre + incl - tsum;  // staged position of the thread's data
-            reinterpret_cast<uint2 *>(s_qoff)[tid] =
+            const uint32_t o0 = base + incl - tsum;
+            reinterpret_cast<uint2 *>(pos)[lane] =
                 make_uint2(o0 | ((o0 + o1) << 16), (o0 + o2) | ((o0 + o3) << 16));
         }
-        named_sync(1, kThreads);
+        __syncwarp();
 
-        // ---- gather: one quad per lane per round ----------------------------
-        const uint32_t lq0 = warp * (32 * kTileRounds) + lane;
-        const uint8_t *Cl = C + lq0;
-        const uint16_t *Ql = s_qoff + lq0;
-        uint32_t *op = a.out + 4 * (q0 + lq0);
-        uint32_t v[kTileRounds][4];
-        if (full) {
+        // ---- gather: one quad per lane per round ------------------------------
+        uint32_t *op = a.out + 4 * (q0 + lane);
+        uint32_t v[kSubRounds][4];
 #pragma unroll
-            for (int r = 0; r < kTileRounds; r++) {
-                const uint32_t c = Cl[32 * r];
-                const uint32_t p = Ql[32 * r];
-                uint4 x;
+        for (int r = 0; r < kSubRounds; r++) {
+            const uint32_t lq = r * 32 + lane;
+            uint4 x;
+            if (full) {
+                const uint32_t c = C[lq];
+                const uint32_t p = pos[lq];
                 if (__all_sync(0xffffffffu, c == 0))
                     x = widen_quad(D, p);
                 else
                     x = decode_quad(D, p, c);
-                v[r][0] = x.x;
-                v[r][1] = x.y;
-                v[r][2] = x.z;
-                v[r][3] = x.w;
-                if (kMode == kPlain) {
-                    if (a.out_aligned) {
-                        stg_stream128(op + 128 * r, x);
-                    } else {
-                        op[128 * r + 0] = x.x;
-                        op[128 * r + 1] = x.y;
-                        op[128 * r + 2] = x.z;
-                        op[128 * r + 3] = x.w;
-                    }
-                }
-            }
-        } else {
-#pragma unroll
-            for (int r = 0; r < kTileRounds; r++) {
-                const uint32_t lq = lq0 + r * 32;
+            } else {
                 const bool valid = lq < nq;
                 uint32_t c = valid ? C[lq] : 0u;
                 const uint32_t nints = !valid ? 0u : (q0 + lq == a.nquads - 1 ? last_nints : 4u);
                 if (nints < 4)
                     c &= (1u << (2 * nints)) - 1u;
-                const uint32_t p = valid ? s_qoff[lq] : h;
-                uint4 x = decode_quad(D, p, c);
-                v[r][0] = nints > 0 ? x.x : 0u;
-                v[r][1] = nints > 1 ? x.y : 0u;
-                v[r][2] = nints > 2 ? x.z : 0u;
-                v[r][3] = nints > 3 ? x.w : 0u;
-                if (kMode == kPlain && valid) {
-                    op[128 * r] = x.x;
-                    if (nints > 1)
-                        op[128 * r + 1] = x.y;
-                    if (nints > 2)
-                        op[128 * r + 2] = x.z;
-                    if (nints > 3)
-                        op[128 * r + 3] = x.w;
-                }
+                x = decode_quad(D, valid ? pos[lq] : base, c);
+                x.x = nints > 0 ? x.x : 0u;
+                x.y = nints > 1 ? x.y : 0u;
+                x.z = nints > 2 ? x.z : 0u;
+                x.w = nints > 3 ? x.w : 0u;
             }
+            v[r][0] = x.x;
+            v[r][1] = x.y;
+            v[r][2] = x.z;
+            v[r][3] = x.w;
         }
         // This warp no longer reads stage s.
         __syncwarp();
@@ -480,106 +468,96 @@ __device__ void consume(const TiledArgs &a, Pipe &P, uint16_t *s_qoff, uint32_t 
             mbar_arrive(&P.empty[s]);
 
         if (kMode == kSums) {
-            // ---- the tile's gap sum; thread 0 keeps the CTA's running total --
             uint32_t t = 0;
 #pragma unroll
-            for (int r = 0; r < kTileRounds; r++)
+            for (int r = 0; r < kSubRounds; r++)
                 t += v[r][0] + v[r][1] + v[r][2] + v[r][3];
 #pragma unroll
             for (int d = 16; d >= 1; d >>= 1)
                 t += __shfl_xor_sync(0xffffffffu, t, d);
-            named_sync(1, kThreads);  // every warp has read s_warp (offsets) above
             if (lane == 0)
-                s_warp[warp] = t;
-            named_sync(1, kThreads);
-            if (tid == 0) {
-                uint32_t vagg = 0;
-#pragma unroll
-                for (int j = 0; j < kWarps; j++)
-                    vagg += s_warp[j];
-                a.carries[tile] = running;  // carry relative to the CTA's first tile
-                running += vagg;
-            }
+                a.carries[sb] = t;  // the sub-tile's gap sum; made a carry later
+            continue;
         }
         if (kMode == kDelta) {
-            // ---- running sums: quad, warp, block, plus the carry-in -----------
-            uint32_t qexcl[kTileRounds], wrun = 0;
+            // Running sums: within the quad, across the warp's rounds, carry-in.
+            uint32_t run = carry_in;
 #pragma unroll
-            for (int r = 0; r < kTileRounds; r++) {
+            for (int r = 0; r < kSubRounds; r++) {
                 v[r][1] += v[r][0];
                 v[r][2] += v[r][1];
                 v[r][3] += v[r][2];
-                uint32_t qs = v[r][3];
-                uint32_t inc = warp_incl_scan(qs);
-                qexcl[r] = wrun + inc - qs;
-                wrun += __shfl_sync(0xffffffffu, inc, 31);
+                const uint32_t qs = v[r][3];
+                const uint32_t inc = warp_incl_scan(qs);
+                const uint32_t add = run + inc - qs;
+#pragma unroll
+                for (int j = 0; j < 4; j++)
+                    v[r][j] += add;
+                run += __shfl_sync(0xffffffffu, inc, 31);
             }
-            named_sync(1, kThreads);  // every warp has read s_warp (offsets) above
-            if (lane == 0)
-                s_warp[warp] = wrun;
-            named_sync(1, kThreads);
-            uint32_t bpre = carry_in;
+        }
 #pragma unroll
-            for (int j = 0; j < kWarps; j++)
-                bpre += j < warp ? s_warp[j] : 0u;
-#pragma unroll
-            for (int r = 0; r < kTileRounds; r++) {
-                const uint32_t lq = lq0 + r * 32;
-                if (lq >= nq)
-                    continue;
-                const uint32_t nints = full ? 4u : (q0 + lq == a.nquads - 1 ? last_nints : 4u);
-                const uint32_t add = bpre + qexcl[r];
-                uint32_t *dst = op + 128 * r;
-                uint4 y = make_uint4(v[r][0] + add, v[r][1] + add, v[r][2] + add, v[r][3] + add);
-                if (nints == 4 && a.out_aligned) {
-                    stg_stream128(dst, y);
-                } else {
-                    dst[0] = y.x;
-                    if (nints > 1)
-                        dst[1] = y.y;
-                    if (nints > 2)
-                        dst[2] = y.z;
-                    if (nints > 3)
-                        dst[3] = y.w;
-                }
+        for (int r = 0; r < kSubRounds; r++) {
+            const uint32_t lq = r * 32 + lane;
+            uint32_t *dst = op + 128 * r;
+            if (full && a.out_aligned) {
+                stg_stream128(dst, make_uint4(v[r][0], v[r][1], v[r][2], v[r][3]));
+            } else if (lq < nq) {
+                const uint32_t nints = q0 + lq == a.nquads - 1 ? last_nints : 4u;
+                dst[0] = v[r][0];
+                if (nints > 1)
+                    dst[1] = v[r][1];
+                if (nints > 2)
+                    dst[2] = v[r][2];
+                if (nints > 3)
+                    dst[3] = v[r][3];
             }
         }
     }
+}
 
-    if (kMode == kSums) {
-        // Chain this CTA's range total with the ranges before it, then turn
-        // the range-relative carries into absolute ones (prev included).
-        __shared__ uint32_t s_base;
-        if (warp == 0) {
-            u64 range_total = __shfl_sync(0xffffffffu, running, 0);
-            TileStatus *me = &a.st[first / (a.per_cta ? a.per_cta : 1)];
-            const u64 cta = first / (a.per_cta ? a.per_cta : 1);
-            u64 base = a.prev;
-            bool ok = true;
-            if (cta == 0) {
-                if (lane == 0)
-                    publish(&me->val_tag, &me->val_pre, (uint32_t)(a.prev + range_total),
-                            kFlagPrefix, etag);
-            } else {
-                if (lane == 0)
-                    publish(&me->val_tag, &me->val_agg, (uint32_t)range_total, kFlagAgg, etag);
-                base = lookback<true>(a.st, cta, etag, a.spin_limit, a.hdr, ok);
-                if (ok && lane == 0)
-                    publish(&me->val_tag, &me->val_pre, (uint32_t)(base + range_total),
-                            kFlagPrefix, etag);
-            }
-            if (lane == 0) {
-                if (!ok)
-                    raise_error(a.hdr, kErrTimeout);
-                s_base = (uint32_t)base;
-            }
+// kSums epilogue: turn this CTA's sub-tile gap sums into carries.  Scans the
+// range's sums in order (relative carries), chains the range total with the
+// ranges before by one look-back, then adds the base (prev for the first).
+__device__ void sums_to_carries(const TiledArgs &a, u64 first, u64 etag, uint32_t *s_base)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const u64 s0 = first * kSubs;
+    const u64 s1 = min(min(first + a.per_cta, a.ntiles) * kSubs, a.nsubs);
+    if (warp == 0) {
+        uint32_t run = 0;
+        for (u64 b = s0; b < s1; b += 32) {
+            const u64 i = b + lane;
+            const uint32_t v = i < s1 ? a.carries[i] : 0u;
+            const uint32_t inc = warp_incl_scan(v);
+            if (i < s1)
+                a.carries[i] = run + inc - v;
+            run += __shfl_sync(0xffffffffu, inc, 31);
         }
-        named_sync(1, kThreads);
-        const uint32_t base = s_base;
-        const u64 end = min(first + a.per_cta, a.ntiles);
-        for (u64 t = first + tid; t < end; t += kThreads)
-            a.carries[t] += base;
+        const u64 cta = first / (a.per_cta ? a.per_cta : 1);
+        TileStatus *me = &a.st[cta];
+        u64 base = a.prev;
+        bool ok = true;
+        if (cta == 0) {
+            if (lane == 0)
+                publish(&me->val_tag, &me->val_pre, (uint32_t)(a.prev + run), kFlagPrefix, etag);
+        } else {
+            if (lane == 0)
+                publish(&me->val_tag, &me->val_agg, run, kFlagAgg, etag);
+            base = lookback<true>(a.st, cta, etag, a.spin_limit, a.hdr, ok);
+            if (ok && lane == 0)
+                publish(&me->val_tag, &me->val_pre, (uint32_t)(base + run), kFlagPrefix, etag);
+        }
+        if (lane == 0) {
+            if (!ok)
+                raise_error(a.hdr, kErrTimeout);
+            *s_base = (uint32_t)base;
+        }
     }
+    named_sync(1, kThreads);
+    const uint32_t base = *s_base;
+    for (u64 i = s0 + tid; i < s1; i += kThreads)
+        a.carries[i] += base;
 }
 
 template <int kMode>
@@ -587,10 +565,9 @@ __global__ void __launch_bounds__(kDecBlock, 3) decode_tiled_kernel(TiledArgs a)
 {
     extern __shared__ __align__(128) uint8_t dyn_smem[];
     Pipe &P = *reinterpret_cast<Pipe *>(dyn_smem);
-    __shared__ __align__(16) uint16_t s_qoff[kTileQuads];
-    __shared__ uint32_t s_warp[kWarps];
+    __shared__ __align__(16) uint16_t s_pos[kTileQuads];
     __shared__ u64 s_etag, s_first;
-    __shared__ uint32_t s_flag;
+    __shared__ uint32_t s_flag, s_base;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
@@ -608,10 +585,15 @@ __global__ void __launch_bounds__(kDecBlock, 3) decode_tiled_kernel(TiledArgs a)
     }
     __syncthreads();
     if (!s_flag) {  // else the offsets pass failed (truncated stream)
-        if (warp == kWarps)
+        if (warp == kWarps) {
             produce<kMode>(a, P, s_first, lane);
-        else
-            consume<kMode>(a, P, s_qoff, s_warp, s_first, s_etag);
+        } else {
+            consume<kMode>(a, P, s_pos);
+            if (kMode == kSums) {
+                named_sync(1, kThreads);  // every sub-tile sum of the range is written
+                sums_to_carries(a, s_first, s_etag, &s_base);
+            }
+        }
     }
     if (kMode == kSums) {
         // The decode pass that follows owns the result and the counters; only
@@ -678,6 +660,7 @@ int launch_decode_tiled(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, uin
     const WsLayout L = ws_layout(n);
     const u64 nquads = (n + 3) / 4;
     const u64 ntiles = (nquads + kTileQuads - 1) / kTileQuads;
+    const u64 nsubs = (nquads + kSubQuads - 1) / kSubQuads;
     WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
     u64 *offs = reinterpret_cast<u64 *>(static_cast<char *>(ws) + L.offs);
     uint32_t *carries = reinterpret_cast<uint32_t *>(static_cast<char *>(ws) + L.carries);
@@ -688,8 +671,8 @@ int launch_decode_tiled(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, uin
     o.in_len = in_len;
     o.n = n;
     o.nquads = nquads;
-    o.ntiles = ntiles;
-    o.groups = (ntiles + kOffGroup - 1) / kOffGroup;
+    o.nsubs = nsubs;
+    o.groups = (nquads + kOffGroupQuads - 1) / kOffGroupQuads;
     u64 ogrid = min((u64)offsets_grid(), o.groups);
     o.per_cta = (o.groups + ogrid - 1) / ogrid;
     ogrid = (o.groups + o.per_cta - 1) / o.per_cta;  // no CTA without groups
@@ -707,6 +690,7 @@ int launch_decode_tiled(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, uin
     t.n = n;
     t.nquads = nquads;
     t.ntiles = ntiles;
+    t.nsubs = nsubs;
     t.out = out;
     t.offs = offs;
     t.carries = carries;

@@ -21,7 +21,8 @@ typedef unsigned long long u64;
 
 constexpr int kThreads = 256;                      // threads per CTA
 constexpr int kWarps = kThreads / 32;
-constexpr int kMinQuadsPerTile = 256;              // workspace sizing unit
+constexpr int kMinQuadsPerTile = 256;              // workspace sizing unit (tile records)
+constexpr int kSubQuads = 128;                     // sub-tile: the quads one warp decodes
 
 // Status word low bits: what the tile has published.
 constexpr u64 kFlagNone = 0, kFlagAgg = 1, kFlagPrefix = 2;
@@ -63,13 +64,14 @@ struct WsLayout {
     size_t total;    // workspace bytes
 };
 
-// Layout for up to `tiles` tiles (of any tile size >= kMinQuadsPerTile quads).
-inline WsLayout ws_layout_for_tiles(u64 tiles)
+// Layout for up to `subs` sub-tiles (offsets and carries, one per kSubQuads
+// quads) and `tiles` tile records (one per kMinQuadsPerTile quads or more).
+inline WsLayout ws_layout_for(u64 subs, u64 tiles)
 {
     WsLayout l;
     l.offs = kOffsetsOffset;
-    l.carries = (l.offs + 8 * (tiles + 1) + 63) & ~(size_t)63;
-    l.status = (l.carries + 4 * (tiles ? tiles : 1) + 63) & ~(size_t)63;
+    l.carries = (l.offs + 8 * (subs + 1) + 63) & ~(size_t)63;
+    l.status = (l.carries + 4 * (subs ? subs : 1) + 63) & ~(size_t)63;
     l.total = l.status + sizeof(TileStatus) * (tiles ? tiles : 1);
     return l;
 }
@@ -77,7 +79,8 @@ inline WsLayout ws_layout_for_tiles(u64 tiles)
 inline WsLayout ws_layout(u64 n)
 {
     u64 nq = (n + 3) / 4;
-    return ws_layout_for_tiles((nq + kMinQuadsPerTile - 1) / kMinQuadsPerTile);
+    return ws_layout_for((nq + kSubQuads - 1) / kSubQuads,
+                         (nq + kMinQuadsPerTile - 1) / kMinQuadsPerTile);
 }
 
 struct DeviceResult {

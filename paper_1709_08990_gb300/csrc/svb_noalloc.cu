@@ -11,7 +11,7 @@
 // and a pinned result buffer; this one never does.
 //
 // The scratch holds the workspace of one decode of up to SVB_NOALLOC_MAX_N
-// integers (about 1.2 MB).  Every GPU that loads the library keeps it until
+// integers (about 1.4 MB).  Every GPU that loads the library keeps it until
 // the process exits.  All calls share it, so calls that overlap on the GPU
 // race: order them on one stream or serialize them on the host.
 #include <cuda_runtime.h>
@@ -29,9 +29,10 @@ using svb::u64;
 // Workspace bytes of one decode of SVB_NOALLOC_MAX_N integers, laid out as
 // svb::ws_layout lays it out (header, tile offsets, tile records).
 constexpr u64 kNoAllocQuads = ((u64)SVB_NOALLOC_MAX_N + 3) / 4;
+constexpr u64 kNoAllocSubs = (kNoAllocQuads + svb::kSubQuads - 1) / svb::kSubQuads;
 constexpr u64 kNoAllocTiles = (kNoAllocQuads + svb::kMinQuadsPerTile - 1) / svb::kMinQuadsPerTile;
-constexpr u64 kNoAllocCarries = (svb::kOffsetsOffset + 8 * (kNoAllocTiles + 1) + 63) & ~(u64)63;
-constexpr u64 kNoAllocStatus = (kNoAllocCarries + 4 * kNoAllocTiles + 63) & ~(u64)63;
+constexpr u64 kNoAllocCarries = (svb::kOffsetsOffset + 8 * (kNoAllocSubs + 1) + 63) & ~(u64)63;
+constexpr u64 kNoAllocStatus = (kNoAllocCarries + 4 * kNoAllocSubs + 63) & ~(u64)63;
 constexpr u64 kNoAllocBytes = kNoAllocStatus + sizeof(svb::TileStatus) * kNoAllocTiles;
 
 // Zero-initialised when the module loads; never freed.
