@@ -184,6 +184,7 @@ __device__ void bdec_produce(const BatchDecArgs &a, BPipe &P, int lane)
         const uint32_t nq = min((uint32_t)kBQuads, nql - k * kBQuads);
         const uint32_t dsize =
             tile_data_bytes(P.ctrl[s] + P.hc[s], nq, last_tile, last_nints, lane);
+        fence_proxy_async_smem();  // these reads come before any later copy into the stage
         const bool trunc = nql + running + dsize > L.in_len;
         const uint8_t *gd = a.in + L.in_off + nql + running;
         const uint32_t dlen = trunc ? 0u : dsize;
@@ -325,6 +326,7 @@ __device__ void bdec_consume(const BatchDecArgs &a, BPipe &P, uint16_t *s_qoff,
             v[r][2] = nints > 2 ? x.z : 0u;
             v[r][3] = nints > 3 ? x.w : 0u;
         }
+        fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0)
             mbar_arrive(&P.empty[s]);
@@ -665,6 +667,7 @@ __device__ void benc_consume(const BatchEncArgs &a, EPipe &P, uint32_t *s_warp, 
             agg += t;
         }
         before = *s_last;
+        fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0)
             mbar_arrive(&P.empty[s]);

@@ -279,6 +279,7 @@ __device__ void produce(const TiledArgs &a, Pipe &P, u64 first, int lane)
                 car = a.carries[sb];
         }
     };
+    const uint8_t *stream_end = a.in + a.nquads + a.offs[a.nsubs];
     u64 next = tile_of<kMode>(a, first, 0);
     u64 noff = 0;
     uint32_t ncar = 0;
@@ -321,21 +322,24 @@ __device__ void produce(const TiledArgs &a, Pipe &P, u64 first, int lane)
         const uint8_t *gc = a.in + q0;
         const uint8_t *gd = a.in + a.nquads + d0;
         const uint32_t dlen = (uint32_t)(d1 - d0);
-        range_edges(gc, clen, P.ctrl[s], lane);
-        range_edges(gd, dlen, P.data[s], lane);
+        // Everything in [in, stream end) may be read: a tile's aligned ends
+        // are bytes of its neighbours, so almost every tile is one bulk copy
+        // per stream and the producer never waits on a load of its own.
+        const StagePlan pc = stage_plan(gc, clen, a.in, stream_end);
+        const StagePlan pd = stage_plan(gd, dlen, a.in, stream_end);
+        if (pc.edges)
+            range_edges(gc, clen, P.ctrl[s], lane);
+        if (pd.edges)
+            range_edges(gd, dlen, P.data[s], lane);
         if (lane == 0) {
-            const uint8_t *ac, *ad;
-            uint32_t oc, od;
-            uint32_t bc = range_interior(gc, clen, ac, oc);
-            uint32_t bd = range_interior(gd, dlen, ad, od);
             P.tile[s] = t;
             P.hc[s] = (uint32_t)((uintptr_t)gc & 15u);
             P.hd[s] = (uint32_t)((uintptr_t)gd & 15u);
-            mbar_arrive_expect_tx(&P.full[s], bc + bd);
-            if (bc)
-                bulk_g2s(P.ctrl[s] + oc, ac, bc, &P.full[s]);
-            if (bd)
-                bulk_g2s(P.data[s] + od, ad, bd, &P.full[s]);
+            mbar_arrive_expect_tx(&P.full[s], pc.bytes + pd.bytes);
+            if (pc.bytes)
+                bulk_g2s(P.ctrl[s] + pc.dst_off, pc.src, pc.bytes, &P.full[s]);
+            if (pd.bytes)
+                bulk_g2s(P.data[s] + pd.dst_off, pd.src, pd.bytes, &P.full[s]);
         } else {
             mbar_arrive(&P.full[s]);
         }
@@ -372,6 +376,7 @@ __device__ void consume(const TiledArgs &a, Pipe &P, uint16_t *s_pos)
         const u64 q0 = tile * kTileQuads + (u64)warp * kSubQuads;  // first quad of the sub-tile
         const u64 sb = tile * kSubs + warp;
         if (q0 >= a.nquads) {  // the last tile may have fewer sub-tiles
+            fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0)
                 mbar_arrive(&P.empty[s]);
@@ -463,6 +468,7 @@ __device__ void consume(const TiledArgs &a, Pipe &P, uint16_t *s_pos)
             v[r][3] = x.w;
         }
         // This warp no longer reads stage s.
+        fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0)
             mbar_arrive(&P.empty[s]);

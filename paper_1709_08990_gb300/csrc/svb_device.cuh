@@ -307,6 +307,15 @@ __device__ __forceinline__ void fence_mbar_init()
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// Orders this thread's earlier shared-memory accesses (generic proxy) before
+// later bulk-copy accesses (async proxy) that are ordered after it through an
+// mbarrier: a stage's readers issue it before they release the stage, so the
+// copy that refills the stage cannot overtake their loads.
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");

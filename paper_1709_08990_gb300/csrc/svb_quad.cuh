@@ -36,6 +36,36 @@ __device__ __forceinline__ void range_edges(const uint8_t *g, uint32_t len, uint
         base[h + i] = __ldg(g + i);
 }
 
+// How to stage global [g, g + len) so that byte g lands at smem base +
+// (g mod 16).  When the 16-byte-aligned range around it lies inside [lo, hi)
+// (the bytes the caller may read), one bulk copy of that whole range does it;
+// otherwise the aligned interior goes by bulk copy and the ragged ends (under
+// 16 bytes each) by plain loads (range_edges).
+struct StagePlan {
+    const uint8_t *src;
+    uint32_t dst_off;
+    uint32_t bytes;
+    bool edges;
+};
+
+__device__ __forceinline__ StagePlan stage_plan(const uint8_t *g, uint32_t len, const uint8_t *lo,
+                                                const uint8_t *hi)
+{
+    StagePlan p;
+    const uintptr_t s = (uintptr_t)g, e = s + len;
+    const uintptr_t o0 = s & ~(uintptr_t)15, o1 = (e + 15) & ~(uintptr_t)15;
+    if (len && o0 >= (uintptr_t)lo && o1 <= (uintptr_t)hi) {
+        p.src = reinterpret_cast<const uint8_t *>(o0);
+        p.dst_off = 0;
+        p.bytes = (uint32_t)(o1 - o0);
+        p.edges = false;
+    } else {
+        p.bytes = range_interior(g, len, p.src, p.dst_off);
+        p.edges = len != 0;
+    }
+    return p;
+}
+
 __device__ __forceinline__ uint32_t quad_count(uint32_t c, uint32_t nints)
 {
     return nints + __popc(c & 0x55u) + 2u * __popc(c & 0xAAu);

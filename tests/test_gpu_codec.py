@@ -249,3 +249,23 @@ def test_full_size_skewed_1g(variant):
     del d_x
     back = svb.decode(got, x.size, checked=False)
     assert np.array_equal(host_u32(back), x)
+
+
+@pytest.mark.parametrize("delta", [False, True])
+def test_repeated_runs_are_identical(delta, variant):
+    """Eight encodes and decodes of the same 2^27 integers in a row, each
+    against the oracle: a race between the readers of a shared-memory stage
+    and the bulk copy that refills it shows up as a rare, run-dependent
+    mismatch, so one run is not enough to rule it out."""
+    x = W.skewed_lengths(77, 1 << 27)
+    if delta:
+        x = np.cumsum(x.astype(np.uint64)).astype(np.uint32)
+    want = oracle.encode(x, delta=delta)
+    d_x = to_dev(x)
+    want_d = to_dev(want)
+    for _ in range(8):
+        got = svb.encode(d_x, delta=delta)
+        assert got.numel() == want.size
+        assert bool(torch.equal(got, want_d))
+        back = svb.decode(want_d, x.size, delta=delta, checked=False)
+        assert bool(torch.equal(back, d_x))
