@@ -184,82 +184,86 @@ __device__ __forceinline__ void fence_acq_rel_gpu()
 // sum, else the byte offsets), computed by one whole warp.  One round trip
 // inspects a window of 32 * kLookbackPerLane predecessors (lane l owns the
 // run of kLookbackPerLane tiles starting l * kLookbackPerLane tiles back,
-// nearest first); the window is summed up to its nearest published inclusive
-// prefix, or wholly, and then the next window is taken.  The tag loads of a
-// window are relaxed and independent, so they are in flight together; one
-// acquire fence after the window's tags are valid orders the value loads
+// nearest first).  Only the tiles nearer than the window's nearest published
+// inclusive prefix matter: while one of them has published nothing yet, those
+// (and only those) are polled again; then the window is summed up to that
+// prefix, or wholly when it holds none, and the next window is taken.  The
+// tag loads are relaxed and independent, so they are in flight together; one
+// acquire fence after the tags that matter are valid orders the value loads
 // after them (a release store of the tag, a relaxed load that sees it and an
-// acquire fence synchronise).  Every poll is bounded: after spin_limit polls
-// (backing off to ~0.25 us each), or as soon as another tile has raised an
-// error, it returns with ok = false and the caller records the failure.
+// acquire fence synchronise).  Every wait is bounded: after spin_limit polling
+// rounds (backing off to ~0.25 us each), or as soon as another tile has raised
+// an error, it returns with ok = false and the caller records the failure.
 template <bool kVal>
 __device__ u64 lookback(TileStatus *st, u64 tile, u64 etag, u64 spin_limit, WsHeader *hdr,
                         bool &ok)
 {
     constexpr int K = kLookbackPerLane;
+    constexpr int kWindow = 32 * K;
     const int lane = threadIdx.x & 31;
     u64 excl = 0;
     long long base = (long long)tile - 1;
+    u64 spins = 0;
     ok = true;
+    auto tag_of = [&](long long p) -> const u64 * {
+        return kVal ? &st[p].val_tag : &st[p].off_tag;
+    };
     for (;;) {
         u64 tags[K];
 #pragma unroll
         for (int j = 0; j < K; j++) {
-            long long p = base - (lane * K + j);
-            tags[j] = p >= 0 ? ld_relaxed(kVal ? &st[p].val_tag : &st[p].off_tag)
-                             : (etag | kFlagPrefix);
+            const long long p = base - (lane * K + j);
+            tags[j] = p >= 0 ? ld_relaxed(tag_of(p)) : (etag | kFlagPrefix);
         }
-        bool failed = false;
+        int ppos, npos;  // window positions of the nearest prefix / not-ready tile
+        for (;;) {
+            int pk = K, nk = K;
 #pragma unroll
-        for (int j = 0; j < K; j++) {
-            long long p = base - (lane * K + j);
-            u64 spins = 0;
-            while (!failed && p >= 0 &&
-                   ((tags[j] & ~3ull) != etag || (tags[j] & 3ull) == kFlagNone)) {
-                if (++spins > spin_limit || ((spins & 31) == 0 && error_raised(hdr))) {
-                    failed = true;
-                } else {
-                    if (spins > 4)
-                        __nanosleep(spins < 64 ? 32 : 256);
-                    tags[j] = ld_relaxed(kVal ? &st[p].val_tag : &st[p].off_tag);
-                }
+            for (int j = K - 1; j >= 0; j--) {
+                const bool ready = (tags[j] & ~3ull) == etag && (tags[j] & 3ull) != kFlagNone;
+                if (!ready)
+                    nk = j;
+                if (ready && (tags[j] & 3ull) == kFlagPrefix)
+                    pk = j;
             }
-        }
-        if (__any_sync(0xffffffffu, failed)) {
-            ok = false;
-            return 0;
+            const unsigned pm = __ballot_sync(0xffffffffu, pk < K);
+            const unsigned nm = __ballot_sync(0xffffffffu, nk < K);
+            const int pl = pm ? __ffs(pm) - 1 : 0, nl = nm ? __ffs(nm) - 1 : 0;
+            const int pk_l = __shfl_sync(0xffffffffu, pk, pl);
+            const int nk_l = __shfl_sync(0xffffffffu, nk, nl);
+            ppos = pm ? pl * K + pk_l : kWindow;
+            npos = nm ? nl * K + nk_l : kWindow;
+            if (npos > ppos || npos == kWindow)
+                break;  // every tile nearer than the prefix (or in the window) is ready
+            if (++spins > spin_limit || ((spins & 31) == 0 && error_raised(hdr))) {
+                ok = false;
+                return 0;
+            }
+            if (spins > 4)
+                __nanosleep(spins < 64 ? 32 : 256);
+#pragma unroll
+            for (int j = 0; j < K; j++) {
+                const long long p = base - (lane * K + j);
+                const bool ready = (tags[j] & ~3ull) == etag && (tags[j] & 3ull) != kFlagNone;
+                if (p >= 0 && !ready && lane * K + j < ppos)
+                    tags[j] = ld_relaxed(tag_of(p));
+            }
         }
         fence_acq_rel_gpu();
-        // Lane-local: sum up to and including this lane's nearest prefix.
-        u64 vals[K];
-        int stop = K;  // index of this lane's nearest prefix, K if none
-#pragma unroll
-        for (int j = K - 1; j >= 0; j--) {
-            long long p = base - (lane * K + j);
-            bool pre = p < 0 || (tags[j] & 3ull) == kFlagPrefix;
-            if (pre)
-                stop = j;
-        }
-#pragma unroll
-        for (int j = 0; j < K; j++) {
-            long long p = base - (lane * K + j);
-            vals[j] = 0;
-            if (j <= stop && p >= 0) {
-                bool pre = (tags[j] & 3ull) == kFlagPrefix;
-                vals[j] = ld_relaxed(kVal ? (pre ? &st[p].val_pre : &st[p].val_agg)
-                                          : (pre ? &st[p].off_pre : &st[p].off_agg));
-            }
-        }
         u64 sum = 0;
 #pragma unroll
-        for (int j = 0; j < K; j++)
-            sum += vals[j];
-        unsigned pm = __ballot_sync(0xffffffffu, stop < K);
-        int k = pm ? __ffs(pm) - 1 : 31;
-        excl += warp_sum64(lane <= k ? sum : 0ull);
-        if (pm)
+        for (int j = 0; j < K; j++) {
+            const long long p = base - (lane * K + j);
+            if (p >= 0 && lane * K + j <= ppos) {
+                const bool pre = (tags[j] & 3ull) == kFlagPrefix;
+                sum += ld_relaxed(kVal ? (pre ? &st[p].val_pre : &st[p].val_agg)
+                                       : (pre ? &st[p].off_pre : &st[p].off_agg));
+            }
+        }
+        excl += warp_sum64(sum);
+        if (ppos < kWindow)
             break;
-        base -= 32 * K;
+        base -= kWindow;
     }
     return kVal ? (excl & 0xffffffffull) : excl;
 }
@@ -353,6 +357,27 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
+// As mbar_wait_bounded, but each poll may suspend the thread for up to
+// `hint_ns` (it resumes as soon as the phase completes), so a long wait costs
+// few instructions.  At most limit * hint_ns in all.
+__device__ __forceinline__ bool mbar_wait_suspend(uint64_t *bar, uint32_t parity, u64 limit,
+                                                  uint32_t hint_ns)
+{
+    for (u64 i = 0; i < limit; i++) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+            : "memory");
+        if (ok)
+            return true;
+    }
+    return false;
+}
+
 // Barrier among the first `count` threads of the CTA (named barrier `id`).
 __device__ __forceinline__ void named_sync(int id, int count)
 {
@@ -368,6 +393,32 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
             "r"(smem_u32(dst)),
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// L2 eviction priority for a bulk copy's source lines.
+__device__ __forceinline__ uint64_t l2_policy_evict_last()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint64_t l2_policy_evict_first()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// bulk_g2s with an L2 cache policy for the source.
+__device__ __forceinline__ void bulk_g2s_hint(void *dst, const void *src, uint32_t bytes,
+                                              uint64_t *bar, uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
         : "memory");
 }
 

@@ -9,22 +9,23 @@
 //
 // The only serial dependency is where each sub-tile's data bytes go: the sum
 // of all earlier lengths.  Persistent CTAs claim chunks of kChunkTiles tiles
-// (64 sub-tiles of 512 values) in order, and the producer warp streams each
+// (32 sub-tiles of 512 values) in order, and the producer warp streams each
 // chunk's values in twice with bulk copies (cp.async.bulk, mbarrier
 // completion):
 //   sizing pass   each consumer warp sums the byte lengths of its sub-tile;
-//                 at the chunk's end warp 0 scans the 64 sizes and publishes
-//                 the chunk's aggregate for a decoupled look-back;
-//   writing pass  posted after the next chunk's sizing pass, so the look-back
-//                 (warp 0, just before it) usually finds its predecessors
-//                 done.  Each warp then forms its sub-tile's control bytes and
-//                 data bytes alone - warp scans and shuffles, no barrier with
-//                 the other warps - assembling the data word by word in its
-//                 own shared slice, phased like the destination, and storing
-//                 it with 16-byte writes (ragged ends byte by byte).
-// Consumers meet at two bounded barriers per chunk.  The second read of a
-// chunk comes from L2 (the chunks in flight on the whole GPU take far less
-// than its 129 MB), so DRAM sees each value once.
+//                 the chunk warp then scans the chunk's sub-tile sizes,
+//                 publishes its aggregate and finds its offset by decoupled
+//                 look-back, while the consumers size the next chunk;
+//   writing pass  each warp forms its sub-tile's control bytes and data bytes
+//                 alone - warp scans and shuffles, no barrier with the other
+//                 warps - assembling the data word by word in its own shared
+//                 slice, phased like the destination, and storing it with
+//                 16-byte writes (ragged ends byte by byte).
+// Consumers and the chunk warp hand chunks over through two mbarriers; the
+// chunk warp writes no output, so its release stores and fences do not wait
+// on data stores in flight.  The sizing read asks L2 to keep the values and
+// the writing read, one chunk later, takes them from there, so DRAM sees each
+// value once.
 #include <cuda_runtime.h>
 
 #include "svb_device.cuh"
@@ -36,18 +37,20 @@ namespace svb {
 constexpr int kEtQuads = 1024;                  // quads per tile (4096 values)
 constexpr int kEtSubs = kEtQuads / kSubQuads;   // sub-tiles per tile = consumer warps
 constexpr int kEtRounds = kSubQuads / 32;       // quads per lane per sub-tile
-constexpr int kChunkTiles = 8;                  // tiles per look-back unit
+constexpr int kChunkTiles = 4;                  // tiles per look-back unit
 constexpr int kChunkSubs = kChunkTiles * kEtSubs;
 constexpr int kEtStages = 3;
 constexpr int kEtStageBytes = 16 * kEtQuads + 16;
 constexpr int kEtSliceWords = (16 * kSubQuads + 32) / 4;   // one warp's data bytes + phase
-constexpr int kEtBlock = kThreads + 32;
-constexpr u64 kEtPolls = 1ull << 24;
+constexpr int kEtBlock = kThreads + 64;          // 8 consumer warps, producer, chunk warp
+constexpr u64 kEtPolls = 1ull << 24;            // bound on a busy-polled wait
+constexpr u64 kEtSuspends = 1ull << 18;         // bound on a suspending wait ...
+constexpr uint32_t kEtSuspendNs = 10000;        // ... of up to 10 us per poll (2.6 s in all)
 constexpr uint32_t kEtNone = 0xffffffffu;
 constexpr u64 kNoChunk = ~0ull;
 
 static_assert(kEtSubs == kWarps, "one consumer warp per sub-tile");
-static_assert(kChunkSubs == 64, "a chunk's sub-tile sizes are scanned two per lane");
+static_assert(kChunkSubs <= 32, "a chunk's sub-tile sizes are scanned one per lane");
 
 struct EncTiledArgs {
     const uint32_t *in;
@@ -66,20 +69,22 @@ struct EtPipe {
     uint32_t slice[kWarps][kEtSliceWords];   // each warp's data bytes, phased like the output
     uint64_t full[kEtStages];
     uint64_t empty[kEtStages];
-    uint64_t group;                          // consumer-warp barrier
+    uint64_t sizes_ready[2];    // consumers -> chunk warp: a chunk's sub-tile sizes are in
+    uint64_t base_ready[2];     // chunk warp -> consumers: the chunk's offsets are known
     uint32_t tile[kEtStages];   // tile index, or kEtNone
     uint32_t pass[kEtStages];   // 0 sizing, 1 writing
     uint32_t hv[kEtStages];     // phase (mod 16) of the staged values
 };
 
-// Per-chunk bookkeeping, double-buffered by the CTA's own chunk count: chunk
-// k is sized, then chunk k+1 is sized while chunk k's look-back result is
-// still pending, then chunk k is written.
+// Per-chunk bookkeeping, double-buffered by the CTA's own chunk count (the
+// k-th chunk uses buffer k & 1): chunk k is sized, then chunk k+1 is sized
+// while the chunk warp finds chunk k's offset, then chunk k is written.
 struct EtChunks {
     uint32_t size[2][kChunkSubs];   // data bytes of each sub-tile
     uint32_t excl[2][kChunkSubs];   // exclusive prefix inside the chunk
     uint32_t agg[2];
     u64 base[2];                    // the chunk's offset in the data stream
+    u64 chunk[2];                   // the chunk's index, kNoChunk once the work is out
 };
 
 // The producer warp claims chunks in order and posts, for each, its sizing
@@ -88,12 +93,14 @@ struct EtChunks {
 __device__ void et_produce(const EncTiledArgs &a, EtPipe &P, int lane)
 {
     uint32_t g = 0;
+    const uint64_t keep = l2_policy_evict_last(), keep_not = l2_policy_evict_first();
     const uint8_t *lo = reinterpret_cast<const uint8_t *>(a.in);
     const uint8_t *hi = lo + 4 * a.n;
     auto post = [&](uint32_t tile, uint32_t pass) -> bool {
         const int s = g % kEtStages;
         if (g >= (uint32_t)kEtStages) {
-            bool ok = mbar_wait_bounded(&P.empty[s], ((g / kEtStages) - 1) & 1u, kEtPolls);
+            bool ok = mbar_wait_suspend(&P.empty[s], ((g / kEtStages) - 1) & 1u, kEtSuspends,
+                                        kEtSuspendNs);
             if (!__all_sync(0xffffffffu, ok)) {
                 if (lane == 0)
                     raise_error(a.hdr, kErrTimeout);
@@ -119,8 +126,11 @@ __device__ void et_produce(const EncTiledArgs &a, EtPipe &P, int lane)
                 P.pass[s] = pass;
                 P.hv[s] = (uint32_t)((uintptr_t)gv & 15u);
                 mbar_arrive_expect_tx(&P.full[s], pv.bytes);
+                // The sizing read asks L2 to keep the lines for the writing
+                // read, which marks them first to go.
                 if (pv.bytes)
-                    bulk_g2s(P.vals[s] + pv.dst_off, pv.src, pv.bytes, &P.full[s]);
+                    bulk_g2s_hint(P.vals[s] + pv.dst_off, pv.src, pv.bytes, &P.full[s],
+                                  pass ? keep_not : keep);
             } else {
                 mbar_arrive(&P.full[s]);
             }
@@ -167,37 +177,34 @@ __device__ void et_produce(const EncTiledArgs &a, EtPipe &P, int lane)
     __syncwarp();
 }
 
-// Barrier of the eight consumer warps, bounded.
-__device__ __forceinline__ bool et_group_sync(EtPipe &P, uint32_t &phase)
+// L(v) - 1 (Sec. 3) with 0 -> 0: the index of the highest set bit over 8.
+__device__ __forceinline__ uint32_t extra_bytes(uint32_t v)
 {
-    __syncwarp();
-    if ((threadIdx.x & 31) == 0)
-        mbar_arrive(&P.group);
-    const bool ok = mbar_wait_bounded(&P.group, phase & 1u, kEtPolls);
-    phase++;
-    return __all_sync(0xffffffffu, ok);
+    return (31u - (uint32_t)__clz(v | 1u)) >> 3;
 }
 
-// Integers of quad q (tile-local lq): 4, fewer for the stream's last quad, 0
-// past the end.
-__device__ __forceinline__ uint32_t et_nints(const EncTiledArgs &a, u64 q0, uint32_t lq,
-                                             uint32_t nq, uint32_t last_nints)
-{
-    return lq >= nq ? 0u : (q0 + lq == a.nquads - 1 ? last_nints : 4u);
-}
-
-// The coded values of one warp's sub-tile: lane l holds quad sq0 + 32r + l in
-// round r.  Gaps for differential coding (the first gap from prev, Sec. 5);
-// 0 in every field past the end.
-__device__ __forceinline__ void et_load(const EncTiledArgs &a, const uint32_t *V, bool aligned,
-                                        u64 q0, uint32_t sq0, const uint32_t (&nints)[kEtRounds],
-                                        uint32_t (&d)[kEtRounds][4])
+// One warp's sub-tile, read from the staged tile: lane l holds quad
+// sq0 + 32r + l in round r.  For each quad: the integers it holds (4, fewer
+// for the stream's last quad, 0 past the end), the coded values (gaps for
+// differential coding, the first from prev, Sec. 5; 0 past the end), its
+// control byte and its data bytes.  kFast: all 128 quads hold 4 integers and
+// the staged values are 16-byte aligned.
+template <bool kFast>
+__device__ __forceinline__ void et_quads(const EncTiledArgs &a, const uint32_t *V, u64 q0,
+                                         uint32_t sq0, uint32_t nq, uint32_t last_nints,
+                                         uint32_t (&nints)[kEtRounds], uint32_t (&d)[kEtRounds][4],
+                                         uint32_t (&ctrl)[kEtRounds], uint32_t (&cb)[kEtRounds])
 {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int r = 0; r < kEtRounds; r++) {
         const uint32_t lq = sq0 + 32 * r + lane;
-        if (nints[r] == 4 && aligned) {
+        if (kFast) {
+            nints[r] = 4;
+        } else {
+            nints[r] = lq >= nq ? 0u : (q0 + lq == a.nquads - 1 ? last_nints : 4u);
+        }
+        if (kFast) {
             const uint4 v = *reinterpret_cast<const uint4 *>(V + 4 * lq);
             d[r][0] = v.x;
             d[r][1] = v.y;
@@ -226,13 +233,21 @@ __device__ __forceinline__ void et_load(const EncTiledArgs &a, const uint32_t *V
             d[r][0] = nints[r] > 0 ? x0 - pv : 0u;
         }
     }
+    // Fields past the end are 0 and add nothing.
+#pragma unroll
+    for (int r = 0; r < kEtRounds; r++) {
+        uint32_t c = 0, C = nints[r];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const uint32_t e = extra_bytes(d[r][j]);
+            c |= e << (2 * j);
+            C += e;
+        }
+        ctrl[r] = c;
+        cb[r] = C;
+    }
 }
 
-// L(v) - 1 (Sec. 3) with 0 -> 0: the index of the highest set bit over 8.
-__device__ __forceinline__ uint32_t extra_bytes(uint32_t v)
-{
-    return (31u - (uint32_t)__clz(v | 1u)) >> 3;
-}
 
 // 128-bit left shift of (s3:s2:s1:s0) by k in [0, 32] bits.
 __device__ __forceinline__ void shl128(uint32_t &s0, uint32_t &s1, uint32_t &s2, uint32_t &s3,
@@ -244,18 +259,16 @@ __device__ __forceinline__ void shl128(uint32_t &s0, uint32_t &s1, uint32_t &s2,
     s0 = __funnelshift_lc(0u, s0, k);
 }
 
-// Warp 0 at the end of a chunk's sizing tiles: prefix of the sub-tile sizes
-// and the chunk's aggregate, published for the look-back.
+// Chunk warp, once a chunk's sizing tiles are done: prefix of the sub-tile
+// sizes and the chunk's aggregate, published for the look-back.
 __device__ void et_chunk_scan(const EncTiledArgs &a, EtChunks &C, int b, u64 chunk, u64 etag)
 {
     const int lane = threadIdx.x & 31;
     const u64 tiles = min((u64)kChunkTiles, a.ntiles - chunk * kChunkTiles);
-    const uint32_t v0 = (u64)(2 * lane) / kEtSubs < tiles ? C.size[b][2 * lane] : 0u;
-    const uint32_t v1 = (u64)(2 * lane + 1) / kEtSubs < tiles ? C.size[b][2 * lane + 1] : 0u;
-    const uint32_t t = v0 + v1;
+    const uint32_t t = lane < kChunkSubs && (u64)lane / kEtSubs < tiles ? C.size[b][lane] : 0u;
     const uint32_t inc = warp_incl_scan(t);
-    C.excl[b][2 * lane] = inc - t;
-    C.excl[b][2 * lane + 1] = inc - t + v0;
+    if (lane < kChunkSubs)
+        C.excl[b][lane] = inc - t;
     const uint32_t agg = __shfl_sync(0xffffffffu, inc, 31);
     if (lane == 0) {
         C.agg[b] = agg;
@@ -267,7 +280,8 @@ __device__ void et_chunk_scan(const EncTiledArgs &a, EtChunks &C, int b, u64 chu
     }
 }
 
-// Warp 0 before a chunk's writing tiles: the chunk's offset in the data stream.
+// Chunk warp, right after: the chunk's offset in the data stream, by
+// decoupled look-back over the chunks claimed before it.
 __device__ void et_chunk_base(const EncTiledArgs &a, EtChunks &C, int b, u64 chunk, u64 etag)
 {
     const int lane = threadIdx.x & 31;
@@ -293,8 +307,9 @@ __device__ void et_chunk_base(const EncTiledArgs &a, EtChunks &C, int b, u64 chu
 // their destination (word by word: each lane shifts its quad's 4..16 bytes to
 // their byte position and writes the words it completes, taking the partial
 // first word from the previous lane), then copied out with 16-byte stores.
+template <bool kFast>
 __device__ __forceinline__ void et_write(const EncTiledArgs &a, uint32_t *slice, uint8_t *dst,
-                                         u64 q0, uint32_t sq0, uint32_t nvq,
+                                         u64 q0, uint32_t sq0, uint32_t nvq_any,
                                          const uint32_t (&nints)[kEtRounds],
                                          const uint32_t (&ctrl)[kEtRounds],
                                          const uint32_t (&cb)[kEtRounds],
@@ -302,6 +317,7 @@ __device__ __forceinline__ void et_write(const EncTiledArgs &a, uint32_t *slice,
 {
     const int lane = threadIdx.x & 31;
     const uint32_t h = (uint32_t)((uintptr_t)dst & 15u);
+    const uint32_t nvq = kFast ? (uint32_t)kSubQuads : nvq_any;
     uint32_t run = 0, carry = 0, fidx = kEtNone, fword = 0;
 #pragma unroll
     for (int r = 0; r < kEtRounds; r++) {
@@ -309,11 +325,12 @@ __device__ __forceinline__ void et_write(const EncTiledArgs &a, uint32_t *slice,
             break;
         const uint32_t lq = sq0 + 32 * r + lane;
         const uint32_t C = cb[r];
+        const uint32_t nint = kFast ? 4u : nints[r];
         uint32_t L[4];
 #pragma unroll
         for (int j = 0; j < 4; j++)
-            L[j] = (uint32_t)j < nints[r] ? ((ctrl[r] >> (2 * j)) & 3u) + 1 : 0u;
-        if (nints[r])
+            L[j] = (uint32_t)j < nint ? ((ctrl[r] >> (2 * j)) & 3u) + 1 : 0u;
+        if (nint)
             a.out[q0 + lq] = (uint8_t)ctrl[r];
         const uint32_t inc = warp_incl_scan(C);
         const uint32_t pos = h + run + inc - C;
@@ -376,46 +393,71 @@ __device__ __forceinline__ void et_write(const EncTiledArgs &a, uint32_t *slice,
     __syncwarp();
 }
 
+// The chunk warp: for each chunk of this CTA, in order, once the consumers
+// have sized it: scan, publish, look back, hand the offsets to the
+// consumers.  It writes no output, so its release stores and fences wait on
+// nothing but its own status records.
+__device__ void et_chunk_warp(const EncTiledArgs &a, EtPipe &P, EtChunks &C, u64 etag)
+{
+    const int lane = threadIdx.x & 31;
+    for (uint32_t k = 0;; k++) {
+        const int b = k & 1;
+        if (!mbar_wait_suspend(&P.sizes_ready[b], (k >> 1) & 1u, kEtSuspends, kEtSuspendNs)) {
+            if (lane == 0)
+                raise_error(a.hdr, kErrTimeout);
+            break;
+        }
+        const u64 chunk = C.chunk[b];
+        if (chunk == kNoChunk)
+            break;
+        et_chunk_scan(a, C, b, chunk, etag);
+        __syncwarp();
+        et_chunk_base(a, C, b, chunk, etag);
+        __syncwarp();
+        if (lane == 0)
+            mbar_arrive(&P.base_ready[b]);
+    }
+}
+
 __device__ void et_consume(const EncTiledArgs &a, EtPipe &P, EtChunks &C, u64 etag)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t last_nints = (uint32_t)(a.n - 4 * (a.nquads - 1));
     const uint32_t sq0 = warp * kSubQuads;
-    uint32_t sized = 0, written = 0, phase = 0;   // chunks this CTA has sized / written
+    uint32_t sized = 0, written = 0;   // chunks this CTA has sized / started writing
     for (uint32_t g = 0;; g++) {
         const int s = g % kEtStages;
-        if (!mbar_wait_bounded(&P.full[s], (g / kEtStages) & 1u, kEtPolls)) {
+        if (!mbar_wait_suspend(&P.full[s], (g / kEtStages) & 1u, kEtSuspends, kEtSuspendNs)) {
             if (lane == 0)
                 raise_error(a.hdr, kErrTimeout);
             break;
         }
         const uint32_t tile = P.tile[s];
-        if (tile == kEtNone)
+        if (tile == kEtNone) {
+            // Tell the chunk warp that no chunk follows.
+            const int b = sized & 1;
+            if (warp == 0 && lane == 0)
+                C.chunk[b] = kNoChunk;
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(&P.sizes_ready[b]);
             break;
+        }
         const uint32_t pass = P.pass[s];
         const u64 q0 = (u64)tile * kEtQuads;
         const uint32_t nq = (uint32_t)min((u64)kEtQuads, a.nquads - q0);
         const uint32_t nvq = nq > sq0 ? min(nq - sq0, (uint32_t)kSubQuads) : 0u;
         const uint32_t *V = reinterpret_cast<const uint32_t *>(P.vals[s] + P.hv[s]);
+        // Whole sub-tile of 512 integers, staged 16-byte aligned: no per-quad
+        // end checks.
+        const bool fast = P.hv[s] == 0 && 4 * (q0 + sq0 + kSubQuads) <= a.n;
         uint32_t nints[kEtRounds], d[kEtRounds][4], ctrl[kEtRounds], cb[kEtRounds];
-#pragma unroll
-        for (int r = 0; r < kEtRounds; r++)
-            nints[r] = et_nints(a, q0, sq0 + 32 * r + lane, nq, last_nints);
-        et_load(a, V, P.hv[s] == 0, q0, sq0, nints, d);
-        // Control byte and data bytes of each quad (fields past the end are 0
-        // and add nothing); they use every staged value this warp loaded.
-#pragma unroll
-        for (int r = 0; r < kEtRounds; r++) {
-            uint32_t c = 0, C = nints[r];
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                const uint32_t e = extra_bytes(d[r][j]);
-                c |= e << (2 * j);
-                C += e;
-            }
-            ctrl[r] = c;
-            cb[r] = C;
-        }
+        if (fast)
+            et_quads<true>(a, V, q0, sq0, nq, last_nints, nints, d, ctrl, cb);
+        else
+            et_quads<false>(a, V, q0, sq0, nq, last_nints, nints, d, ctrl, cb);
+        // The control bytes use every staged value this warp loaded, so its
+        // loads are complete; the fence orders them before the refill.
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0)
@@ -432,35 +474,35 @@ __device__ void et_consume(const EncTiledArgs &a, EtPipe &P, EtChunks &C, u64 et
             for (int k = 16; k >= 1; k >>= 1)
                 t += __shfl_xor_sync(0xffffffffu, t, k);
             const int b = sized & 1;
-            if (lane == 0)
+            if (lane == 0) {
                 C.size[b][ti * kEtSubs + warp] = t;
+                if (warp == 0 && ti == 0)
+                    C.chunk[b] = chunk;
+            }
             if (ti + 1 == kChunkTiles || tile + 1 == a.ntiles) {
                 sized++;
-                if (!et_group_sync(P, phase)) {
-                    if (lane == 0)
-                        raise_error(a.hdr, kErrTimeout);
-                    break;
-                }
-                if (warp == 0)
-                    et_chunk_scan(a, C, b, chunk, etag);
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(&P.sizes_ready[b]);
             }
             continue;
         }
 
         if (ti == 0)
             written++;
-        const int b = (written - 1) & 1;   // the same buffer for all tiles of the chunk
-        if (ti == 0) {
-            if (warp == 0)
-                et_chunk_base(a, C, b, chunk, etag);
-            if (!et_group_sync(P, phase)) {
-                if (lane == 0)
-                    raise_error(a.hdr, kErrTimeout);
-                break;
-            }
+        const uint32_t k = written - 1;   // this CTA's chunk count: buffer k & 1
+        const int b = k & 1;
+        if (ti == 0 &&
+            !mbar_wait_suspend(&P.base_ready[b], (k >> 1) & 1u, kEtSuspends, kEtSuspendNs)) {
+            if (lane == 0)
+                raise_error(a.hdr, kErrTimeout);
+            break;
         }
         uint8_t *dst = a.out + a.nquads + C.base[b] + C.excl[b][ti * kEtSubs + warp];
-        et_write(a, P.slice[warp], dst, q0, sq0, nvq, nints, ctrl, cb, d);
+        if (fast)
+            et_write<true>(a, P.slice[warp], dst, q0, sq0, nvq, nints, ctrl, cb, d);
+        else
+            et_write<false>(a, P.slice[warp], dst, q0, sq0, nvq, nints, ctrl, cb, d);
     }
 }
 
@@ -477,13 +519,18 @@ __global__ void __launch_bounds__(kEtBlock, 3) encode_tiled_kernel(EncTiledArgs 
             mbar_init(&P.full[s], 32);
             mbar_init(&P.empty[s], kWarps);
         }
-        mbar_init(&P.group, kWarps);
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&P.sizes_ready[b], kWarps);
+            mbar_init(&P.base_ready[b], 1);
+        }
         fence_mbar_init();
         s_etag = (ld_relaxed(&a.hdr->epoch) + 1) << 2;
     }
     __syncthreads();
     if (warp == kWarps)
         et_produce(a, P, lane);
+    else if (warp == kWarps + 1)
+        et_chunk_warp(a, P, s_chunks, s_etag);
     else
         et_consume(a, P, s_chunks, s_etag);
     finish_launch(a.hdr, a.result);
