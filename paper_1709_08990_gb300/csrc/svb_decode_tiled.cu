@@ -399,6 +399,34 @@ __device__ void consume(const TiledArgs &a, Pipe &P, uint16_t *s_pos)
                 if (4u * lane + j < nq)
                     w |= (uint32_t)C[4 * lane + j] << (8 * j);
         }
+        if (kMode == kSums && full && __all_sync(0xffffffffu, w == 0)) {
+            // All 512 integers take one byte (Sec. 4: an all-zero control byte
+            // covers 4 bytes): the gaps are the data bytes [base, base + 512).
+            // Sum them a word at a time, masking the bytes outside the range.
+            const uint32_t *Wd = reinterpret_cast<const uint32_t *>(D);
+            const uint32_t b0 = base >> 2, b1 = (base + 4 * kSubQuads + 3) >> 2;
+            const uint32_t head = base & 3u, tail = (base + 4 * kSubQuads) & 3u;
+            uint32_t t = 0;
+            for (uint32_t i = b0 + lane; i < b1; i += 32) {
+                uint32_t x = Wd[i];
+                if (i == b0)
+                    x &= 0xffffffffu << (8 * head);
+                if (i == b1 - 1 && tail)
+                    x &= 0xffffffffu >> (8 * (4 - tail));
+                const uint32_t y = (x & 0x00ff00ffu) + ((x >> 8) & 0x00ff00ffu);
+                t += (y & 0xffffu) + (y >> 16);
+            }
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(&P.empty[s]);
+#pragma unroll
+            for (int d = 16; d >= 1; d >>= 1)
+                t += __shfl_xor_sync(0xffffffffu, t, d);
+            if (lane == 0)
+                a.carries[sb] = t;
+            continue;
+        }
         uint32_t o1, o2, o3, tsum;
         if (full) {
             // Byte j of cs = sum of the four codes of quad j; the multiply turns
@@ -522,48 +550,46 @@ __device__ void consume(const TiledArgs &a, Pipe &P, uint16_t *s_pos)
     }
 }
 
-// kSums epilogue: turn this CTA's sub-tile gap sums into carries.  Scans the
-// range's sums in order (relative carries), chains the range total with the
-// ranges before by one look-back, then adds the base (prev for the first).
-__device__ void sums_to_carries(const TiledArgs &a, u64 first, u64 etag, uint32_t *s_base)
+// kSums epilogue, warp 0: turn this CTA's sub-tile gap sums into carries.
+// Each lane takes a contiguous run of the range's sums (its loads all in
+// flight at once), the lane totals are scanned, the range total is chained
+// with the ranges before by one look-back (prev starts the first range), and
+// each lane writes its run's carries.
+__device__ void sums_to_carries(const TiledArgs &a, u64 first, u64 etag)
 {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int lane = threadIdx.x & 31;
     const u64 s0 = first * kSubs;
     const u64 s1 = min(min(first + a.per_cta, a.ntiles) * kSubs, a.nsubs);
-    if (warp == 0) {
-        uint32_t run = 0;
-        for (u64 b = s0; b < s1; b += 32) {
-            const u64 i = b + lane;
-            const uint32_t v = i < s1 ? a.carries[i] : 0u;
-            const uint32_t inc = warp_incl_scan(v);
-            if (i < s1)
-                a.carries[i] = run + inc - v;
-            run += __shfl_sync(0xffffffffu, inc, 31);
-        }
-        const u64 cta = first / (a.per_cta ? a.per_cta : 1);
-        TileStatus *me = &a.st[cta];
-        u64 base = a.prev;
-        bool ok = true;
-        if (cta == 0) {
-            if (lane == 0)
-                publish(&me->val_tag, &me->val_pre, (uint32_t)(a.prev + run), kFlagPrefix, etag);
-        } else {
-            if (lane == 0)
-                publish(&me->val_tag, &me->val_agg, run, kFlagAgg, etag);
-            base = lookback<true>(a.st, cta, etag, a.spin_limit, a.hdr, ok);
-            if (ok && lane == 0)
-                publish(&me->val_tag, &me->val_pre, (uint32_t)(base + run), kFlagPrefix, etag);
-        }
-        if (lane == 0) {
-            if (!ok)
-                raise_error(a.hdr, kErrTimeout);
-            *s_base = (uint32_t)base;
-        }
+    const u64 per = (s1 - s0 + 31) / 32;
+    const u64 b = min(s0 + lane * per, s1), e = min(b + per, s1);
+    uint32_t tot = 0;
+#pragma unroll 4
+    for (u64 i = b; i < e; i++)
+        tot += a.carries[i];
+    const uint32_t inc = warp_incl_scan(tot);
+    const uint32_t run = __shfl_sync(0xffffffffu, inc, 31);
+    const u64 cta = first / (a.per_cta ? a.per_cta : 1);
+    TileStatus *me = &a.st[cta];
+    u64 base = a.prev;
+    bool ok = true;
+    if (cta == 0) {
+        if (lane == 0)
+            publish(&me->val_tag, &me->val_pre, (uint32_t)(a.prev + run), kFlagPrefix, etag);
+    } else {
+        if (lane == 0)
+            publish(&me->val_tag, &me->val_agg, run, kFlagAgg, etag);
+        base = lookback<true>(a.st, cta, etag, a.spin_limit, a.hdr, ok);
+        if (ok && lane == 0)
+            publish(&me->val_tag, &me->val_pre, (uint32_t)(base + run), kFlagPrefix, etag);
     }
-    named_sync(1, kThreads);
-    const uint32_t base = *s_base;
-    for (u64 i = s0 + tid; i < s1; i += kThreads)
-        a.carries[i] += base;
+    if (!ok && lane == 0)
+        raise_error(a.hdr, kErrTimeout);
+    uint32_t c = (uint32_t)base + inc - tot;
+    for (u64 i = b; i < e; i++) {
+        const uint32_t v = a.carries[i];
+        a.carries[i] = c;
+        c += v;
+    }
 }
 
 template <int kMode>
@@ -573,7 +599,7 @@ __global__ void __launch_bounds__(kDecBlock, 3) decode_tiled_kernel(TiledArgs a)
     Pipe &P = *reinterpret_cast<Pipe *>(dyn_smem);
     __shared__ __align__(16) uint16_t s_pos[kTileQuads];
     __shared__ u64 s_etag, s_first;
-    __shared__ uint32_t s_flag, s_base;
+    __shared__ uint32_t s_flag;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
@@ -597,7 +623,8 @@ __global__ void __launch_bounds__(kDecBlock, 3) decode_tiled_kernel(TiledArgs a)
             consume<kMode>(a, P, s_pos);
             if (kMode == kSums) {
                 named_sync(1, kThreads);  // every sub-tile sum of the range is written
-                sums_to_carries(a, s_first, s_etag, &s_base);
+                if (warp == 0)
+                    sums_to_carries(a, s_first, s_etag);
             }
         }
     }
