@@ -11,6 +11,11 @@ Every function here is pinned by the ``-m "not gpu"`` tests: the paper's
 worked byte examples (Fig. 1, Fig. 3), its prefix-sum example (Sec. 2), the
 length boundaries (Sec. 3), the size formula (Sec. 4), brute force over all
 length patterns for n <= 12, and an independently written Python definition.
+
+``vbyte_ref.c`` (the ``VByte`` class) states the VByte format the paper
+compares Stream VByte with (Sec. 2-3), for the size comparison of Sec. 5
+(Fig. 5b); its pins are the paper's two byte examples (32, 128), the 7-bit
+length boundaries, the decoding sum of Sec. 3 and the Python definition.
 """
 from __future__ import annotations
 
@@ -24,6 +29,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "svb_ref.c")
 LIB = os.path.join(HERE, "libsvb_ref.so")
 
+VSRC = os.path.join(HERE, "vbyte_ref.c")
+VLIB = os.path.join(HERE, "libvbyte_ref.so")
+
 ERROR = (1 << 64) - 1  # SVB_REF_ERROR, (size_t)-1
 
 
@@ -33,10 +41,11 @@ def build_cmd(src: str = SRC, out: str = LIB) -> list[str]:
 
 
 def build() -> None:
-    """Compile the oracle if its library is missing or older than its source."""
-    if os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
-        return
-    subprocess.run(build_cmd(), check=True)
+    """Compile the oracle libraries that are missing or older than their source."""
+    for src, lib in ((SRC, LIB), (VSRC, VLIB)):
+        if os.path.exists(lib) and os.path.getmtime(lib) >= os.path.getmtime(src):
+            continue
+        subprocess.run(build_cmd(src, lib), check=True)
 
 
 class Codec:
@@ -109,7 +118,59 @@ class Codec:
         return self.lib.svb_ref_data_bytes(ctrl.ctypes.data, n)
 
 
+class VByte:
+    """The VByte oracle's entry points, bound to one build of ``vbyte_ref.c``."""
+
+    def __init__(self, path: str = VLIB):
+        L = ctypes.CDLL(path)
+        sz, u32, vp, i32 = ctypes.c_size_t, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_int
+        L.vbyte_ref_length.argtypes = [u32]
+        L.vbyte_ref_length.restype = ctypes.c_uint
+        L.vbyte_ref_size.argtypes = [vp, sz, i32, u32]
+        L.vbyte_ref_size.restype = sz
+        L.vbyte_ref_encode.argtypes = [vp, sz, vp, i32, u32]
+        L.vbyte_ref_encode.restype = sz
+        L.vbyte_ref_decode.argtypes = [vp, sz, sz, vp, i32, u32]
+        L.vbyte_ref_decode.restype = sz
+        self.lib = L
+        self.path = path
+
+    def length(self, v: int) -> int:
+        return self.lib.vbyte_ref_length(v & 0xFFFFFFFF)
+
+    def size(self, x, prev: int = 0, delta: bool = False) -> int:
+        x = np.ascontiguousarray(x, dtype=np.uint32)
+        buf = x if x.size else np.zeros(1, dtype=np.uint32)
+        return self.lib.vbyte_ref_size(buf.ctypes.data, x.size, int(delta), prev & 0xFFFFFFFF)
+
+    def encode(self, x, prev: int = 0, delta: bool = False) -> np.ndarray:
+        x = np.ascontiguousarray(x, dtype=np.uint32)
+        buf = x if x.size else np.zeros(1, dtype=np.uint32)
+        out = np.zeros(max(1, 5 * x.size), dtype=np.uint8)
+        k = self.lib.vbyte_ref_encode(buf.ctypes.data, x.size, out.ctypes.data, int(delta),
+                                      prev & 0xFFFFFFFF)
+        return out[:k].copy()
+
+    def decode(self, stream, n: int, prev: int = 0, delta: bool = False):
+        """(decoded uint32 array, bytes consumed or ERROR)."""
+        stream = np.ascontiguousarray(stream, dtype=np.uint8)
+        buf = stream if stream.size else np.zeros(1, dtype=np.uint8)
+        out = np.zeros(max(1, n), dtype=np.uint32)
+        k = self.lib.vbyte_ref_decode(buf.ctypes.data, stream.size, n, out.ctypes.data,
+                                      int(delta), prev & 0xFFFFFFFF)
+        return out[:n], k
+
+
 _default: Codec | None = None
+_vbyte: VByte | None = None
+
+
+def vbyte() -> VByte:
+    global _vbyte
+    if _vbyte is None:
+        build()
+        _vbyte = VByte(VLIB)
+    return _vbyte
 
 
 def codec() -> Codec:

@@ -225,3 +225,90 @@ ALL = [fig3_stream, fig1_blocks, sec2_prefix_sum, zero_control, control_range,
 
 def run_all(c) -> dict[str, list[str]]:
     return {f.__name__: f(c) for f in ALL}
+
+
+# --- VByte oracle pins (Sec. 2-3) -------------------------------------------
+
+def vbyte_paper_examples(v) -> list[str]:
+    """Sec. 2: 32 is one byte 00100000, 128 is 10000000 00000001."""
+    g = _read_golden("vbyte_examples.txt")
+    errs = []
+    for line in g["example"]:
+        val, hexes = line.split("=")
+        val = int(val)
+        want = bytes(int(b, 16) for b in hexes.split())
+        got = v.encode(np.array([val], dtype=np.uint32)).tobytes()
+        if got != want:
+            errs.append(f"vbyte {val}: {got.hex()} != {want.hex()}")
+        back, k = v.decode(np.frombuffer(want, dtype=np.uint8), 1)
+        if k != len(want) or int(back[0]) != val:
+            errs.append(f"vbyte decode of {want.hex()}: {back.tolist()} consumed {k}")
+    return errs
+
+
+def vbyte_length_boundaries(v) -> list[str]:
+    """Sec. 3: lengths change at 2^7, 2^14, 2^21, 2^28 (five bytes above),
+    in every position of a stream."""
+    errs = []
+    edges = [0, 1]
+    for e in (7, 14, 21, 28):
+        edges += [(1 << e) - 1, 1 << e]
+    edges.append((1 << 32) - 1)
+    for x in edges:
+        want = D.vbyte_length(x)
+        if v.length(x) != want:
+            errs.append(f"vbyte length({x}) = {v.length(x)}, want {want}")
+    rng = np.random.default_rng(21)
+    for pos in range(4):
+        for x in edges:
+            vals = rng.integers(0, 128, 4).astype(np.uint32)
+            vals[pos] = x
+            s = v.encode(vals)
+            want = sum(D.vbyte_length(int(t)) for t in vals)
+            if s.size != want or v.size(vals) != want:
+                errs.append(f"vbyte size with {x} at {pos}: {s.size}/{v.size(vals)}, want {want}")
+    return errs
+
+
+def vbyte_definition_agrees(v, seed: int = 22) -> list[str]:
+    """Bytes, sizes and values equal those of the Python definition."""
+    rng = np.random.default_rng(seed)
+    errs = []
+    for n in (1, 2, 3, 5, 17, 200):
+        for delta in (False, True):
+            bits = rng.integers(0, 33, n)
+            x = (rng.integers(0, 1 << 32, n, dtype=np.uint64) >> (32 - bits).astype(np.uint64))
+            x = x.astype(np.uint32)
+            prev = int(rng.integers(0, 1 << 32))
+            want = D.vbyte_encode([int(t) for t in x], prev, delta)
+            got = v.encode(x, prev, delta).tobytes()
+            if got != want:
+                errs.append(f"vbyte n={n} delta={delta}: bytes differ")
+            if v.size(x, prev, delta) != len(want):
+                errs.append(f"vbyte n={n} delta={delta}: size {v.size(x, prev, delta)}")
+            back, k = v.decode(np.frombuffer(want, dtype=np.uint8), n, prev, delta)
+            if k != len(want) or back.tolist() != D.vbyte_decode(want, n, prev, delta) \
+                    or back.tolist() != x.tolist():
+                errs.append(f"vbyte n={n} delta={delta}: decode differs")
+    return errs
+
+
+def vbyte_truncation(v) -> list[str]:
+    """A stream that ends inside an integer, or an integer over more than
+    five bytes (no 32-bit value needs six), is rejected."""
+    import oracle
+    errs = []
+    s = v.encode(np.array([1, 300, 1 << 30], dtype=np.uint32))
+    for cut in range(s.size):
+        _, k = v.decode(s[:cut], 3)
+        if k != oracle.ERROR:
+            errs.append(f"vbyte truncated at {cut}: consumed {k}")
+    _, k = v.decode(np.array([0x80] * 5 + [0x01], dtype=np.uint8), 1)
+    if k != oracle.ERROR:
+        errs.append("vbyte six-byte integer accepted")
+    return errs
+
+
+def run_all_vbyte(v) -> dict[str, list[str]]:
+    return {f.__name__: f(v) for f in (vbyte_paper_examples, vbyte_length_boundaries,
+                                       vbyte_definition_agrees, vbyte_truncation)}

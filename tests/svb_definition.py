@@ -56,3 +56,46 @@ def decode(stream: bytes, n: int, prev: int = 0, delta: bool = False):
     if delta:
         vals = [(prev + s) & M32 for s in accumulate(vals)]
     return vals, pos
+
+
+# --- VByte (Sec. 2-3), stated with divmod by 128 and bit_length -------------
+
+def vbyte_length(v: int) -> int:
+    """Sec. 3: an integer in [2^(7(L-1)), 2^(7L)) takes L bytes; zero one."""
+    return max(1, -(-v.bit_length() // 7))
+
+
+def vbyte_encode(xs: list[int], prev: int = 0, delta: bool = False) -> bytes:
+    """Sec. 2: seven bits per byte from the least significant end; a byte's
+    top bit says that the next byte continues the integer."""
+    if delta:
+        before = [prev] + list(xs[:-1])
+        vals = [(x - p) & M32 for x, p in zip(xs, before)]
+    else:
+        vals = [x & M32 for x in xs]
+    out = bytearray()
+    for v in vals:
+        while True:
+            v, group = divmod(v, 128)
+            out.append(group + (128 if v else 0))
+            if not v:
+                break
+    return bytes(out)
+
+
+def vbyte_decode(stream: bytes, n: int, prev: int = 0, delta: bool = False) -> list[int]:
+    """Sec. 3: the value is the sum of (b_i mod 2^7) * 2^(7i) over its bytes,
+    the last of which is below 2^7."""
+    vals, i = [], 0
+    for _ in range(n):
+        parts = []
+        while True:
+            b = stream[i]
+            i += 1
+            parts.append(b % 128)
+            if b < 128:
+                break
+        vals.append(sum(p * 128 ** k for k, p in enumerate(parts)) & M32)
+    if delta:
+        return [(prev + s) & M32 for s in accumulate(vals)]
+    return vals
