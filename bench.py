@@ -405,9 +405,31 @@ def time_encode(svb, W, name, dev, peaks, h_x):
     alg = 4 * n + size
     out = {"gints_per_s": n / ms / 1e6, "ms": ms, "frac": alg / (ms / 1e3) / 1e9 / peaks["hbm_gbs"],
            "alg_bytes": alg}
-    del d_x, d_s, ws
+    del d_s, ws
+    torch.cuda.empty_cache()
+    out["size_report"] = time_size_report(svb, d_x, delta, peaks)
+    # The paper's reference line: copying the uncompressed integers (memcpy).
+    d_y = torch.empty_like(d_x)
+    ms_c = _time(lambda: d_y.copy_(d_x), 20, stream)
+    out["memcpy_4n"] = {"gints_per_s": n / ms_c / 1e6, "ms": ms_c,
+                        "gb_per_s": 8 * n / (ms_c / 1e3) / 1e9}
+    del d_x, d_y
     torch.cuda.empty_cache()
     return out
+
+
+def time_size_report(svb, d_x, delta, peaks):
+    """Stream VByte and VByte sizes (Sec. 5, Fig. 5b) of the resident values,
+    and the size kernel's own read bandwidth (4n bytes per call)."""
+    import torch
+    n = d_x.numel()
+    s_svb, s_vb = svb.size_report(d_x, delta=delta)
+    d = torch.zeros(2, dtype=torch.int64, device=d_x.device)
+    stream = torch.cuda.current_stream()
+    ms = _time(lambda: svb.svb_size_report_async(d_x, n, 0, int(delta), d, stream), 50, stream)
+    return {"svb_bits_per_int": 8.0 * s_svb / n, "vbyte_bits_per_int": 8.0 * s_vb / n,
+            "extra_bits_per_int": 8.0 * (s_svb - s_vb) / n, "ms": ms,
+            "frac": 4 * n / (ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
 
 
 def time_codec(svb, W, name, dev, peaks):
@@ -432,7 +454,10 @@ def time_codec(svb, W, name, dev, peaks):
     ok = torch.equal(d_o, d_x)
     alg = 4 * n + size
     hb = peaks["hbm_gbs"]
+    s_svb, s_vb = svb.size_report(d_x, delta=w.delta)
     return {"n": n, "delta": w.delta, "stream_bytes": size, "verified": bool(ok),
+            "bits_per_int": {"svb": 8.0 * s_svb / n, "vbyte": 8.0 * s_vb / n,
+                             "extra": 8.0 * (s_svb - s_vb) / n},
             "decode": {"gints_per_s": n / ms_d / 1e6, "us": ms_d * 1e3,
                        "frac": alg / (ms_d / 1e3) / 1e9 / hb},
             "encode": {"gints_per_s": n / ms_e / 1e6, "us": ms_e * 1e3,

@@ -263,6 +263,26 @@ int svb_batch_encode(const void *d_plan, const svb_list *d_lists, const uint32_t
 size_t svb_decode_noalloc(const uint8_t *in, size_t in_len, size_t n, uint32_t *out,
                           uint32_t prev, int delta, svb_stream_t stream);
 
+/* ---- compressed-size report: Stream VByte against VByte ------------------ */
+
+/* Sizes of n integers coded two ways, without writing either stream (Sec. 5,
+ * Fig. 5b: the extra bits per integer of Stream VByte over VByte):
+ *   sizes[0]  Stream VByte bytes: ceil(n/4) control bytes plus L(v) =
+ *             max(1, ceil(bits(v)/8)) data bytes per coded value (Sec. 3-4);
+ *   sizes[1]  VByte bytes: max(1, ceil(bits(v)/7)) per coded value, seven
+ *             data bits and one continuation bit per byte (Sec. 2-3).
+ * The coded values are the integers, or with delta != 0 their differences
+ * x_i - x_{i-1} mod 2^32 with x_{-1} = prev (Sec. 1, Sec. 5).
+ * in: device array of n uint32 (any alignment; 16-byte aligned is faster).
+ * svb_size_report writes the two sizes to the host array `sizes`, running on
+ * the current stream and waiting for it; svb_size_report_async writes them to
+ * the device array d_sizes (two uint64) on `stream` and returns at once.
+ * Both return SVB_OK, SVB_EINVAL (null sizes, or null in with n > 0) or
+ * SVB_ECUDA / SVB_ENOMEM, also left in svb_last_error().  n = 0 gives 0, 0. */
+int svb_size_report(const uint32_t *in, size_t n, uint32_t prev, int delta, uint64_t *sizes);
+int svb_size_report_async(const uint32_t *in, size_t n, uint32_t prev, int delta,
+                          uint64_t *d_sizes, svb_stream_t stream);
+
 /* ---- test hook ---------------------------------------------------------- */
 
 /* Failure-detection check: launches one decode tile whose predecessor is

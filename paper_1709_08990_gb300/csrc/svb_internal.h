@@ -43,6 +43,10 @@ size_t batch_plan_bytes(size_t num_lists);
 int build_batch_plan(const svb_list *h_lists, size_t num_lists, uint32_t threshold, void *d_plan,
                      cudaStream_t stream);
 
+// Stream VByte and VByte sizes of n values into d_sizes[0..2) (svb_size.cu).
+int launch_size_report(const uint32_t *in, u64 n, uint32_t prev, bool delta, u64 *d_sizes,
+                       cudaStream_t stream);
+
 // Per-kernel CUDA-event timing (svb_profile.cu); no-ops unless profiling is on.
 void prof_begin(const char *name, cudaStream_t s);
 void prof_end(cudaStream_t s);

@@ -63,6 +63,8 @@ def lib() -> ctypes.CDLL:
             "svb_decode_async": ([vp, sz, sz, vp, u32, i32, vp, vp, sz, vp], i32),
             "svb_testhook_lookback_timeout": ([vp, sz, vp, u64, vp, vp, sz, vp], i32),
             "svb_decode_noalloc": ([vp, sz, sz, vp, u32, i32, vp], sz),
+            "svb_size_report": ([vp, sz, u32, i32, vp], i32),
+            "svb_size_report_async": ([vp, sz, u32, i32, vp, vp], i32),
             "svb_batch_plan_bytes": ([sz], sz),
             "svb_profile_begin": ([], i32),
             "svb_profile_end": ([ctypes.c_char_p, sz], sz),
@@ -252,6 +254,26 @@ def profile_end() -> dict:
 
 
 SVB_NOALLOC_MAX_N = 1 << 24
+
+
+def svb_size_report(inp, n: int, prev: int, delta: int, sizes) -> int:
+    """sizes: a writable host buffer of two uint64 (numpy array)."""
+    return lib().svb_size_report(_p(inp), n, prev & 0xFFFFFFFF, int(delta), _p(sizes))
+
+
+def svb_size_report_async(inp, n: int, prev: int, delta: int, d_sizes, stream=None) -> int:
+    return lib().svb_size_report_async(_p(inp), n, prev & 0xFFFFFFFF, int(delta), _p(d_sizes),
+                                       _stream(stream))
+
+
+def size_report(x, delta: bool = False, prev: int = 0) -> tuple[int, int]:
+    """(Stream VByte bytes, VByte bytes) of a CUDA tensor of 4-byte integers."""
+    import numpy as np
+    sizes = np.zeros(2, dtype=np.uint64)
+    st = svb_size_report(x, x.numel(), prev, int(delta), sizes)
+    if st != 0:
+        raise SvbError(st, "svb_size_report")
+    return int(sizes[0]), int(sizes[1])
 
 
 def svb_decode_noalloc(inp, in_len: int, n: int, out, prev: int, delta: int, stream=None) -> int:
