@@ -70,6 +70,10 @@ class Codec:
         L.svb_ref_delta_decode.restype = sz
         L.svb_ref_data_bytes.argtypes = [vp, sz]
         L.svb_ref_data_bytes.restype = sz
+        L.svb_ref_seek.argtypes = [vp, sz, sz, u32, ctypes.c_int, u32, ctypes.POINTER(u32)]
+        L.svb_ref_seek.restype = sz
+        L.svb_ref_select.argtypes = [vp, sz, sz, u32, ctypes.c_int, sz, ctypes.POINTER(u32)]
+        L.svb_ref_select.restype = sz
         self.lib = L
         self.path = path
 
@@ -112,6 +116,29 @@ class Codec:
         else:
             k = self.lib.svb_ref_decode(buf.ctypes.data, in_len, n, out.ctypes.data)
         return out[:n], k
+
+    def seek(self, stream, n: int, target: int, prev: int = 0, delta: bool = False,
+             in_len: int | None = None) -> tuple[int, int]:
+        """(index of the first integer >= target or n, that integer or 0);
+        index is ERROR when the stream ends before the answer is decided."""
+        stream = np.ascontiguousarray(stream, dtype=np.uint8)
+        buf = stream if stream.size else np.zeros(1, dtype=np.uint8)
+        v = ctypes.c_uint32(0)
+        k = self.lib.svb_ref_seek(buf.ctypes.data, stream.size if in_len is None else in_len,
+                                  n, prev & 0xFFFFFFFF, int(delta), target & 0xFFFFFFFF,
+                                  ctypes.byref(v))
+        return k, v.value
+
+    def select(self, stream, n: int, index: int, prev: int = 0, delta: bool = False,
+               in_len: int | None = None) -> int | None:
+        """The integer at `index`, or None when index >= n or the stream ends
+        before it."""
+        stream = np.ascontiguousarray(stream, dtype=np.uint8)
+        buf = stream if stream.size else np.zeros(1, dtype=np.uint8)
+        v = ctypes.c_uint32(0)
+        k = self.lib.svb_ref_select(buf.ctypes.data, stream.size if in_len is None else in_len,
+                                    n, prev & 0xFFFFFFFF, int(delta), index, ctypes.byref(v))
+        return None if k == ERROR else v.value
 
     def data_bytes(self, ctrl, n: int) -> int:
         ctrl = np.ascontiguousarray(ctrl, dtype=np.uint8)

@@ -176,3 +176,68 @@ size_t svb_ref_data_bytes(const uint8_t *ctrl, size_t n)
         total += ((ctrl[i / 4] >> (2 * (i % 4))) & 3u) + 1;
     return total;
 }
+
+/* Seek and select on a compressed array (the operations benchmarked at the
+ * end of Sec. 5, Fig. 6): both read the integers in order exactly as
+ * decode_stream does - code, then length-many little-endian bytes, then the
+ * running sum for differential coding - and stop at the answer.
+ *
+ *   seek(target)  the index of the first integer >= target, with that
+ *                 integer in *value; n (and *value = 0) when there is none;
+ *   select(i)     the integer at index i (i < n) in *value, returning 0.
+ *
+ * All ceil(n/4) control bytes must be present.  Either returns SVB_REF_ERROR
+ * when the data stream ends before the integer that decides the answer
+ * (for seek without a match, before the last integer), and select does so
+ * for i >= n. */
+size_t svb_ref_seek(const uint8_t *in, size_t in_len, size_t n, uint32_t prev,
+                    int delta, uint32_t target, uint32_t *value)
+{
+    *value = 0;
+    size_t nctrl = svb_ref_control_bytes(n);
+    if (in_len < nctrl)
+        return SVB_REF_ERROR;
+    size_t pos = nctrl;
+    uint32_t run = prev;
+    for (size_t i = 0; i < n; i++) {
+        unsigned len = ((in[i / 4] >> (2 * (i % 4))) & 3u) + 1;
+        if (len > in_len - pos)
+            return SVB_REF_ERROR;
+        uint32_t v = 0;
+        for (unsigned b = 0; b < len; b++)
+            v |= (uint32_t)in[pos + b] << (8 * b);
+        pos += len;
+        if (delta) {
+            run += v;
+            v = run;
+        }
+        if (v >= target) {
+            *value = v;
+            return i;
+        }
+    }
+    return n;
+}
+
+size_t svb_ref_select(const uint8_t *in, size_t in_len, size_t n, uint32_t prev,
+                      int delta, size_t index, uint32_t *value)
+{
+    *value = 0;
+    size_t nctrl = svb_ref_control_bytes(n);
+    if (index >= n || in_len < nctrl)
+        return SVB_REF_ERROR;
+    size_t pos = nctrl;
+    uint32_t run = prev;
+    for (size_t i = 0; i <= index; i++) {
+        unsigned len = ((in[i / 4] >> (2 * (i % 4))) & 3u) + 1;
+        if (len > in_len - pos)
+            return SVB_REF_ERROR;
+        uint32_t v = 0;
+        for (unsigned b = 0; b < len; b++)
+            v |= (uint32_t)in[pos + b] << (8 * b);
+        pos += len;
+        run = delta ? run + v : v;
+    }
+    *value = run;
+    return 0;
+}

@@ -218,9 +218,94 @@ def nonminimal_codes(c) -> list[str]:
     return []
 
 
+def _paper_query_list(rng, bits: int, n: int = 256) -> np.ndarray:
+    """The setup of Sec. 5's seek/select test: n random deltas in [0, 2^b),
+    prefix-summed."""
+    d = rng.integers(0, 1 << bits, n, dtype=np.uint64)
+    return (np.cumsum(d) & 0xFFFFFFFF).astype(np.uint32)
+
+
+def seek_matches_searchsorted(c, seed: int = 31) -> list[str]:
+    """Seek on sorted, differentially coded lists (Sec. 5, Fig. 6a) returns
+    numpy's left insertion point and the integer there."""
+    rng = np.random.default_rng(seed)
+    errs = []
+    for bits in (1, 4, 8, 12, 20, 24):
+        x = _paper_query_list(rng, bits)
+        s = c.encode(x, delta=True)
+        targets = [0, int(x[0]), int(x[-1]), int(x[-1]) + 1, (1 << 32) - 1]
+        targets += rng.integers(0, int(x[-1]) + 2, 40).tolist()
+        for t in targets:
+            t &= 0xFFFFFFFF
+            want = int(np.searchsorted(x, t, side="left"))
+            k, v = c.seek(s, x.size, t, delta=True)
+            wv = int(x[want]) if want < x.size else 0
+            if (k, v) != (want, wv):
+                errs.append(f"seek b={bits} t={t}: {(k, v)} != {(want, wv)}")
+    return errs
+
+
+def seek_first_match_unsorted(c, seed: int = 32) -> list[str]:
+    """On unsorted plain data, seek is the first position holding a value >= target."""
+    rng = np.random.default_rng(seed)
+    x = rng.integers(0, 1 << 20, 300).astype(np.uint32)
+    s = c.encode(x)
+    errs = []
+    for t in rng.integers(0, 1 << 20, 50).tolist() + [0, (1 << 20) + 5]:
+        hit = np.flatnonzero(x >= t)
+        want = (int(hit[0]), int(x[hit[0]])) if hit.size else (x.size, 0)
+        if c.seek(s, x.size, t) != want:
+            errs.append(f"unsorted seek t={t}: {c.seek(s, x.size, t)} != {want}")
+    return errs
+
+
+def select_matches_definition(c, seed: int = 33) -> list[str]:
+    """Select(i) is the i-th integer the Python definition decodes (Fig. 6b);
+    i = n is out of range."""
+    rng = np.random.default_rng(seed)
+    errs = []
+    for delta in (False, True):
+        for n in (1, 5, 37):
+            x = rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32)
+            prev = int(rng.integers(0, 1 << 32))
+            s = c.encode(x, prev=prev, delta=delta)
+            dec, _ = D.decode(s.tobytes(), n, prev, delta)
+            if dec is None:
+                errs.append(f"select delta={delta} n={n}: the definition rejects the stream")
+                continue
+            for i in range(n):
+                if c.select(s, n, i, prev, delta) != dec[i]:
+                    errs.append(f"select delta={delta} n={n} i={i}")
+            if c.select(s, n, n, prev, delta) is not None:
+                errs.append(f"select delta={delta} n={n}: index n accepted")
+    return errs
+
+
+def seek_select_truncation(c) -> list[str]:
+    """Cutting the data stream makes exactly the answers that need the lost
+    bytes fail; all control bytes are required."""
+    import oracle
+    x = np.array([1, 300, 70000, 5, 1 << 30, 2, 3], dtype=np.uint32)
+    s = c.encode(x)
+    nctrl = 2
+    ends = nctrl + np.cumsum([D.length_of(int(v)) for v in x])
+    errs = []
+    for cut in range(s.size + 1):
+        for i in range(x.size):
+            got = c.select(s, x.size, i, in_len=cut)
+            ok = cut >= ends[i]
+            if (got is not None) != ok or (ok and got != int(x[i])):
+                errs.append(f"select i={i} cut={cut}: {got}")
+        k, _ = c.seek(s, x.size, 70000, in_len=cut)   # decided by index 2
+        if (k != oracle.ERROR) != (cut >= ends[2]):
+            errs.append(f"seek cut={cut}: {k}")
+    return errs
+
+
 ALL = [fig3_stream, fig1_blocks, sec2_prefix_sum, zero_control, control_range,
        length_boundaries, round_trips, definition_agrees, truncation,
-       pad_fields_ignored, nonminimal_codes]
+       pad_fields_ignored, nonminimal_codes, seek_matches_searchsorted,
+       seek_first_match_unsorted, select_matches_definition, seek_select_truncation]
 
 
 def run_all(c) -> dict[str, list[str]]:

@@ -115,6 +115,10 @@ MUTANTS = {
                           "if (x == 0)\n        return 1;\n    if (x < (1u << 8))\n        return 1;"),
                          ("unsigned len = svb_ref_byte_length(v[i]);\n        out[i / 4]",
                           "unsigned len = v[i] ? svb_ref_byte_length(v[i]) : 0;\n        out[i / 4]")],
+    # seek stops at the first integer strictly above the target
+    "seek_strict_greater": [("if (v >= target)", "if (v > target)")],
+    # select returns the integer before the one asked for
+    "select_off_by_one": [("for (size_t i = 0; i <= index; i++)", "for (size_t i = 0; i < index; i++)")],
     # decoder forgets the truncation check
     "no_truncation_check": [("if (len > in_len - pos)\n            return SVB_REF_ERROR;", "")],
 }
