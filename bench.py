@@ -362,6 +362,7 @@ def main():
         del h_x
         sec["delta_64m"] = time_codec(svb, W, "delta_64m", dev, peaks)
         sec["uniform_1m"] = time_codec(svb, W, "uniform_1m", dev, peaks)
+        sec["seek_select_256"] = time_queries(svb, dev)
         if not args.no_lists:
             torch.cuda.empty_cache()
             sec["lists_100k"] = time_lists(svb, W, dev, peaks, args.list_count)
@@ -462,6 +463,57 @@ def time_codec(svb, W, name, dev, peaks):
                        "frac": alg / (ms_d / 1e3) / 1e9 / hb},
             "encode": {"gints_per_s": n / ms_e / 1e6, "us": ms_e * 1e3,
                        "frac": alg / (ms_e / 1e3) / 1e9 / hb}}
+
+
+def time_queries(svb, dev, num_lists: int = 1 << 20, nq: int = 1 << 22):
+    """Seek and select (Sec. 5, Fig. 6) in the paper's setting: lists of 256
+    integers whose deltas are uniform in [0, 2^b), prefix-summed and
+    differentially coded; queries pick a list uniformly, seek targets are
+    uniform in [0, the list's last integer], select indexes uniform in
+    [0, 256).  One launch answers all queries; reported as queries/s."""
+    import torch
+    from paper_1709_08990_gb300.batch import ListPool
+    out = {"lists": num_lists, "list_len": 256, "queries": nq}
+    for bits in (8, 24):
+        rng = np.random.default_rng(600 + bits)
+        d = rng.integers(0, 1 << bits, (num_lists, 256), dtype=np.uint64)
+        vals = (np.cumsum(d, axis=1) & 0xFFFFFFFF).astype(np.uint32)
+        lengths = np.full(num_lists, 256, dtype=np.uint32)
+        pool = ListPool(lengths, vals.reshape(-1), delta=True, device=dev)
+        res = {"pool_bytes": pool.pool_bytes}
+        d_tab = torch.from_numpy(pool.dec_table.view(np.uint8).copy()).to(dev)
+        for op in (svb.SVB_SEEK, svb.SVB_SELECT):
+            q = np.zeros(nq, dtype=svb.query_dtype())
+            q["list"] = rng.integers(0, num_lists, nq)
+            q["op"] = op
+            if op == svb.SVB_SEEK:
+                last = vals[q["list"], -1].astype(np.uint64)
+                q["arg"] = (rng.random(nq) * (last + 1)).astype(np.uint64)
+            else:
+                q["arg"] = rng.integers(0, 256, nq)
+            d_q = torch.from_numpy(q.view(np.uint8).copy()).to(dev)
+            d_a = torch.zeros(nq * svb.answer_dtype().itemsize, dtype=torch.uint8, device=dev)
+            stream = torch.cuda.current_stream()
+            ms = _time(lambda: svb.svb_query_batch(d_tab, num_lists, pool.pool, 1, d_q, nq, d_a,
+                                                   stream), 20, stream)
+            a = d_a.cpu().numpy().view(svb.answer_dtype())
+            # spot-check against the decoded lists
+            k = rng.integers(0, nq, 256)
+            ok = bool(np.all(a["status"][k] == 0))
+            for i in k:
+                li, arg = int(q["list"][i]), int(q["arg"][i])
+                row = vals[li]
+                if op == svb.SVB_SEEK:
+                    j = int(np.searchsorted(row, arg, side="left"))
+                    ok &= int(a["index"][i]) == j and (j == 256 or int(a["value"][i]) == int(row[j]))
+                else:
+                    ok &= int(a["value"][i]) == int(row[arg])
+            res["seek" if op == svb.SVB_SEEK else "select"] = {
+                "mqueries_per_s": nq / ms / 1e3, "ms": ms, "verified_sample": bool(ok)}
+        out[f"b{bits}"] = res
+        del pool, d_tab
+        torch.cuda.empty_cache()
+    return out
 
 
 def time_serve(pool, W, seconds: float = 1.0):

@@ -263,6 +263,42 @@ int svb_batch_encode(const void *d_plan, const svb_list *d_lists, const uint32_t
 size_t svb_decode_noalloc(const uint8_t *in, size_t in_len, size_t n, uint32_t *out,
                           uint32_t prev, int delta, svb_stream_t stream);
 
+/* ---- seek and select on compressed lists --------------------------------- */
+
+/* The two operations benchmarked at the end of Sec. 5 (Fig. 6), answered on
+ * the compressed bytes of lists held in one pool (a table of svb_list as for
+ * the batched codec; out_off is not used), many queries per launch:
+ *   SVB_SEEK    arg = target (< 2^32): index of the first integer >= target
+ *               and that integer; n and 0 when there is none;
+ *   SVB_SELECT  arg = index i < n: the integer at i (index = i).
+ * delta != 0 reads every list as differentially coded from its prev (the
+ * paper's setting: sorted lists, Sec. 5).  Each answer's status is SVB_OK,
+ * SVB_EINVAL (list id >= num_lists, unknown op, select index >= n) or
+ * SVB_ETRUNCATED (the list's in_len holds fewer than its ceil(n/4) control
+ * bytes, or not the data bytes of the integer that decides the answer).  No
+ * byte outside a list's [in_off, in_off + in_len) is read.
+ * All pointers are device pointers; answers[k] answers queries[k].  Runs on
+ * `stream` and returns at once: SVB_OK, SVB_EINVAL (null pointer with
+ * num_queries > 0) or SVB_ECUDA. */
+#define SVB_SEEK 0
+#define SVB_SELECT 1
+
+typedef struct svb_query {
+    uint32_t list;   /* index into the list table */
+    uint32_t op;     /* SVB_SEEK or SVB_SELECT */
+    uint64_t arg;    /* seek: target; select: index */
+} svb_query;
+
+typedef struct svb_answer {
+    uint64_t index;  /* seek: position found (n if none); select: the index */
+    uint32_t value;  /* the integer there (0 if none or on error) */
+    uint32_t status; /* svb_status */
+} svb_answer;
+
+int svb_query_batch(const svb_list *d_lists, size_t num_lists, const uint8_t *in_base, int delta,
+                    const svb_query *d_queries, size_t num_queries, svb_answer *d_answers,
+                    svb_stream_t stream);
+
 /* ---- compressed-size report: Stream VByte against VByte ------------------ */
 
 /* Sizes of n integers coded two ways, without writing either stream (Sec. 5,

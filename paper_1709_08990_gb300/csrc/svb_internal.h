@@ -43,6 +43,11 @@ size_t batch_plan_bytes(size_t num_lists);
 int build_batch_plan(const svb_list *h_lists, size_t num_lists, uint32_t threshold, void *d_plan,
                      cudaStream_t stream);
 
+// Seek / select queries on a pool of lists (svb_query.cu).
+int launch_query(const svb_list *lists, u64 num_lists, const uint8_t *in, bool delta,
+                 const svb_query *queries, u64 num_queries, svb_answer *answers,
+                 cudaStream_t stream);
+
 // Stream VByte and VByte sizes of n values into d_sizes[0..2) (svb_size.cu).
 int launch_size_report(const uint32_t *in, u64 n, uint32_t prev, bool delta, u64 *d_sizes,
                        cudaStream_t stream);

@@ -63,6 +63,7 @@ def lib() -> ctypes.CDLL:
             "svb_decode_async": ([vp, sz, sz, vp, u32, i32, vp, vp, sz, vp], i32),
             "svb_testhook_lookback_timeout": ([vp, sz, vp, u64, vp, vp, sz, vp], i32),
             "svb_decode_noalloc": ([vp, sz, sz, vp, u32, i32, vp], sz),
+            "svb_query_batch": ([vp, sz, vp, i32, vp, sz, vp, vp], i32),
             "svb_size_report": ([vp, sz, u32, i32, vp], i32),
             "svb_size_report_async": ([vp, sz, u32, i32, vp, vp], i32),
             "svb_batch_plan_bytes": ([sz], sz),
@@ -254,6 +255,27 @@ def profile_end() -> dict:
 
 
 SVB_NOALLOC_MAX_N = 1 << 24
+
+
+SVB_SEEK, SVB_SELECT = 0, 1
+
+
+def query_dtype():
+    """numpy dtype laid out like svb_query."""
+    import numpy as np
+    return np.dtype([("list", np.uint32), ("op", np.uint32), ("arg", np.uint64)])
+
+
+def answer_dtype():
+    """numpy dtype laid out like svb_answer."""
+    import numpy as np
+    return np.dtype([("index", np.uint64), ("value", np.uint32), ("status", np.uint32)])
+
+
+def svb_query_batch(d_lists, num_lists: int, in_base, delta: int, d_queries, num_queries: int,
+                    d_answers, stream=None) -> int:
+    return lib().svb_query_batch(_p(d_lists), num_lists, _p(in_base), int(delta), _p(d_queries),
+                                 num_queries, _p(d_answers), _stream(stream))
 
 
 def svb_size_report(inp, n: int, prev: int, delta: int, sizes) -> int:
