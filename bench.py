@@ -363,6 +363,7 @@ def main():
         sec["delta_64m"] = time_codec(svb, W, "delta_64m", dev, peaks)
         sec["uniform_1m"] = time_codec(svb, W, "uniform_1m", dev, peaks)
         sec["seek_select_256"] = time_queries(svb, dev)
+        sec["append"] = time_append(svb, W, dev)
         if not args.no_lists:
             torch.cuda.empty_cache()
             sec["lists_100k"] = time_lists(svb, W, dev, peaks, args.list_count)
@@ -514,6 +515,49 @@ def time_queries(svb, dev, num_lists: int = 1 << 20, nq: int = 1 << 22):
         del pool, d_tab
         torch.cuda.empty_cache()
     return out
+
+
+def time_append(svb, W, dev, n0: int = 1 << 26, k: int = 1 << 20):
+    """Appending k integers to an n0-integer compressed array (Sec. 4's
+    closing remark) against encoding all n0 + k from scratch; skewed values."""
+    import torch
+    x = W.array_values("skewed_1g", n=n0 + k)
+    d_x = torch.from_numpy(x.view(np.int32)).to(dev)
+    s = svb.encode(d_x[:n0])
+    nc = (n0 + 3) // 4
+    ctrl_cap, data_cap = (n0 + k + 3) // 4 + 8, s.numel() - nc + 4 * k + 64
+    d_ctrl = torch.zeros(ctrl_cap, dtype=torch.uint8, device=dev)
+    d_data = torch.zeros(data_cap, dtype=torch.uint8, device=dev)
+    d_ctrl0 = s[:nc].clone()
+    d_data0 = s[nc:].clone()
+    data_len0 = s.numel() - nc
+    d_new = d_x[n0:]
+    reps = 20
+    torch.cuda.synchronize()
+    t = 0.0
+    for i in range(reps + 3):
+        d_ctrl[:nc].copy_(d_ctrl0)          # restore the n0-integer array (untimed)
+        d_data[:data_len0].copy_(d_data0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dl = svb.svb_append(d_ctrl, ctrl_cap, d_data, data_cap, data_len0, n0, d_new, k, 0, 0)
+        el = time.perf_counter() - t0
+        if i >= 3:
+            t += el
+    ms = t / reps * 1e3
+    whole = svb.encode(d_x)
+    ok = bool(torch.equal(d_ctrl[:(n0 + k + 3) // 4], whole[:(n0 + k + 3) // 4])) and \
+        bool(torch.equal(d_data[:dl], whole[(n0 + k + 3) // 4:]))
+    ws = torch.empty(svb.svb_workspace_size(n0 + k), dtype=torch.uint8, device=dev)
+    res = torch.zeros(2, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream()
+    svb.svb_workspace_init(ws, ws.numel(), stream)
+    out = torch.empty(svb.svb_max_compressed_size(n0 + k), dtype=torch.uint8, device=dev)
+    ms_enc = _time(lambda: svb.svb_encode_async(d_x, n0 + k, out, 0, 0, res, ws, ws.numel(),
+                                                stream), 10, stream)
+    return {"n0": n0, "k": k, "append_ms": ms, "append_gints_per_s": k / ms / 1e6,
+            "reencode_all_ms": ms_enc, "verified": ok,
+            "note": "append timed on the host around the synchronous call"}
 
 
 def time_serve(pool, W, seconds: float = 1.0):

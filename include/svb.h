@@ -263,6 +263,27 @@ int svb_batch_encode(const void *d_plan, const svb_list *d_lists, const uint32_t
 size_t svb_decode_noalloc(const uint8_t *in, size_t in_len, size_t n, uint32_t *out,
                           uint32_t prev, int delta, svb_stream_t stream);
 
+/* ---- appending ------------------------------------------------------------ */
+
+/* Append k integers to a compressed array without recompressing it (Sec. 4's
+ * closing remark: the new data follow the existing data and the control
+ * stream grows).  The array is kept as two device buffers that can grow:
+ *   ctrl[0 .. ceil(n/4))  its control bytes; room for ceil((n + k)/4);
+ *   data[0 .. data_len)   its data bytes; room for data_len + 4k + 3 (n mod 4).
+ * Joined, ctrl and data are the usual stream [ctrl][data].  in[0..k) are the
+ * new integers (device).  With delta != 0 the array is differentially coded
+ * and `last` is its last integer (the start value prev when n = 0); otherwise
+ * `last` is unused.  Afterwards the array holds n + k integers, exactly as if
+ * all of them had been encoded at once; only the last control byte and the
+ * data of its integers are rewritten, so the cost is O(k).  Runs on the
+ * current stream and waits for it.  Returns the new data length, or
+ * SVB_ERROR with svb_last_error() = SVB_EINVAL (null pointer, too little
+ * room, data_len too short for the integers of the last control byte),
+ * SVB_ENOMEM, SVB_ECUDA or SVB_ETIMEOUT.  k = 0 returns data_len. */
+size_t svb_append(uint8_t *ctrl, size_t ctrl_cap, uint8_t *data, size_t data_cap,
+                  size_t data_len, size_t n, const uint32_t *in, size_t k, uint32_t last,
+                  int delta);
+
 /* ---- seek and select on compressed lists --------------------------------- */
 
 /* The two operations benchmarked at the end of Sec. 5 (Fig. 6), answered on

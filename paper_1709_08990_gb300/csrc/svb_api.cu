@@ -147,6 +147,15 @@ size_t decode_sync(const uint8_t *in, u64 in_len, size_t n, uint32_t *out, uint3
     });
 }
 
+// Scratch for appends (the re-coded tail and the new values), per device;
+// kept apart from the encoder workspace so its bytes never pass for records.
+struct ScratchCache {
+    std::mutex mu;
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+ScratchCache g_append_scratch[kMaxDevices];
+
 }  // namespace
 
 void svb::set_last_error(int code)
@@ -244,6 +253,46 @@ size_t svb_encode_host(const uint32_t *h_in, size_t n, uint8_t *h_out, uint32_t 
         return set_error(SVB_ECUDA);
     t_last_error = SVB_OK;
     return k;
+}
+
+size_t svb_append(uint8_t *ctrl, size_t ctrl_cap, uint8_t *data, size_t data_cap,
+                  size_t data_len, size_t n, const uint32_t *in, size_t k, uint32_t last,
+                  int delta)
+{
+    if (!ctrl || !data || (k && !in))
+        return set_error(SVB_EINVAL);
+    if (k == 0) {
+        t_last_error = SVB_OK;
+        return data_len;
+    }
+    const size_t r = n % 4;
+    if (ctrl_cap < (n + k + 3) / 4 || data_cap < data_len + 4 * k + 3 * r)
+        return set_error(SVB_EINVAL);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return set_error(SVB_ECUDA);
+    ScratchCache &sc = g_append_scratch[dev];
+    std::lock_guard<std::mutex> lock(sc.mu);
+    const size_t need = svb::append_scratch_bytes(k);
+    if (sc.bytes < need) {
+        if (sc.p) {
+            cudaDeviceSynchronize();
+            cudaFree(sc.p);
+            sc.p = nullptr;
+            sc.bytes = 0;
+        }
+        const size_t grow = std::max(need, 2 * sc.bytes);
+        if (cudaMalloc(&sc.p, grow) != cudaSuccess) {
+            cudaGetLastError();
+            sc.p = nullptr;
+            return set_error(SVB_ENOMEM);
+        }
+        sc.bytes = grow;
+    }
+    return run_sync(k + 3, [&](void *ws, svb::DeviceResult *res, cudaStream_t s) {
+        return svb::launch_append(ctrl, data, data_len, n, in, k, last, delta != 0, sc.p, ws, res,
+                                  s, spin_limit());
+    });
 }
 
 int svb_set_stream(svb_stream_t stream)

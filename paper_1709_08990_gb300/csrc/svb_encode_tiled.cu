@@ -55,7 +55,9 @@ static_assert(kChunkSubs <= 32, "a chunk's sub-tile sizes are scanned one per la
 struct EncTiledArgs {
     const uint32_t *in;
     u64 n, nquads, ntiles, nchunks;
-    uint8_t *out;
+    uint8_t *out;             // control bytes (and, unless data is set, the data after them)
+    uint8_t *data;            // where data byte 0 goes, minus *data_back; null: out + nquads
+    const u64 *data_back;     // device value subtracted from data (null: 0)
     WsHeader *hdr;
     TileStatus *st;
     DeviceResult *result;
@@ -422,6 +424,8 @@ __device__ void et_chunk_warp(const EncTiledArgs &a, EtPipe &P, EtChunks &C, u64
 __device__ void et_consume(const EncTiledArgs &a, EtPipe &P, EtChunks &C, u64 etag)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint8_t *const data_base =
+        a.data ? a.data - (a.data_back ? *a.data_back : 0ull) : a.out + a.nquads;
     const uint32_t last_nints = (uint32_t)(a.n - 4 * (a.nquads - 1));
     const uint32_t sq0 = warp * kSubQuads;
     uint32_t sized = 0, written = 0;   // chunks this CTA has sized / started writing
@@ -498,7 +502,7 @@ __device__ void et_consume(const EncTiledArgs &a, EtPipe &P, EtChunks &C, u64 et
                 raise_error(a.hdr, kErrTimeout);
             break;
         }
-        uint8_t *dst = a.out + a.nquads + C.base[b] + C.excl[b][ti * kEtSubs + warp];
+        uint8_t *dst = data_base + C.base[b] + C.excl[b][ti * kEtSubs + warp];
         if (fast)
             et_write<true>(a, P.slice[warp], dst, q0, sq0, nvq, nints, ctrl, cb, d);
         else
@@ -537,7 +541,8 @@ __global__ void __launch_bounds__(kEtBlock, 3) encode_tiled_kernel(EncTiledArgs 
 }
 
 int launch_encode_tiled(const uint32_t *in, u64 n, uint8_t *out, uint32_t prev, bool delta,
-                        void *ws, DeviceResult *result, cudaStream_t stream, u64 spin_limit)
+                        void *ws, DeviceResult *result, cudaStream_t stream, u64 spin_limit,
+                        uint8_t *data, const u64 *data_back)
 {
     static int grid = 0;
     if (!grid) {
@@ -558,6 +563,8 @@ int launch_encode_tiled(const uint32_t *in, u64 n, uint8_t *out, uint32_t prev, 
     a.ntiles = (a.nquads + kEtQuads - 1) / kEtQuads;
     a.nchunks = (a.ntiles + kChunkTiles - 1) / kChunkTiles;
     a.out = out;
+    a.data = data;
+    a.data_back = data_back;
     a.hdr = reinterpret_cast<WsHeader *>(ws);
     a.st = reinterpret_cast<TileStatus *>(static_cast<char *>(ws) + L.status);
     a.result = result;

@@ -28,9 +28,21 @@ int launch_encode(const uint32_t *in, u64 n, uint8_t *out, uint32_t prev, bool d
                   DeviceResult *result, cudaStream_t stream, u64 spin_limit);
 u64 encode_tiles(u64 n);
 
-// Chunked single-pass encoder (svb_encode_tiled.cu).
+// Chunked single-pass encoder (svb_encode_tiled.cu).  Control bytes go to
+// out; data bytes to out + ceil(n/4), or, when data is given, to
+// data - *data_back (data_back a device pointer, or null for 0).
 int launch_encode_tiled(const uint32_t *in, u64 n, uint8_t *out, uint32_t prev, bool delta,
-                        void *ws, DeviceResult *result, cudaStream_t stream, u64 spin_limit);
+                        void *ws, DeviceResult *result, cudaStream_t stream, u64 spin_limit,
+                        uint8_t *data = nullptr, const u64 *data_back = nullptr);
+
+// Append k integers to a stream kept as separate control and data buffers
+// (svb_append.cu); scratch holds the re-coded tail and the new values
+// (append_scratch_bytes(k)), ws/result are an encoder workspace.  result->bytes
+// becomes the new data length.
+size_t append_scratch_bytes(u64 k);
+int launch_append(uint8_t *ctrl, uint8_t *data, u64 data_len, u64 n, const uint32_t *in, u64 k,
+                  uint32_t last, bool delta, void *scratch, void *ws, DeviceResult *result,
+                  cudaStream_t stream, u64 spin_limit);
 
 // Batched codec (svb_batch.cu).
 int launch_batch_decode(const void *d_plan, const svb_list *d_lists, const uint8_t *in,

@@ -64,6 +64,7 @@ def lib() -> ctypes.CDLL:
             "svb_testhook_lookback_timeout": ([vp, sz, vp, u64, vp, vp, sz, vp], i32),
             "svb_decode_noalloc": ([vp, sz, sz, vp, u32, i32, vp], sz),
             "svb_query_batch": ([vp, sz, vp, i32, vp, sz, vp, vp], i32),
+            "svb_append": ([vp, sz, vp, sz, sz, sz, vp, sz, u32, i32], sz),
             "svb_size_report": ([vp, sz, u32, i32, vp], i32),
             "svb_size_report_async": ([vp, sz, u32, i32, vp, vp], i32),
             "svb_batch_plan_bytes": ([sz], sz),
@@ -255,6 +256,12 @@ def profile_end() -> dict:
 
 
 SVB_NOALLOC_MAX_N = 1 << 24
+
+
+def svb_append(ctrl, ctrl_cap: int, data, data_cap: int, data_len: int, n: int, inp, k: int,
+               last: int, delta: int) -> int:
+    return _sized(lib().svb_append(_p(ctrl), ctrl_cap, _p(data), data_cap, data_len, n, _p(inp),
+                                   k, last & 0xFFFFFFFF, int(delta)), "svb_append")
 
 
 SVB_SEEK, SVB_SELECT = 0, 1
