@@ -54,16 +54,25 @@ struct BatchDecArgs {
     uint32_t delta;
 };
 
+// Control bytes travel ahead of the data: tile g's control bytes sit in ring
+// slot g % kCRing and are fetched kCAhead tiles before its data, so the
+// producer never waits a round trip to learn where a tile's data start.  Slot
+// (g + kCAhead) % kCRing was last used by tile g - kBStages, whose stage the
+// producer has seen released before it refills the slot.
+constexpr int kCAhead = 2;
+constexpr int kCRing = kBStages + kCAhead;
+
 struct BPipe {
     uint8_t data[kBStages][kBStageData];
-    uint8_t ctrl[kBStages][kBStageCtrl];
+    uint8_t ctrl[kCRing][kBStageCtrl];
     uint64_t full[kBStages];   // control and data landed (consumers wait)
-    uint64_t cfull[kBStages];  // control landed (the producer waits)
+    uint64_t cfull[kCRing];    // control landed (the producer waits)
     uint64_t empty[kBStages];  // consumers done with the stage
     uint32_t list[kBStages];   // list id, or kNoList
     uint32_t tile[kBStages];   // tile index within the list
     uint32_t skip[kBStages];   // the list is truncated: decode nothing
     uint32_t hd[kBStages], hc[kBStages];
+    uint32_t clist[kCRing], ctile[kCRing], chc[kCRing];   // what each ring slot holds
 };
 
 __device__ __forceinline__ const uint32_t *plan_big(const PlanHeader *p)
@@ -95,58 +104,74 @@ __device__ __forceinline__ uint32_t tile_data_bytes(const uint8_t *C, uint32_t n
     return t;
 }
 
-// Producer warp of the big-list phase.
+// Producer warp of the big-list phase.  Two cursors walk the big lists in
+// claim order: the look-ahead cursor fetches control bytes kCAhead tiles
+// ahead (claiming the next list as soon as it needs one), the data cursor
+// sums each tile's staged control bytes to find where its data start and
+// copies the data.  Every tile whose control bytes were fetched gets one stage
+// (a skipped one if its list's data are cut short), so stage g always pairs
+// with ring slot g % kCRing.
 __device__ void bdec_produce(const BatchDecArgs &a, BPipe &P, int lane)
 {
     const PlanHeader *plan = a.plan;
     const uint32_t *big = plan_big(plan);
-    uint32_t issued = 0;
+    uint32_t issued = 0;   // stages posted
 
-    // Current list and tile.
-    uint32_t li = kNoList, k = 0, ntl = 0, nql = 0, last_nints = 4;
-    u64 running = 0;
-    svb_list L = {};
-    auto claim = [&]() -> bool {
-        uint32_t j = 0;
-        if (lane == 0)
-            j = (uint32_t)atomicAdd(&a.hdr->tile_counter, 1ull);
-        j = __shfl_sync(0xffffffffu, j, 0);
-        if (j >= plan->nbig)
-            return false;
-        li = big[j];
-        L = a.lists[li];
-        nql = (L.n + 3) / 4;
-        ntl = (nql + kBQuads - 1) / kBQuads;
-        last_nints = L.n - 4 * (nql - 1);
-        k = 0;
-        running = 0;
-        return true;
-    };
-    auto issue_ctrl = [&](int s) {
-        const uint8_t *gc = a.in + L.in_off + (u64)k * kBQuads;
-        const uint32_t clen = min((uint32_t)kBQuads, nql - k * kBQuads);
-        range_edges(gc, clen, P.ctrl[s], lane);
-        if (lane == 0) {
-            const uint8_t *ac;
-            uint32_t oc;
-            uint32_t bc = range_interior(gc, clen, ac, oc);
-            P.list[s] = li;
-            P.tile[s] = k;
-            P.hc[s] = (uint32_t)((uintptr_t)gc & 15u);
-            mbar_arrive_expect_tx(&P.cfull[s], bc);
-            if (bc)
-                bulk_g2s(P.ctrl[s] + oc, ac, bc, &P.cfull[s]);
-        } else {
-            mbar_arrive(&P.cfull[s]);
+    // Look-ahead cursor.
+    uint32_t la_li = kNoList, la_k = 0, la_ntl = 0, la_nql = 0;
+    u64 la_off = 0, la_len = 0;
+    bool la_have = false;
+    auto la_claim = [&]() {
+        for (;;) {
+            uint32_t j = 0;
+            if (lane == 0)
+                j = (uint32_t)atomicAdd(&a.hdr->tile_counter, 1ull);
+            j = __shfl_sync(0xffffffffu, j, 0);
+            if (j >= plan->nbig) {
+                la_have = false;
+                return;
+            }
+            const svb_list L = a.lists[big[j]];
+            const uint32_t nql = (L.n + 3) / 4;
+            if (nql > L.in_len) {   // its control bytes do not fit: reported, skipped
+                if (lane == 0)
+                    raise_error(a.hdr, kErrTruncated);
+                continue;
+            }
+            la_li = big[j];
+            la_nql = nql;
+            la_ntl = (nql + kBQuads - 1) / kBQuads;
+            la_off = L.in_off;
+            la_len = L.in_len;
+            la_k = 0;
+            la_have = true;
+            return;
         }
     };
-    auto post_none = [&](int s) {
+    uint32_t c_issued = 0;   // tiles whose control bytes were fetched
+    auto fetch_ctrl = [&]() {
+        if (!la_have)
+            return;
+        const int slot = c_issued % kCRing;
+        const uint8_t *lo = a.in + la_off;
+        const uint8_t *gc = lo + (u64)la_k * kBQuads;
+        const uint32_t clen = min((uint32_t)kBQuads, la_nql - la_k * kBQuads);
+        const StagePlan pc = stage_plan(gc, clen, lo, lo + la_len);
+        if (pc.edges)
+            range_edges(gc, clen, P.ctrl[slot], lane);
         if (lane == 0) {
-            P.list[s] = kNoList;
-            mbar_arrive_expect_tx(&P.full[s], 0);
+            P.clist[slot] = la_li;
+            P.ctile[slot] = la_k;
+            P.chc[slot] = (uint32_t)((uintptr_t)gc & 15u);
+            mbar_arrive_expect_tx(&P.cfull[slot], pc.bytes);
+            if (pc.bytes)
+                bulk_g2s(P.ctrl[slot] + pc.dst_off, pc.src, pc.bytes, &P.cfull[slot]);
         } else {
-            mbar_arrive(&P.full[s]);
+            mbar_arrive(&P.cfull[slot]);
         }
+        c_issued++;
+        if (++la_k == la_ntl)
+            la_claim();
     };
     auto wait_empty = [&](uint32_t g) -> bool {
         if (g < (uint32_t)kBStages)
@@ -155,80 +180,92 @@ __device__ void bdec_produce(const BatchDecArgs &a, BPipe &P, int lane)
         return __all_sync(0xffffffffu, ok);
     };
 
-    bool have = claim();
-    if (!have) {
-        post_none(0);
-        issued = 1;
-    } else {
-        // A list whose control bytes do not fit is reported and skipped.
-        while (have && nql > L.in_len) {
-            if (lane == 0)
-                raise_error(a.hdr, kErrTruncated);
-            have = claim();
-        }
-        if (!have) {
-            post_none(0);
-            issued = 1;
-        } else {
-            issue_ctrl(0);
-        }
-    }
-    for (uint32_t g = 0; have; g++) {
-        const int s = g % kBStages;
-        if (!mbar_wait_bounded(&P.cfull[s], (g / kBStages) & 1u, kBPolls)) {
+    la_claim();
+    for (int j = 0; j < kCAhead; j++)
+        fetch_ctrl();
+
+    // Data cursor.
+    uint32_t li = kNoList, nql = 0, ntl = 0, last_nints = 4;
+    u64 running = 0;
+    svb_list L = {};
+    bool cut = false;
+    uint32_t g = 0;
+    bool failed = false;
+    for (; g < c_issued; g++) {
+        const int slot = g % kCRing, s = g % kBStages;
+        if (!mbar_wait_bounded(&P.cfull[slot], (g / kCRing) & 1u, kBPolls)) {
             if (lane == 0)
                 raise_error(a.hdr, kErrTimeout);
         }
         __syncwarp();
-        const bool last_tile = k + 1 == ntl;
-        const uint32_t nq = min((uint32_t)kBQuads, nql - k * kBQuads);
-        const uint32_t dsize =
-            tile_data_bytes(P.ctrl[s] + P.hc[s], nq, last_tile, last_nints, lane);
-        fence_proxy_async_smem();  // these reads come before any later copy into the stage
-        const bool trunc = nql + running + dsize > L.in_len;
-        const uint8_t *gd = a.in + L.in_off + nql + running;
-        const uint32_t dlen = trunc ? 0u : dsize;
-        range_edges(gd, dlen, P.data[s], lane);
+        const uint32_t tli = P.clist[slot], tk = P.ctile[slot];
+        if (tk == 0) {   // a new list
+            li = tli;
+            L = a.lists[li];
+            nql = (L.n + 3) / 4;
+            ntl = (nql + kBQuads - 1) / kBQuads;
+            last_nints = L.n - 4 * (nql - 1);
+            running = 0;
+            cut = false;
+        }
+        if (!wait_empty(g)) {
+            if (lane == 0)
+                raise_error(a.hdr, kErrTimeout);
+            failed = true;
+            break;
+        }
+        const bool last_tile = tk + 1 == ntl;
+        const uint32_t nq = min((uint32_t)kBQuads, nql - tk * kBQuads);
+        uint32_t dsize = 0;
+        if (!cut) {
+            dsize = tile_data_bytes(P.ctrl[slot] + P.chc[slot], nq, last_tile, last_nints, lane);
+            if (nql + running + dsize > L.in_len) {
+                cut = true;
+                if (lane == 0)
+                    raise_error(a.hdr, kErrTruncated);
+            }
+        }
+        fence_proxy_async_smem();  // these reads come before the slot's next fill
+        const uint8_t *lo = a.in + L.in_off;
+        const uint8_t *gd = lo + nql + running;
+        const uint32_t dlen = cut ? 0u : dsize;
+        const StagePlan pd = stage_plan(gd, dlen, lo, lo + L.in_len);
+        if (pd.edges)
+            range_edges(gd, dlen, P.data[s], lane);
         if (lane == 0) {
-            const uint8_t *ad;
-            uint32_t od;
-            uint32_t bd = range_interior(gd, dlen, ad, od);
+            P.list[s] = li;
+            P.tile[s] = tk;
+            P.skip[s] = cut ? 1u : 0u;
             P.hd[s] = (uint32_t)((uintptr_t)gd & 15u);
-            P.skip[s] = trunc ? 1u : 0u;
-            if (trunc)
-                raise_error(a.hdr, kErrTruncated);
-            mbar_arrive_expect_tx(&P.full[s], bd);
-            if (bd)
-                bulk_g2s(P.data[s] + od, ad, bd, &P.full[s]);
+            P.hc[s] = P.chc[slot];
+            mbar_arrive_expect_tx(&P.full[s], pd.bytes);
+            if (pd.bytes)
+                bulk_g2s(P.data[s] + pd.dst_off, pd.src, pd.bytes, &P.full[s]);
         } else {
             mbar_arrive(&P.full[s]);
         }
-        running += dsize;
-        if (last_tile && lane == 0)
-            atomicAdd(&a.hdr->total, (u64)nql + running);
-
-        // Next tile: the rest of this list, or the next big list.
-        if (last_tile || trunc) {
-            have = claim();
-            while (have && nql > L.in_len) {
-                if (lane == 0)
-                    raise_error(a.hdr, kErrTruncated);
-                have = claim();
+        if (!cut) {
+            running += dsize;
+            if (last_tile && lane == 0)
+                atomicAdd(&a.hdr->total, (u64)nql + running);
+        }
+        issued = g + 1;
+        fetch_ctrl();   // the control bytes of tile g + kCAhead
+    }
+    if (!failed) {
+        // No tile left: one stage marked kNoList ends the big-list phase.
+        if (wait_empty(g)) {
+            const int s = g % kBStages;
+            if (lane == 0) {
+                P.list[s] = kNoList;
+                mbar_arrive_expect_tx(&P.full[s], 0);
+            } else {
+                mbar_arrive(&P.full[s]);
             }
-        } else {
-            k++;
-        }
-        if (!wait_empty(g + 1)) {
-            if (lane == 0)
-                raise_error(a.hdr, kErrTimeout);
             issued = g + 1;
-            break;
+        } else if (lane == 0) {
+            raise_error(a.hdr, kErrTimeout);
         }
-        if (have)
-            issue_ctrl((g + 1) % kBStages);
-        else
-            post_none((g + 1) % kBStages);
-        issued = g + 2;
     }
     // Let every copy this warp started land before the CTA can exit.
     if (lane == 0) {
@@ -236,6 +273,11 @@ __device__ void bdec_produce(const BatchDecArgs &a, BPipe &P, int lane)
             if (issued > (uint32_t)s) {
                 uint32_t fills = (issued - 1 - s) / kBStages + 1;
                 mbar_wait_bounded(&P.full[s], (fills - 1) & 1u, kBPolls);
+            }
+        for (int r = 0; r < kCRing; r++)
+            if (c_issued > (uint32_t)r) {
+                uint32_t fills = (c_issued - 1 - r) / kCRing + 1;
+                mbar_wait_bounded(&P.cfull[r], (fills - 1) & 1u, kBPolls);
             }
     }
     __syncwarp();
@@ -266,7 +308,7 @@ __device__ void bdec_consume(const BatchDecArgs &a, BPipe &P, uint16_t *s_qoff,
         const bool skip = P.skip[s] != 0;
         if (k == 0)
             carry = L.prev;
-        const uint8_t *C = P.ctrl[s] + P.hc[s];
+        const uint8_t *C = P.ctrl[g % kCRing] + P.hc[s];
         const uint8_t *D = P.data[s];
         const uint32_t h = P.hd[s];
 
@@ -465,9 +507,10 @@ __global__ void __launch_bounds__(kBBlock, 3) batch_decode_kernel(BatchDecArgs a
     if (tid == 0) {
         for (int s = 0; s < kBStages; s++) {
             mbar_init(&P.full[s], 32);
-            mbar_init(&P.cfull[s], 32);
             mbar_init(&P.empty[s], kWarps);
         }
+        for (int r = 0; r < kCRing; r++)
+            mbar_init(&P.cfull[r], 32);
         fence_mbar_init();
     }
     __syncthreads();

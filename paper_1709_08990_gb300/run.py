@@ -77,10 +77,10 @@ def _array(op: str, name: str, n: int, reps: int) -> dict:
             "gints_per_s": n / (ms / 1e3) / 1e9, "verified": ok}
 
 
-def _lists(op: str, name: str, count: int, reps: int) -> dict:
+def _lists(op: str, name: str, count: int, reps: int, cap: int = 1 << 30) -> dict:
     from .batch import ListPool
     dev = torch.device("cuda", torch.cuda.current_device())
-    lengths = W.lists_lengths(count)
+    lengths = W.lists_lengths(count, cap)
     total = int(lengths.sum(dtype=np.uint64))
     vals = np.empty(total, dtype=np.uint32)
     W.posting_lists(W.WORKLOADS[name].seed, lengths, out=vals)
@@ -106,10 +106,13 @@ def main(argv=None) -> None:
     ap.add_argument("--workload", default=None)
     ap.add_argument("--n", type=int, default=0, help="integers (array workloads; 0 = full)")
     ap.add_argument("--lists", type=int, default=100_000, help="lists (list workload)")
+    ap.add_argument("--cap", type=int, default=1 << 30,
+                    help="total integers the list lengths are scaled to (list workload); "
+                         "--lists 12500 --cap 134217728 is lists_100k at 1/8 scale")
     ap.add_argument("--reps", type=int, default=10)
     a = ap.parse_args(argv)
     if a.op.startswith("batch"):
-        r = _lists(a.op, a.workload or "lists_100k", a.lists, a.reps)
+        r = _lists(a.op, a.workload or "lists_100k", a.lists, a.reps, a.cap)
     else:
         name = a.workload or "skewed_1g"
         r = _array(a.op, name, a.n or W.WORKLOADS[name].n, a.reps)
