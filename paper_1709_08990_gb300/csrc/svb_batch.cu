@@ -23,6 +23,7 @@
 #include "svb_device.cuh"
 #include "svb_internal.h"
 #include "svb_quad.cuh"
+#include "svb_subtile.cuh"
 
 namespace svb {
 
@@ -35,6 +36,8 @@ constexpr int kBBlock = kThreads + 32;       // 8 consumer warps + 1 producer wa
 constexpr u64 kBPolls = 1ull << 24;
 constexpr uint32_t kNoList = 0xffffffffu;
 constexpr uint32_t kDefaultBigThreshold = 8192;
+constexpr int kBSubs = kBQuads / kSubQuads;   // sub-tiles per tile = consumer warps
+static_assert(kBSubs == kWarps, "one consumer warp per sub-tile");
 
 // Plan layout in device memory: header, then big ids, then small ids.
 struct PlanHeader {
@@ -73,6 +76,7 @@ struct BPipe {
     uint32_t skip[kBStages];   // the list is truncated: decode nothing
     uint32_t hd[kBStages], hc[kBStages];
     uint32_t clist[kCRing], ctile[kCRing], chc[kCRing];   // what each ring slot holds
+    uint32_t soff[kBStages][kBSubs];   // each sub-tile's data offset inside the tile
 };
 
 __device__ __forceinline__ const uint32_t *plan_big(const PlanHeader *p)
@@ -87,6 +91,56 @@ __device__ __forceinline__ const uint32_t *plan_small(const PlanHeader *p)
 
 // Data bytes of the quads of one tile, from its staged control bytes
 // (pad fields of the list's last quad count nothing).
+// Data bytes before each sub-tile of one tile, from its staged control bytes
+// (C, 16-byte phase h in the stage): lane i < kBSubs gets the offset of
+// sub-tile i, every lane the tile's total.  A whole tile is read a word (four
+// control bytes) at a time: word lane + 32i lies in sub-tile i, and a word of
+// codes covers 16 + the sum of its codes bytes (Sec. 4).
+__device__ __forceinline__ uint32_t tile_sub_offsets(const uint8_t *stage, uint32_t h, uint32_t nq,
+                                                     bool last_tile, uint32_t last_nints,
+                                                     int lane, uint32_t &total)
+{
+    uint32_t acc[kBSubs];
+    if (nq == (uint32_t)kBQuads && !(last_tile && last_nints < 4)) {
+        const uint32_t *W = reinterpret_cast<const uint32_t *>(stage) + (h >> 2);
+        const uint32_t sh = 8 * (h & 3u);
+#pragma unroll
+        for (int i = 0; i < kBSubs; i++) {
+            const uint32_t w = __funnelshift_r(W[lane + 32 * i], W[lane + 32 * i + 1], sh);
+            acc[i] = 16u + __popc(w & 0x55555555u) + 2u * __popc(w & 0xAAAAAAAAu);
+        }
+    } else {
+        const uint8_t *C = stage + h;
+#pragma unroll
+        for (int i = 0; i < kBSubs; i++) {
+            acc[i] = 0;
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const uint32_t q = 4 * (lane + 32 * i) + j;
+                if (q < nq) {
+                    uint32_t c = C[q];
+                    const uint32_t k = (last_tile && q == nq - 1) ? last_nints : 4u;
+                    if (k < 4)
+                        c &= (1u << (2 * k)) - 1u;
+                    acc[i] += quad_count(c, k);
+                }
+            }
+        }
+    }
+    uint32_t mine = 0, run = 0;
+#pragma unroll
+    for (int i = 0; i < kBSubs; i++) {
+        uint32_t t = acc[i];
+#pragma unroll
+        for (int d = 16; d >= 1; d >>= 1)
+            t += __shfl_xor_sync(0xffffffffu, t, d);
+        mine = lane == i ? run : mine;
+        run += t;
+    }
+    total = run;
+    return mine;
+}
+
 __device__ __forceinline__ uint32_t tile_data_bytes(const uint8_t *C, uint32_t nq, bool last_tile,
                                                     uint32_t last_nints, int lane)
 {
@@ -216,9 +270,10 @@ __device__ void bdec_produce(const BatchDecArgs &a, BPipe &P, int lane)
         }
         const bool last_tile = tk + 1 == ntl;
         const uint32_t nq = min((uint32_t)kBQuads, nql - tk * kBQuads);
-        uint32_t dsize = 0;
+        uint32_t dsize = 0, soff = 0;
         if (!cut) {
-            dsize = tile_data_bytes(P.ctrl[slot] + P.chc[slot], nq, last_tile, last_nints, lane);
+            soff = tile_sub_offsets(P.ctrl[slot], P.chc[slot], nq, last_tile, last_nints, lane,
+                                    dsize);
             if (nql + running + dsize > L.in_len) {
                 cut = true;
                 if (lane == 0)
@@ -232,6 +287,8 @@ __device__ void bdec_produce(const BatchDecArgs &a, BPipe &P, int lane)
         const StagePlan pd = stage_plan(gd, dlen, lo, lo + L.in_len);
         if (pd.edges)
             range_edges(gd, dlen, P.data[s], lane);
+        if (lane < kBSubs)
+            P.soff[s][lane] = soff;
         if (lane == 0) {
             P.list[s] = li;
             P.tile[s] = tk;
@@ -283,12 +340,16 @@ __device__ void bdec_produce(const BatchDecArgs &a, BPipe &P, int lane)
     __syncwarp();
 }
 
-// Consumer warps of the big-list phase.
-__device__ void bdec_consume(const BatchDecArgs &a, BPipe &P, uint16_t *s_qoff,
-                             uint32_t *s_warp)
+// Consumer warps of the big-list phase: warp w decodes sub-tile w of every
+// tile on its own (the same sub-tile decode as the single-stream decoder).
+// For differential lists the eight warps trade their sub-tile gap sums once
+// per tile (one barrier), and each keeps the list's running sum itself.
+__device__ void bdec_consume(const BatchDecArgs &a, BPipe &P, uint16_t *s_pos,
+                             uint32_t (*s_sum)[kWarps])
 {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    uint32_t carry = 0;  // running differential sum of the current list
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint16_t *pos = s_pos + warp * kSubQuads;
+    uint32_t carry = 0;  // the list's integer before the current tile
     for (uint32_t g = 0;; g++) {
         const int s = g % kBStages;
         if (!mbar_wait_bounded(&P.full[s], (g / kBStages) & 1u, kBPolls)) {
@@ -302,71 +363,23 @@ __device__ void bdec_consume(const BatchDecArgs &a, BPipe &P, uint16_t *s_qoff,
         const uint32_t k = P.tile[s];
         const uint32_t nql = (L.n + 3) / 4;
         const uint32_t last_nints = L.n - 4 * (nql - 1);
-        const uint32_t q0 = k * kBQuads;
-        const uint32_t nq = min((uint32_t)kBQuads, nql - q0);
-        const bool full = nq == kBQuads && (q0 + kBQuads < nql || last_nints == 4);
+        const uint32_t q0 = k * kBQuads + warp * kSubQuads;   // first quad of the sub-tile
         const bool skip = P.skip[s] != 0;
         if (k == 0)
             carry = L.prev;
-        const uint8_t *C = P.ctrl[g % kCRing] + P.hc[s];
-        const uint8_t *D = P.data[s];
-        const uint32_t h = P.hd[s];
-
-        uint32_t w = 0;
-#pragma unroll
-        for (int j = 0; j < 4; j++)
-            if (4u * tid + j < nq)
-                w |= (uint32_t)C[4 * tid + j] << (8 * j);
-        uint32_t cnt[4], tsum = 0;
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-            uint32_t lq = 4u * tid + j;
-            uint32_t c = (w >> (8 * j)) & 0xffu;
-            uint32_t nints = 4;
-            if (q0 + lq == nql - 1 && last_nints < 4) {
-                nints = last_nints;
-                c &= (1u << (2 * nints)) - 1u;
-            }
-            cnt[j] = lq < nq ? quad_count(c, nints) : 0u;
-            tsum += cnt[j];
-        }
-        uint32_t incl = warp_incl_scan(tsum);
-        if (lane == 31)
-            s_warp[warp] = incl;
-        named_sync(1, kThreads);
-        uint32_t wpre = 0;
-#pragma unroll
-        for (int j = 0; j < kWarps; j++)
-            wpre += j < warp ? s_warp[j] : 0u;
-        {
-            const uint32_t o0 = h + wpre + incl - tsum;
-            const uint32_t o1 = o0 + cnt[0], o2 = o1 + cnt[1], o3 = o2 + cnt[2];
-            reinterpret_cast<uint2 *>(s_qoff)[tid] = make_uint2(o0 | (o1 << 16), o2 | (o3 << 16));
-        }
-        named_sync(1, kThreads);
-
-        const uint32_t lq0 = warp * (32 * kBRounds) + lane;
-        uint32_t *op = a.out + L.out_off + 4 * (u64)(q0 + lq0);
-        const bool aligned = ((uintptr_t)(a.out + L.out_off) & 15u) == 0;
-        uint32_t v[kBRounds][4];
-#pragma unroll
-        for (int r = 0; r < kBRounds; r++) {
-            const uint32_t lq = lq0 + r * 32;
-            const bool valid = lq < nq;
-            uint32_t c = valid ? C[lq] : 0u;
-            const uint32_t nints = !valid ? 0u : (q0 + lq == nql - 1 ? last_nints : 4u);
-            if (nints < 4)
-                c &= (1u << (2 * nints)) - 1u;
-            const uint32_t p = valid ? s_qoff[lq] : h;
-            uint4 x;
-            if (full && __all_sync(0xffffffffu, c == 0))
-                x = widen_quad(D, p);
-            else
-                x = decode_quad(D, p, c);
-            v[r][0] = nints > 0 ? x.x : 0u;
-            v[r][1] = nints > 1 ? x.y : 0u;
-            v[r][2] = nints > 2 ? x.z : 0u;
-            v[r][3] = nints > 3 ? x.w : 0u;
+        const bool have = !skip && q0 < nql;
+        uint32_t v[kSubRounds][4] = {};
+        SubTile t;
+        t.nq = have ? min((uint32_t)kSubQuads, nql - q0) : 0u;
+        if (have) {
+            t.C = P.ctrl[g % kCRing] + P.hc[s] + warp * kSubQuads;
+            t.D = P.data[s];
+            t.base = P.hd[s] + P.soff[s][warp];
+            t.tail = q0 + t.nq == nql ? last_nints : 4u;
+            const uint32_t w = subtile_ctrl_word(t);
+            subtile_positions(t, w, pos);
+            __syncwarp();
+            subtile_gather(t, pos, v);
         }
         fence_proxy_async_smem();
         __syncwarp();
@@ -374,45 +387,48 @@ __device__ void bdec_consume(const BatchDecArgs &a, BPipe &P, uint16_t *s_qoff,
             mbar_arrive(&P.empty[s]);
 
         if (a.delta) {
-            uint32_t qexcl[kBRounds], wrun = 0;
+            uint32_t run = 0;   // this sub-tile's gaps so far
 #pragma unroll
-            for (int r = 0; r < kBRounds; r++) {
+            for (int r = 0; r < kSubRounds; r++) {
                 v[r][1] += v[r][0];
                 v[r][2] += v[r][1];
                 v[r][3] += v[r][2];
-                uint32_t qs = v[r][3];
-                uint32_t inc = warp_incl_scan(qs);
-                qexcl[r] = wrun + inc - qs;
-                wrun += __shfl_sync(0xffffffffu, inc, 31);
-            }
-            named_sync(1, kThreads);
-            if (lane == 0)
-                s_warp[warp] = wrun;
-            named_sync(1, kThreads);
-            uint32_t bpre = carry, vagg = 0;
-#pragma unroll
-            for (int j = 0; j < kWarps; j++) {
-                uint32_t t = s_warp[j];
-                bpre += j < warp ? t : 0u;
-                vagg += t;
-            }
-            carry += vagg;
-#pragma unroll
-            for (int r = 0; r < kBRounds; r++) {
-                const uint32_t add = bpre + qexcl[r];
+                const uint32_t qs = v[r][3];
+                const uint32_t inc = warp_incl_scan(qs);
+                const uint32_t add = run + inc - qs;
 #pragma unroll
                 for (int j = 0; j < 4; j++)
                     v[r][j] += add;
+                run += __shfl_sync(0xffffffffu, inc, 31);
             }
-        }
-        if (skip)
-            continue;
+            uint32_t *sums = s_sum[g & 1];   // double-buffered: the next tile's barrier
+            if (lane == 0)                   // orders these reads before the reuse
+                sums[warp] = run;
+            named_sync(1, kThreads);
+            uint32_t before = carry, all = 0;
 #pragma unroll
-        for (int r = 0; r < kBRounds; r++) {
-            const uint32_t lq = lq0 + r * 32;
-            if (lq >= nq)
+            for (int j = 0; j < kWarps; j++) {
+                const uint32_t x = sums[j];
+                before += j < warp ? x : 0u;
+                all += x;
+            }
+            carry += all;
+#pragma unroll
+            for (int r = 0; r < kSubRounds; r++)
+#pragma unroll
+                for (int j = 0; j < 4; j++)
+                    v[r][j] += before;
+        }
+        if (!have)
+            continue;
+        uint32_t *op = a.out + L.out_off + 4 * (u64)(q0 + lane);
+        const bool aligned = ((uintptr_t)(a.out + L.out_off) & 15u) == 0;
+#pragma unroll
+        for (int r = 0; r < kSubRounds; r++) {
+            const uint32_t lq = r * 32 + lane;
+            const uint32_t nints = subtile_nints(t, lq);
+            if (!nints)
                 continue;
-            const uint32_t nints = q0 + lq == nql - 1 ? last_nints : 4u;
             uint32_t *dst = op + 128 * r;
             if (nints == 4 && aligned) {
                 stg_stream128(dst, make_uint4(v[r][0], v[r][1], v[r][2], v[r][3]));
@@ -500,8 +516,8 @@ __global__ void __launch_bounds__(kBBlock, 3) batch_decode_kernel(BatchDecArgs a
 {
     extern __shared__ __align__(128) uint8_t dyn_smem[];
     BPipe &P = *reinterpret_cast<BPipe *>(dyn_smem);
-    __shared__ __align__(16) uint16_t s_qoff[kBQuads];
-    __shared__ uint32_t s_warp[kWarps];
+    __shared__ __align__(16) uint16_t s_pos[kBQuads];   // each warp's quad positions
+    __shared__ uint32_t s_sum[2][kWarps];                // sub-tile gap sums, per tile parity
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
@@ -517,7 +533,7 @@ __global__ void __launch_bounds__(kBBlock, 3) batch_decode_kernel(BatchDecArgs a
     if (warp == kWarps)
         bdec_produce(a, P, lane);
     else
-        bdec_consume(a, P, s_qoff, s_warp);
+        bdec_consume(a, P, s_pos, s_sum);
 
     // Small lists: every warp takes them one by one.
     const uint32_t *small = plan_small(a.plan);

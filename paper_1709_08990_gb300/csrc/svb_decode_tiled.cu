@@ -36,12 +36,12 @@
 #include "svb_device.cuh"
 #include "svb_internal.h"
 #include "svb_quad.cuh"
+#include "svb_subtile.cuh"
 
 namespace svb {
 
 constexpr int kTileQuads = 1024;                      // quads per tile (4096 integers)
 constexpr int kSubs = kTileQuads / kSubQuads;         // sub-tiles per tile = consumer warps
-constexpr int kSubRounds = kSubQuads / 32;            // quads per lane per sub-tile
 constexpr int kTileData = 16 * kTileQuads;            // data bytes per tile, at most
 constexpr int kStageData = kTileData + 64;            // + 16-byte phase + 2-word read slack
 constexpr int kStageCtrl = kTileQuads + 32;
@@ -382,23 +382,17 @@ __device__ void consume(const TiledArgs &a, Pipe &P, uint16_t *s_pos)
                 mbar_arrive(&P.empty[s]);
             continue;
         }
-        const uint32_t nq = (uint32_t)min((u64)kSubQuads, a.nquads - q0);
-        const bool full = nq == kSubQuads && (q0 + kSubQuads < a.nquads || last_nints == 4);
-        const uint8_t *C = P.ctrl[s] + P.hc[s] + warp * kSubQuads;
-        const uint8_t *D = P.data[s];
-        const uint32_t base = P.hd[s] + P.soff[s][warp];
+        SubTile t;
+        t.C = P.ctrl[s] + P.hc[s] + warp * kSubQuads;
+        t.D = P.data[s];
+        t.base = P.hd[s] + P.soff[s][warp];
+        t.nq = (uint32_t)min((u64)kSubQuads, a.nquads - q0);
+        t.tail = q0 + t.nq == a.nquads ? last_nints : 4u;
+        const bool full = t.full();
+        const uint8_t *D = t.D;
+        const uint32_t base = t.base;
         const uint32_t carry_in = kMode == kDelta ? P.carry[s][warp] : 0u;
-
-        // ---- control bytes -> staged position of each of the warp's quads ----
-        uint32_t w = 0;
-        if (((uintptr_t)C & 3u) == 0 && 4u * lane + 4u <= nq) {
-            w = reinterpret_cast<const uint32_t *>(C)[lane];
-        } else {
-#pragma unroll
-            for (int j = 0; j < 4; j++)
-                if (4u * lane + j < nq)
-                    w |= (uint32_t)C[4 * lane + j] << (8 * j);
-        }
+        const uint32_t w = subtile_ctrl_word(t);
         if (kMode == kSums && full && __all_sync(0xffffffffu, w == 0)) {
             // All 512 integers take one byte (Sec. 4: an all-zero control byte
             // covers 4 bytes): the gaps are the data bytes [base, base + 512).
@@ -427,74 +421,12 @@ __device__ void consume(const TiledArgs &a, Pipe &P, uint16_t *s_pos)
                 a.carries[sb] = t;
             continue;
         }
-        uint32_t o1, o2, o3, tsum;
-        if (full) {
-            // Byte j of cs = sum of the four codes of quad j; the multiply turns
-            // the four bytes into their running sums (at most 48, no carries).
-            uint32_t cs = (w & 0x33333333u) + ((w >> 2) & 0x33333333u);
-            cs = (cs & 0x0F0F0F0Fu) + ((cs >> 4) & 0x0F0F0F0Fu);
-            const uint32_t run = cs * 0x01010101u;
-            o1 = 4u + (run & 0xffu);
-            o2 = 8u + ((run >> 8) & 0xffu);
-            o3 = 12u + ((run >> 16) & 0xffu);
-            tsum = 16u + (run >> 24);
-        } else {
-            uint32_t cnt[4];
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                const uint32_t lq = 4u * lane + j;
-                uint32_t c = (w >> (8 * j)) & 0xffu;
-                uint32_t nints = 4;
-                if (q0 + lq == a.nquads - 1 && last_nints < 4) {
-                    nints = last_nints;
-                    c &= (1u << (2 * nints)) - 1u;
-                }
-                cnt[j] = lq < nq ? quad_count(c, nints) : 0u;
-            }
-            o1 = cnt[0];
-            o2 = o1 + cnt[1];
-            o3 = o2 + cnt[2];
-            tsum = o3 + cnt[3];
-        }
-        const uint32_t incl = warp_incl_scan(tsum);
-        {
-            const uint32_t o0 = base + incl - tsum;
-            reinterpret_cast<uint2 *>(pos)[lane] =
-                make_uint2(o0 | ((o0 + o1) << 16), (o0 + o2) | ((o0 + o3) << 16));
-        }
+        subtile_positions(t, w, pos);
         __syncwarp();
-
-        // ---- gather: one quad per lane per round ------------------------------
         uint32_t *op = a.out + 4 * (q0 + lane);
+        const uint32_t nq = t.nq;
         uint32_t v[kSubRounds][4];
-#pragma unroll
-        for (int r = 0; r < kSubRounds; r++) {
-            const uint32_t lq = r * 32 + lane;
-            uint4 x;
-            if (full) {
-                const uint32_t c = C[lq];
-                const uint32_t p = pos[lq];
-                if (__all_sync(0xffffffffu, c == 0))
-                    x = widen_quad(D, p);
-                else
-                    x = decode_quad(D, p, c);
-            } else {
-                const bool valid = lq < nq;
-                uint32_t c = valid ? C[lq] : 0u;
-                const uint32_t nints = !valid ? 0u : (q0 + lq == a.nquads - 1 ? last_nints : 4u);
-                if (nints < 4)
-                    c &= (1u << (2 * nints)) - 1u;
-                x = decode_quad(D, valid ? pos[lq] : base, c);
-                x.x = nints > 0 ? x.x : 0u;
-                x.y = nints > 1 ? x.y : 0u;
-                x.z = nints > 2 ? x.z : 0u;
-                x.w = nints > 3 ? x.w : 0u;
-            }
-            v[r][0] = x.x;
-            v[r][1] = x.y;
-            v[r][2] = x.z;
-            v[r][3] = x.w;
-        }
+        subtile_gather(t, pos, v);
         // This warp no longer reads stage s.
         fence_proxy_async_smem();
         __syncwarp();
