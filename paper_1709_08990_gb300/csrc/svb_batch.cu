@@ -77,6 +77,8 @@ struct BPipe {
     uint32_t hd[kBStages], hc[kBStages];
     uint32_t clist[kCRing], ctile[kCRing], chc[kCRing];   // what each ring slot holds
     uint32_t soff[kBStages][kBSubs];   // each sub-tile's data offset inside the tile
+    u64 out_off[kBStages];             // the tile's list: where its integers go,
+    uint32_t n[kBStages], prev[kBStages];   // how many, and its start value
 };
 
 __device__ __forceinline__ const uint32_t *plan_big(const PlanHeader *p)
@@ -127,18 +129,37 @@ __device__ __forceinline__ uint32_t tile_sub_offsets(const uint8_t *stage, uint3
             }
         }
     }
-    uint32_t mine = 0, run = 0;
+    // Reduce-scatter over the warp: after the exchanges across lane bits 4, 3
+    // and 2 each lane holds one sub-tile's sum over 8 lanes (sub-tile
+    // lane >> 2), and two more finish it over all 32.
+    const bool hi4 = lane & 16, hi3 = lane & 8, hi2 = lane & 4;
+    uint32_t b[4], c[2];
 #pragma unroll
-    for (int i = 0; i < kBSubs; i++) {
-        uint32_t t = acc[i];
-#pragma unroll
-        for (int d = 16; d >= 1; d >>= 1)
-            t += __shfl_xor_sync(0xffffffffu, t, d);
-        mine = lane == i ? run : mine;
-        run += t;
+    for (int j = 0; j < 4; j++) {
+        const uint32_t keep = hi4 ? acc[4 + j] : acc[j];
+        const uint32_t give = hi4 ? acc[j] : acc[4 + j];
+        b[j] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
     }
-    total = run;
-    return mine;
+#pragma unroll
+    for (int j = 0; j < 2; j++) {
+        const uint32_t keep = hi3 ? b[2 + j] : b[j];
+        const uint32_t give = hi3 ? b[j] : b[2 + j];
+        c[j] = keep + __shfl_xor_sync(0xffffffffu, give, 8);
+    }
+    uint32_t x = (hi2 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, hi2 ? c[0] : c[1], 4);
+    x += __shfl_xor_sync(0xffffffffu, x, 1);
+    x += __shfl_xor_sync(0xffffffffu, x, 2);
+    // Inclusive prefix over the sub-tiles, held by lanes 0, 4, .., 28.
+    uint32_t inc = x;
+#pragma unroll
+    for (int d = 4; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d)
+            inc += y;
+    }
+    total = __shfl_sync(0xffffffffu, inc, 28);
+    const uint32_t excl = __shfl_sync(0xffffffffu, inc - x, (4 * lane) & 31);
+    return lane < kBSubs ? excl : 0u;
 }
 
 __device__ __forceinline__ uint32_t tile_data_bytes(const uint8_t *C, uint32_t nq, bool last_tile,
@@ -292,6 +313,9 @@ __device__ void bdec_produce(const BatchDecArgs &a, BPipe &P, int lane)
         if (lane == 0) {
             P.list[s] = li;
             P.tile[s] = tk;
+            P.out_off[s] = L.out_off;
+            P.n[s] = L.n;
+            P.prev[s] = L.prev;
             P.skip[s] = cut ? 1u : 0u;
             P.hd[s] = (uint32_t)((uintptr_t)gd & 15u);
             P.hc[s] = P.chc[slot];
@@ -359,14 +383,15 @@ __device__ void bdec_consume(const BatchDecArgs &a, BPipe &P, uint16_t *s_pos,
         const uint32_t li = P.list[s];
         if (li == kNoList)
             break;
-        const svb_list L = a.lists[li];
+        const uint32_t n = P.n[s];
+        const u64 out_off = P.out_off[s];
         const uint32_t k = P.tile[s];
-        const uint32_t nql = (L.n + 3) / 4;
-        const uint32_t last_nints = L.n - 4 * (nql - 1);
+        const uint32_t nql = (n + 3) / 4;
+        const uint32_t last_nints = n - 4 * (nql - 1);
         const uint32_t q0 = k * kBQuads + warp * kSubQuads;   // first quad of the sub-tile
         const bool skip = P.skip[s] != 0;
         if (k == 0)
-            carry = L.prev;
+            carry = P.prev[s];
         const bool have = !skip && q0 < nql;
         uint32_t v[kSubRounds][4] = {};
         SubTile t;
@@ -421,8 +446,8 @@ __device__ void bdec_consume(const BatchDecArgs &a, BPipe &P, uint16_t *s_pos,
         }
         if (!have)
             continue;
-        uint32_t *op = a.out + L.out_off + 4 * (u64)(q0 + lane);
-        const bool aligned = ((uintptr_t)(a.out + L.out_off) & 15u) == 0;
+        uint32_t *op = a.out + out_off + 4 * (u64)(q0 + lane);
+        const bool aligned = ((uintptr_t)(a.out + out_off) & 15u) == 0;
 #pragma unroll
         for (int r = 0; r < kSubRounds; r++) {
             const uint32_t lq = r * 32 + lane;
