@@ -24,11 +24,11 @@
 #include "svb_internal.h"
 #include "svb_quad.cuh"
 #include "svb_subtile.cuh"
+#include "svb_subenc.cuh"
 
 namespace svb {
 
 constexpr int kBQuads = 1024;                // quads per tile
-constexpr int kBRounds = kBQuads / kThreads;
 constexpr int kBStages = 4;
 constexpr int kBStageData = 16 * kBQuads + 64;
 constexpr int kBStageCtrl = kBQuads + 32;
@@ -591,16 +591,17 @@ struct BatchEncArgs {
 
 constexpr int kEStages = 3;
 constexpr int kEStageBytes = 16 * kBQuads + 16;  // 4096 values + 16-byte phase
-constexpr int kEOutBytes = 16 * kBQuads + 32;
 
 struct EPipe {
     uint8_t vals[kEStages][kEStageBytes];
-    uint8_t outb[kEOutBytes];
+    uint32_t slice[kWarps][kEncSliceWords];   // each warp's data bytes, phased like the output
     uint64_t full[kEStages];
     uint64_t empty[kEStages];
     uint32_t list[kEStages];
     uint32_t tile[kEStages];
     uint32_t hv[kEStages];  // phase (mod 16) of the staged values
+    u64 out_off[kEStages];  // the tile's list: where its stream goes,
+    uint32_t n[kEStages], prev[kEStages];   // its integers and start value
 };
 
 __device__ void benc_produce(const BatchEncArgs &a, EPipe &P, int lane)
@@ -646,18 +647,21 @@ __device__ void benc_produce(const BatchEncArgs &a, EPipe &P, int lane)
         }
         const u64 i0 = (u64)k * 4 * kBQuads;
         const uint32_t cnt = (uint32_t)min((u64)4 * kBQuads, (u64)L.n - i0);
-        const uint8_t *gv = reinterpret_cast<const uint8_t *>(a.in + L.in_off + i0);
-        range_edges(gv, 4 * cnt, P.vals[s], lane);
+        const uint8_t *lo = reinterpret_cast<const uint8_t *>(a.in + L.in_off);
+        const uint8_t *gv = lo + 4 * i0;
+        const StagePlan pv = stage_plan(gv, 4 * cnt, lo, lo + 4 * (u64)L.n);
+        if (pv.edges)
+            range_edges(gv, 4 * cnt, P.vals[s], lane);
         if (lane == 0) {
-            const uint8_t *av;
-            uint32_t ov;
-            uint32_t bv = range_interior(gv, 4 * cnt, av, ov);
             P.list[s] = li;
             P.tile[s] = k;
             P.hv[s] = (uint32_t)((uintptr_t)gv & 15u);
-            mbar_arrive_expect_tx(&P.full[s], bv);
-            if (bv)
-                bulk_g2s(P.vals[s] + ov, av, bv, &P.full[s]);
+            P.out_off[s] = L.out_off;
+            P.n[s] = L.n;
+            P.prev[s] = L.prev;
+            mbar_arrive_expect_tx(&P.full[s], pv.bytes);
+            if (pv.bytes)
+                bulk_g2s(P.vals[s] + pv.dst_off, pv.src, pv.bytes, &P.full[s]);
         } else {
             mbar_arrive(&P.full[s]);
         }
@@ -675,11 +679,17 @@ __device__ void benc_produce(const BatchEncArgs &a, EPipe &P, int lane)
     __syncwarp();
 }
 
-__device__ void benc_consume(const BatchEncArgs &a, EPipe &P, uint32_t *s_warp, uint32_t *s_last)
+// Consumer warps of the big-list phase: warp w encodes sub-tile w of every
+// tile with the same per-warp code as the single-stream encoder.  A list's
+// tiles come in order to one CTA, so its data offset is a running sum: the
+// eight warps trade their sub-tile sizes once per tile (one barrier) and each
+// keeps the running offset and the list's last integer itself.
+__device__ void benc_consume(const BatchEncArgs &a, EPipe &P, uint32_t (*s_size)[kWarps])
 {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t sq0 = warp * kSubQuads;
     u64 run = 0;          // data bytes of the current list written so far
-    uint32_t before = 0;  // last value of the previous tile (differential)
+    uint32_t before = 0;  // the list's integer before the current tile (differential)
     for (uint32_t g = 0;; g++) {
         const int s = g % kEStages;
         if (!mbar_wait_bounded(&P.full[s], (g / kEStages) & 1u, kBPolls)) {
@@ -689,113 +699,60 @@ __device__ void benc_consume(const BatchEncArgs &a, EPipe &P, uint32_t *s_warp, 
         const uint32_t li = P.list[s];
         if (li == kNoList)
             break;
-        const svb_list L = a.lists[li];
-        const uint32_t k = P.tile[s];
-        const uint32_t nql = (L.n + 3) / 4;
-        const uint32_t last_nints = L.n - 4 * (nql - 1);
+        const uint32_t n = P.n[s], k = P.tile[s];
+        const u64 out_off = P.out_off[s];
+        const uint32_t nql = (n + 3) / 4;
+        const uint32_t last_nints = n - 4 * (nql - 1);
         const uint32_t q0 = k * kBQuads;
         const uint32_t nq = min((uint32_t)kBQuads, nql - q0);
+        const uint32_t cnt = min((uint32_t)(4 * kBQuads), n - 4 * q0);   // values in the tile
         if (k == 0) {
             run = 0;
-            before = L.prev;
+            before = P.prev[s];
         }
         const uint32_t *V = reinterpret_cast<const uint32_t *>(P.vals[s] + P.hv[s]);
-
-        // Values -> gaps -> lengths -> control bytes, one quad per lane per round.
-        uint32_t d[kBRounds][4], ctrl[kBRounds], qexcl[kBRounds], wrun = 0;
-        const uint32_t lq0 = warp * (32 * kBRounds) + lane;
-#pragma unroll
-        for (int r = 0; r < kBRounds; r++) {
-            const uint32_t lq = lq0 + r * 32;
-            const uint32_t nints = lq >= nq ? 0u : (q0 + lq == nql - 1 ? last_nints : 4u);
-            uint32_t x[4];
-#pragma unroll
-            for (int j = 0; j < 4; j++)
-                x[j] = (uint32_t)j < nints ? V[4 * lq + j] : 0u;
-            if (a.delta) {
-                const uint32_t pv = lq == 0 ? before : (nints ? V[4 * lq - 1] : 0u);
-                d[r][0] = x[0] - pv;
-                d[r][1] = x[1] - x[0];
-                d[r][2] = x[2] - x[1];
-                d[r][3] = x[3] - x[2];
-            } else {
-#pragma unroll
-                for (int j = 0; j < 4; j++)
-                    d[r][j] = x[j];
-            }
-            uint32_t c = 0, C = 0;
-#pragma unroll
-            for (int j = 0; j < 4; j++)
-                if ((uint32_t)j < nints) {
-                    const uint32_t Lb = byte_len(d[r][j]);
-                    c |= (Lb - 1) << (2 * j);
-                    C += Lb;
-                }
-            ctrl[r] = c;
-            if (nints)
-                a.out[L.out_off + q0 + lq] = (uint8_t)c;
-            const uint32_t inc = warp_incl_scan(C);
-            qexcl[r] = wrun + inc - C;
-            wrun += __shfl_sync(0xffffffffu, inc, 31);
-        }
-        if (tid == kThreads - 1)
-            *s_last = nq ? V[4 * nq - 1 - (q0 + nq == nql ? 4 - last_nints : 0)] : before;
-        if (lane == 0)
-            s_warp[warp] = wrun;
-        named_sync(1, kThreads);
-        uint32_t bpre = 0, agg = 0;
-#pragma unroll
-        for (int j = 0; j < kWarps; j++) {
-            const uint32_t t = s_warp[j];
-            bpre += j < warp ? t : 0u;
-            agg += t;
-        }
-        before = *s_last;
+        const uint32_t nvq = nq > sq0 ? min(nq - sq0, (uint32_t)kSubQuads) : 0u;
+        const uint32_t tail = q0 + nq == nql ? last_nints : 4u;
+        const bool fast = P.hv[s] == 0 && 4 * (sq0 + kSubQuads) <= cnt;
+        uint32_t nints[kEncRounds], d[kEncRounds][4], ctrl[kEncRounds], cb[kEncRounds];
+        auto prior = [&]() { return before; };
+        if (fast)
+            subenc_load<true>(V, sq0, nq, tail, a.delta != 0, prior, nints, d, ctrl, cb);
+        else
+            subenc_load<false>(V, sq0, nq, tail, a.delta != 0, prior, nints, d, ctrl, cb);
+        const uint32_t tile_last = V[cnt - 1];
+        // The control bytes use every staged value this warp loaded.
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0)
             mbar_arrive(&P.empty[s]);
 
-        // Assemble the tile's data bytes aligned like their destination.
-        uint8_t *dst = a.out + L.out_off + nql + run;
-        const uint32_t h = (uint32_t)((uintptr_t)dst & 15u);
-#pragma unroll
-        for (int r = 0; r < kBRounds; r++) {
-            const uint32_t lq = lq0 + r * 32;
-            const uint32_t nints = lq >= nq ? 0u : (q0 + lq == nql - 1 ? last_nints : 4u);
-            uint32_t p = h + bpre + qexcl[r];
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                if ((uint32_t)j < nints) {
-                    const uint32_t code = (ctrl[r] >> (2 * j)) & 3u;
-#pragma unroll
-                    for (uint32_t b = 0; b < 4; b++)
-                        if (b <= code)
-                            P.outb[p + b] = (uint8_t)(d[r][j] >> (8 * b));
-                    p += code + 1;
-                }
-            }
-        }
+        const uint32_t mine = subenc_bytes(cb);
+        uint32_t *sizes = s_size[g & 1];   // double-buffered: the next tile's barrier
+        if (lane == 0)                     // orders these reads before the reuse
+            sizes[warp] = mine;
         named_sync(1, kThreads);
-        uint8_t *adst = dst - h;
-        const uint32_t nchunks = (h + agg + 15u) >> 4;
-        for (uint32_t c = tid; c < nchunks; c += kThreads) {
-            if (16u * c >= h && 16u * c + 16u <= h + agg) {
-                stg_stream128(adst + 16u * c, *reinterpret_cast<const uint4 *>(P.outb + 16u * c));
-            } else {
-                for (uint32_t b = 0; b < 16; b++) {
-                    const uint32_t idx = 16u * c + b;
-                    if (idx >= h && idx < h + agg)
-                        adst[idx] = P.outb[idx];
-                }
-            }
+        uint32_t pre = 0, all = 0;
+#pragma unroll
+        for (int j = 0; j < kWarps; j++) {
+            const uint32_t x = sizes[j];
+            pre += j < warp ? x : 0u;
+            all += x;
         }
-        run += agg;
-        if (q0 + nq == nql && tid == 0) {
+        uint8_t *stream = a.out + out_off;
+        if (nvq) {
+            uint8_t *cdst = stream + q0 + sq0, *ddst = stream + nql + run + pre;
+            if (fast)
+                subenc_write<true>(P.slice[warp], cdst, ddst, nvq, nints, ctrl, cb, d);
+            else
+                subenc_write<false>(P.slice[warp], cdst, ddst, nvq, nints, ctrl, cb, d);
+        }
+        run += all;
+        before = tile_last;
+        if (q0 + nq == nql && warp == 0 && lane == 0) {
             a.sizes[li] = nql + run;
             atomicAdd(&a.hdr->total, (u64)nql + run);
         }
-        named_sync(1, kThreads);  // P.outb and s_warp free again
     }
 }
 
@@ -866,8 +823,7 @@ __global__ void __launch_bounds__(kBBlock, 3) batch_encode_kernel(BatchEncArgs a
 {
     extern __shared__ __align__(128) uint8_t dyn_smem[];
     EPipe &P = *reinterpret_cast<EPipe *>(dyn_smem);
-    __shared__ uint32_t s_warp[kWarps];
-    __shared__ uint32_t s_last;
+    __shared__ uint32_t s_size[2][kWarps];   // sub-tile data bytes, per tile parity
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
@@ -881,7 +837,7 @@ __global__ void __launch_bounds__(kBBlock, 3) batch_encode_kernel(BatchEncArgs a
     if (warp == kWarps)
         benc_produce(a, P, lane);
     else
-        benc_consume(a, P, s_warp, &s_last);
+        benc_consume(a, P, s_size);
 
     const uint32_t *small = plan_small(a.plan);
     const uint32_t nsmall = a.plan->nsmall;

@@ -31,17 +31,16 @@
 #include "svb_device.cuh"
 #include "svb_internal.h"
 #include "svb_quad.cuh"
+#include "svb_subenc.cuh"
 
 namespace svb {
 
 constexpr int kEtQuads = 1024;                  // quads per tile (4096 values)
 constexpr int kEtSubs = kEtQuads / kSubQuads;   // sub-tiles per tile = consumer warps
-constexpr int kEtRounds = kSubQuads / 32;       // quads per lane per sub-tile
 constexpr int kChunkTiles = 4;                  // tiles per look-back unit
 constexpr int kChunkSubs = kChunkTiles * kEtSubs;
 constexpr int kEtStages = 3;
 constexpr int kEtStageBytes = 16 * kEtQuads + 16;
-constexpr int kEtSliceWords = (16 * kSubQuads + 32) / 4;   // one warp's data bytes + phase
 constexpr int kEtBlock = kThreads + 64;          // 8 consumer warps, producer, chunk warp
 constexpr u64 kEtPolls = 1ull << 24;            // bound on a busy-polled wait
 constexpr u64 kEtSuspends = 1ull << 18;         // bound on a suspending wait ...
@@ -68,7 +67,7 @@ struct EncTiledArgs {
 
 struct EtPipe {
     uint8_t vals[kEtStages][kEtStageBytes];
-    uint32_t slice[kWarps][kEtSliceWords];   // each warp's data bytes, phased like the output
+    uint32_t slice[kWarps][kEncSliceWords];   // each warp's data bytes, phased like the output
     uint64_t full[kEtStages];
     uint64_t empty[kEtStages];
     uint64_t sizes_ready[2];    // consumers -> chunk warp: a chunk's sub-tile sizes are in
@@ -179,88 +178,6 @@ __device__ void et_produce(const EncTiledArgs &a, EtPipe &P, int lane)
     __syncwarp();
 }
 
-// L(v) - 1 (Sec. 3) with 0 -> 0: the index of the highest set bit over 8.
-__device__ __forceinline__ uint32_t extra_bytes(uint32_t v)
-{
-    return (31u - (uint32_t)__clz(v | 1u)) >> 3;
-}
-
-// One warp's sub-tile, read from the staged tile: lane l holds quad
-// sq0 + 32r + l in round r.  For each quad: the integers it holds (4, fewer
-// for the stream's last quad, 0 past the end), the coded values (gaps for
-// differential coding, the first from prev, Sec. 5; 0 past the end), its
-// control byte and its data bytes.  kFast: all 128 quads hold 4 integers and
-// the staged values are 16-byte aligned.
-template <bool kFast>
-__device__ __forceinline__ void et_quads(const EncTiledArgs &a, const uint32_t *V, u64 q0,
-                                         uint32_t sq0, uint32_t nq, uint32_t last_nints,
-                                         uint32_t (&nints)[kEtRounds], uint32_t (&d)[kEtRounds][4],
-                                         uint32_t (&ctrl)[kEtRounds], uint32_t (&cb)[kEtRounds])
-{
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int r = 0; r < kEtRounds; r++) {
-        const uint32_t lq = sq0 + 32 * r + lane;
-        if (kFast) {
-            nints[r] = 4;
-        } else {
-            nints[r] = lq >= nq ? 0u : (q0 + lq == a.nquads - 1 ? last_nints : 4u);
-        }
-        if (kFast) {
-            const uint4 v = *reinterpret_cast<const uint4 *>(V + 4 * lq);
-            d[r][0] = v.x;
-            d[r][1] = v.y;
-            d[r][2] = v.z;
-            d[r][3] = v.w;
-        } else {
-#pragma unroll
-            for (int j = 0; j < 4; j++)
-                d[r][j] = (uint32_t)j < nints[r] ? V[4 * lq + j] : 0u;
-        }
-    }
-    if (a.delta) {
-        uint32_t carry = 0;  // value before the lane's first one, in lane 0
-        if (lane == 0 && nints[0])
-            carry = sq0 ? V[4 * sq0 - 1] : (q0 == 0 ? a.prev : __ldg(a.in + 4 * q0 - 1));
-#pragma unroll
-        for (int r = 0; r < kEtRounds; r++) {
-            uint32_t pv = __shfl_up_sync(0xffffffffu, d[r][3], 1);
-            if (lane == 0)
-                pv = carry;
-            carry = __shfl_sync(0xffffffffu, d[r][3], 31);
-            const uint32_t x0 = d[r][0], x1 = d[r][1], x2 = d[r][2];
-            d[r][3] = nints[r] > 3 ? d[r][3] - x2 : 0u;
-            d[r][2] = nints[r] > 2 ? x2 - x1 : 0u;
-            d[r][1] = nints[r] > 1 ? x1 - x0 : 0u;
-            d[r][0] = nints[r] > 0 ? x0 - pv : 0u;
-        }
-    }
-    // Fields past the end are 0 and add nothing.
-#pragma unroll
-    for (int r = 0; r < kEtRounds; r++) {
-        uint32_t c = 0, C = nints[r];
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-            const uint32_t e = extra_bytes(d[r][j]);
-            c |= e << (2 * j);
-            C += e;
-        }
-        ctrl[r] = c;
-        cb[r] = C;
-    }
-}
-
-
-// 128-bit left shift of (s3:s2:s1:s0) by k in [0, 32] bits.
-__device__ __forceinline__ void shl128(uint32_t &s0, uint32_t &s1, uint32_t &s2, uint32_t &s3,
-                                       uint32_t k)
-{
-    s3 = __funnelshift_lc(s2, s3, k);
-    s2 = __funnelshift_lc(s1, s2, k);
-    s1 = __funnelshift_lc(s0, s1, k);
-    s0 = __funnelshift_lc(0u, s0, k);
-}
-
 // Chunk warp, once a chunk's sizing tiles are done: prefix of the sub-tile
 // sizes and the chunk's aggregate, published for the look-back.
 __device__ void et_chunk_scan(const EncTiledArgs &a, EtChunks &C, int b, u64 chunk, u64 etag)
@@ -302,97 +219,6 @@ __device__ void et_chunk_base(const EncTiledArgs &a, EtChunks &C, int b, u64 chu
         if (chunk + 1 == a.nchunks)
             st_relaxed(&a.hdr->total, a.nquads + base + agg);
     }
-}
-
-// One warp writes its sub-tile: control bytes straight to global memory; the
-// data bytes are laid end to end in the warp's shared slice at the phase of
-// their destination (word by word: each lane shifts its quad's 4..16 bytes to
-// their byte position and writes the words it completes, taking the partial
-// first word from the previous lane), then copied out with 16-byte stores.
-template <bool kFast>
-__device__ __forceinline__ void et_write(const EncTiledArgs &a, uint32_t *slice, uint8_t *dst,
-                                         u64 q0, uint32_t sq0, uint32_t nvq_any,
-                                         const uint32_t (&nints)[kEtRounds],
-                                         const uint32_t (&ctrl)[kEtRounds],
-                                         const uint32_t (&cb)[kEtRounds],
-                                         const uint32_t (&d)[kEtRounds][4])
-{
-    const int lane = threadIdx.x & 31;
-    const uint32_t h = (uint32_t)((uintptr_t)dst & 15u);
-    const uint32_t nvq = kFast ? (uint32_t)kSubQuads : nvq_any;
-    uint32_t run = 0, carry = 0, fidx = kEtNone, fword = 0;
-#pragma unroll
-    for (int r = 0; r < kEtRounds; r++) {
-        if (32u * r >= nvq)
-            break;
-        const uint32_t lq = sq0 + 32 * r + lane;
-        const uint32_t C = cb[r];
-        const uint32_t nint = kFast ? 4u : nints[r];
-        uint32_t L[4];
-#pragma unroll
-        for (int j = 0; j < 4; j++)
-            L[j] = (uint32_t)j < nint ? ((ctrl[r] >> (2 * j)) & 3u) + 1 : 0u;
-        if (nint)
-            a.out[q0 + lq] = (uint8_t)ctrl[r];
-        const uint32_t inc = warp_incl_scan(C);
-        const uint32_t pos = h + run + inc - C;
-        run += __shfl_sync(0xffffffffu, inc, 31);
-        // The quad's bytes end to end (Fig. 3's data layout), then moved to
-        // their phase inside a word.
-        uint32_t s0 = d[r][3], s1 = 0, s2 = 0, s3 = 0;
-        shl128(s0, s1, s2, s3, 8 * L[2]);
-        s0 |= d[r][2];
-        shl128(s0, s1, s2, s3, 8 * L[1]);
-        s0 |= d[r][1];
-        shl128(s0, s1, s2, s3, 8 * L[0]);
-        s0 |= d[r][0];
-        const uint32_t sh = 8 * (pos & 3);
-        const uint32_t t4 = __funnelshift_l(s3, 0u, sh);
-        const uint32_t t3 = __funnelshift_l(s2, s3, sh);
-        const uint32_t t2 = __funnelshift_l(s1, s2, sh);
-        const uint32_t t1 = __funnelshift_l(s0, s1, sh);
-        const uint32_t t0 = s0 << sh;
-        const uint32_t nfull = ((pos & 3) + C) >> 2;   // words this lane completes
-        const uint32_t tail = nfull == 0 ? t0 : nfull == 1 ? t1 : nfull == 2 ? t2
-                                                : nfull == 3 ? t3 : t4;
-        uint32_t pt = __shfl_up_sync(0xffffffffu, tail, 1);
-        if (lane == 0)
-            pt = carry;
-        carry = __shfl_sync(0xffffffffu, tail, 31);
-        const uint32_t w0 = t0 | pt;
-        uint32_t *wp = slice + (pos >> 2);
-        if (nfull > 0)
-            wp[0] = w0;
-        if (nfull > 1)
-            wp[1] = t1;
-        if (nfull > 2)
-            wp[2] = t2;
-        if (nfull > 3)
-            wp[3] = t3;
-        if (lq + 1 == sq0 + nvq && ((pos + C) & 3u)) {   // the sub-tile's last, partial word
-            fidx = (pos + C) >> 2;
-            fword = nfull ? tail : w0;
-        }
-    }
-    if (fidx != kEtNone)
-        slice[fidx] = fword;
-    __syncwarp();
-    const uint8_t *sb = reinterpret_cast<const uint8_t *>(slice);
-    uint8_t *adst = dst - h;
-    const uint32_t end = h + run;
-    const uint32_t c0 = (h + 15) >> 4, c1 = end >> 4;   // whole 16-byte chunks [c0, c1)
-    for (uint32_t c = c0 + lane; c < c1; c += 32)
-        stg_stream128(adst + 16 * c, *reinterpret_cast<const uint4 *>(sb + 16 * c));
-    if (lane < 16) {
-        const uint32_t i = h + lane;
-        if (i < min(16 * c0, end))
-            adst[i] = sb[i];
-    } else {
-        const uint32_t i = 16 * c1 + (lane - 16);
-        if (c1 >= c0 && i < end)
-            adst[i] = sb[i];
-    }
-    __syncwarp();
 }
 
 // The chunk warp: for each chunk of this CTA, in order, once the consumers
@@ -455,11 +281,13 @@ __device__ void et_consume(const EncTiledArgs &a, EtPipe &P, EtChunks &C, u64 et
         // Whole sub-tile of 512 integers, staged 16-byte aligned: no per-quad
         // end checks.
         const bool fast = P.hv[s] == 0 && 4 * (q0 + sq0 + kSubQuads) <= a.n;
-        uint32_t nints[kEtRounds], d[kEtRounds][4], ctrl[kEtRounds], cb[kEtRounds];
+        uint32_t nints[kEncRounds], d[kEncRounds][4], ctrl[kEncRounds], cb[kEncRounds];
+        const uint32_t tail = q0 + nq == a.nquads ? last_nints : 4u;
+        auto before = [&]() { return q0 == 0 ? a.prev : __ldg(a.in + 4 * q0 - 1); };
         if (fast)
-            et_quads<true>(a, V, q0, sq0, nq, last_nints, nints, d, ctrl, cb);
+            subenc_load<true>(V, sq0, nq, tail, a.delta, before, nints, d, ctrl, cb);
         else
-            et_quads<false>(a, V, q0, sq0, nq, last_nints, nints, d, ctrl, cb);
+            subenc_load<false>(V, sq0, nq, tail, a.delta, before, nints, d, ctrl, cb);
         // The control bytes use every staged value this warp loaded, so its
         // loads are complete; the fence orders them before the refill.
         fence_proxy_async_smem();
@@ -470,13 +298,7 @@ __device__ void et_consume(const EncTiledArgs &a, EtPipe &P, EtChunks &C, u64 et
         const u64 chunk = tile / kChunkTiles;
 
         if (pass == 0) {
-            uint32_t t = 0;
-#pragma unroll
-            for (int r = 0; r < kEtRounds; r++)
-                t += cb[r];
-#pragma unroll
-            for (int k = 16; k >= 1; k >>= 1)
-                t += __shfl_xor_sync(0xffffffffu, t, k);
+            const uint32_t t = subenc_bytes(cb);
             const int b = sized & 1;
             if (lane == 0) {
                 C.size[b][ti * kEtSubs + warp] = t;
@@ -504,9 +326,9 @@ __device__ void et_consume(const EncTiledArgs &a, EtPipe &P, EtChunks &C, u64 et
         }
         uint8_t *dst = data_base + C.base[b] + C.excl[b][ti * kEtSubs + warp];
         if (fast)
-            et_write<true>(a, P.slice[warp], dst, q0, sq0, nvq, nints, ctrl, cb, d);
+            subenc_write<true>(P.slice[warp], a.out + q0 + sq0, dst, nvq, nints, ctrl, cb, d);
         else
-            et_write<false>(a, P.slice[warp], dst, q0, sq0, nvq, nints, ctrl, cb, d);
+            subenc_write<false>(P.slice[warp], a.out + q0 + sq0, dst, nvq, nints, ctrl, cb, d);
     }
 }
 
