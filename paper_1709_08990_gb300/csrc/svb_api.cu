@@ -76,15 +76,10 @@ struct DeviceCache {
 constexpr int kMaxDevices = 64;
 DeviceCache g_cache[kMaxDevices];
 
-template <class F>
-size_t run_sync(size_t n, F &&launch)
+// Grows c's workspace to hold a launch over n integers (zeroed when grown);
+// call with c.mu held.
+int ensure_workspace(DeviceCache &c, size_t n, cudaStream_t s)
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-        return set_error(SVB_ECUDA);
-    DeviceCache &c = g_cache[dev];
-    std::lock_guard<std::mutex> lock(c.mu);
-    cudaStream_t s = t_stream;
     size_t need = svb_workspace_size(n);
     if (c.bytes < need) {
         size_t grow = std::max(need, 2 * c.bytes);
@@ -97,16 +92,30 @@ size_t run_sync(size_t n, F &&launch)
         if (cudaMalloc(&c.ws, grow) != cudaSuccess) {
             cudaGetLastError();
             c.ws = nullptr;
-            return set_error(SVB_ENOMEM);
+            return SVB_ENOMEM;
         }
         if (cudaMemsetAsync(c.ws, 0, grow, s) != cudaSuccess)
-            return set_error(SVB_ECUDA);
+            return SVB_ECUDA;
         c.bytes = grow;
     }
     if (!c.h_res && cudaMallocHost(&c.h_res, sizeof(svb_result)) != cudaSuccess) {
         c.h_res = nullptr;
-        return set_error(SVB_ENOMEM);
+        return SVB_ENOMEM;
     }
+    return SVB_OK;
+}
+
+template <class F>
+size_t run_sync(size_t n, F &&launch)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return set_error(SVB_ECUDA);
+    DeviceCache &c = g_cache[dev];
+    std::lock_guard<std::mutex> lock(c.mu);
+    cudaStream_t s = t_stream;
+    if (int st = ensure_workspace(c, n, s))
+        return set_error(st);
     auto *d_res = reinterpret_cast<svb::DeviceResult *>(static_cast<char *>(c.ws) +
                                                          svb::kResultOffset);
     int st = launch(c.ws, d_res, s);
@@ -155,6 +164,152 @@ struct ScratchCache {
     size_t bytes = 0;
 };
 ScratchCache g_append_scratch[kMaxDevices];
+
+// ---- host-buffer decode in pieces ------------------------------------------
+//
+// For a plain stream of many tiles the copy in, the decode and the copy out
+// overlap: the control bytes go first and the data bytes follow in chunks on
+// a second stream; once the offsets pass has placed every tile, each group of
+// tiles is decoded as soon as the chunk holding its last data byte has
+// landed, and its integers go back to the host on a third stream while the
+// next group decodes.  The two copy directions run at the same time.
+
+constexpr u64 kPieceTiles = 4096;          // tiles per decode launch (16 M integers)
+constexpr size_t kCopyChunk = 64u << 20;   // bytes per host-to-device copy
+constexpr int kMaxPieces = 256;
+constexpr int kMaxCopies = 256;
+
+struct HostPipe {
+    bool ready = false;
+    cudaStream_t s_cmp = nullptr, s_in = nullptr, s_out = nullptr;
+    cudaEvent_t start = nullptr, in_done = nullptr, cmp_done = nullptr;
+    cudaEvent_t in_ev[kMaxCopies] = {}, dec_ev[kMaxPieces] = {};
+    u64 *h_meta = nullptr;                  // pinned: error, total, piece offsets
+    svb::DeviceResult *d_res = nullptr;     // one result per piece
+    svb_result *h_res = nullptr;            // pinned copy of those
+};
+HostPipe g_pipe[kMaxDevices];
+
+int pipe_init(HostPipe &p)
+{
+    if (p.ready)
+        return SVB_OK;
+    const unsigned ef = cudaEventDisableTiming;
+    bool ok = cudaStreamCreateWithFlags(&p.s_cmp, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&p.s_in, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&p.s_out, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&p.start, ef) == cudaSuccess &&
+              cudaEventCreateWithFlags(&p.in_done, ef) == cudaSuccess &&
+              cudaEventCreateWithFlags(&p.cmp_done, ef) == cudaSuccess;
+    for (int i = 0; ok && i < kMaxCopies; i++)
+        ok = cudaEventCreateWithFlags(&p.in_ev[i], ef) == cudaSuccess;
+    for (int i = 0; ok && i < kMaxPieces; i++)
+        ok = cudaEventCreateWithFlags(&p.dec_ev[i], ef) == cudaSuccess;
+    ok = ok && cudaMallocHost(&p.h_meta, (2 + kMaxPieces) * sizeof(u64)) == cudaSuccess &&
+         cudaMalloc(&p.d_res, kMaxPieces * sizeof(svb::DeviceResult)) == cudaSuccess &&
+         cudaMallocHost(&p.h_res, kMaxPieces * sizeof(svb_result)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        return SVB_ENOMEM;
+    }
+    p.ready = true;
+    return SVB_OK;
+}
+
+size_t decode_host_pieces(const uint8_t *h_in, u64 in_len, u64 n, uint32_t *h_out, uint8_t *d_in,
+                          uint32_t *d_out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return set_error(SVB_ECUDA);
+    DeviceCache &c = g_cache[dev];
+    std::lock_guard<std::mutex> lock(c.mu);
+    HostPipe &p = g_pipe[dev];
+    cudaStream_t caller = t_stream;
+    if (int st = pipe_init(p))
+        return set_error(st);
+    if (int st = ensure_workspace(c, n, caller))
+        return set_error(st);
+    const u64 nquads = (n + 3) / 4;
+    const u64 tile_ints = svb::decode_tile_ints();
+    const u64 ntiles = (n + tile_ints - 1) / tile_ints;
+    const u64 piece = std::max<u64>(kPieceTiles, (ntiles + kMaxPieces - 1) / kMaxPieces);
+    const u64 npieces = (ntiles + piece - 1) / piece;
+    const u64 dbytes = in_len - nquads;
+    const size_t chunk = std::max<size_t>(kCopyChunk, (dbytes + kMaxCopies - 1) / kMaxCopies);
+    const u64 ncopies = (dbytes + chunk - 1) / chunk;
+    const svb::WsLayout L = svb::ws_layout(n);
+    const u64 *offs = reinterpret_cast<const u64 *>(static_cast<char *>(c.ws) + L.offs);
+
+    // After the caller's earlier work (and the workspace's zeroing).
+    if (cudaEventRecord(p.start, caller) != cudaSuccess ||
+        cudaStreamWaitEvent(p.s_cmp, p.start, 0) != cudaSuccess ||
+        cudaStreamWaitEvent(p.s_in, p.start, 0) != cudaSuccess ||
+        cudaStreamWaitEvent(p.s_out, p.start, 0) != cudaSuccess)
+        return set_error(SVB_ECUDA);
+    bool ok = cudaMemcpyAsync(d_in, h_in, nquads, cudaMemcpyHostToDevice, p.s_cmp) == cudaSuccess;
+    for (u64 j = 0; ok && j < ncopies; j++) {
+        const u64 o = nquads + j * chunk, len = std::min<u64>(chunk, in_len - o);
+        ok = cudaMemcpyAsync(d_in + o, h_in + o, len, cudaMemcpyHostToDevice, p.s_in) ==
+                 cudaSuccess &&
+             cudaEventRecord(p.in_ev[j], p.s_in) == cudaSuccess;
+    }
+    ok = ok && cudaEventRecord(p.in_done, p.s_in) == cudaSuccess;
+    // Offsets, then the error word, the stream size and each piece's data offset.
+    ok = ok && svb::launch_offsets(d_in, in_len, n, c.ws, p.s_cmp, spin_limit()) == 0 &&
+         cudaMemcpyAsync(p.h_meta, static_cast<char *>(c.ws) + offsetof(svb::WsHeader, error),
+                         2 * sizeof(u64), cudaMemcpyDeviceToHost, p.s_cmp) == cudaSuccess &&
+         cudaMemcpy2DAsync(p.h_meta + 2, sizeof(u64), offs, piece * (tile_ints / 512) * sizeof(u64),
+                           sizeof(u64), npieces, cudaMemcpyDeviceToHost, p.s_cmp) == cudaSuccess &&
+         cudaStreamSynchronize(p.s_cmp) == cudaSuccess;
+    if (!ok)
+        return set_error(SVB_ECUDA);
+    const u64 err = p.h_meta[0], total = p.h_meta[1];
+    u64 pieces_run = 0;
+    if (err) {
+        // One decode over everything: it sees the error, skips the work and
+        // readies the workspace for the next call.
+        ok = cudaStreamWaitEvent(p.s_cmp, p.in_done, 0) == cudaSuccess &&
+             svb::launch_decode_range(d_in, n, d_out, c.ws, p.d_res, p.s_cmp, 0, ntiles) == 0;
+        pieces_run = 1;
+    } else {
+        for (u64 k = 0; ok && k < npieces; k++) {
+            const u64 t0 = k * piece, t1 = std::min(t0 + piece, ntiles);
+            // Data bytes this piece may read: its own, plus up to 15 of the
+            // next piece's (tiles are copied as 16-byte-aligned ranges).
+            const u64 dend = k + 1 < npieces ? p.h_meta[2 + k + 1] : total - nquads;
+            const u64 need = std::min<u64>(dend + 16, dbytes);
+            if (need)
+                ok = cudaStreamWaitEvent(p.s_cmp, p.in_ev[std::min<u64>((need - 1) / chunk,
+                                                                        ncopies - 1)],
+                                         0) == cudaSuccess;
+            ok = ok &&
+                 svb::launch_decode_range(d_in, n, d_out, c.ws, p.d_res + k, p.s_cmp, t0, t1) ==
+                     0 &&
+                 cudaEventRecord(p.dec_ev[k], p.s_cmp) == cudaSuccess &&
+                 cudaStreamWaitEvent(p.s_out, p.dec_ev[k], 0) == cudaSuccess;
+            const u64 i0 = t0 * tile_ints, i1 = std::min(t1 * tile_ints, n);
+            ok = ok && cudaMemcpyAsync(h_out + i0, d_out + i0, 4 * (i1 - i0),
+                                       cudaMemcpyDeviceToHost, p.s_out) == cudaSuccess;
+        }
+        pieces_run = npieces;
+    }
+    ok = ok && cudaEventRecord(p.cmp_done, p.s_cmp) == cudaSuccess &&
+         cudaStreamWaitEvent(p.s_out, p.cmp_done, 0) == cudaSuccess &&
+         cudaStreamWaitEvent(p.s_out, p.in_done, 0) == cudaSuccess &&
+         cudaMemcpyAsync(p.h_res, p.d_res, pieces_run * sizeof(svb_result),
+                         cudaMemcpyDeviceToHost, p.s_out) == cudaSuccess &&
+         cudaStreamSynchronize(p.s_out) == cudaSuccess;
+    if (!ok)
+        return set_error(SVB_ECUDA);
+    if (err)
+        return set_error((int)err);
+    for (u64 k = 0; k < pieces_run; k++)
+        if (p.h_res[k].status != SVB_OK)
+            return set_error((int)p.h_res[k].status);
+    t_last_error = SVB_OK;
+    return (size_t)total;
+}
 
 }  // namespace
 
@@ -222,6 +377,11 @@ size_t svb_decode_host(const uint8_t *h_in, size_t in_len, size_t n, uint32_t *h
         return set_error(SVB_OK);
     if (!h_in || !h_out || !d_in || !d_out)
         return set_error(SVB_EINVAL);
+    // Large plain streams: copies and decode overlap, piece by piece.
+    if (!delta && n >= 2 * kPieceTiles * svb::decode_tile_ints() &&
+        in_len >= ((u64)n + 3) / 4 &&
+        g_decode_variant.load(std::memory_order_relaxed) != SVB_DECODE_SINGLE_PASS)
+        return decode_host_pieces(h_in, in_len, n, h_out, d_in, d_out);
     cudaStream_t s = t_stream;
     if (cudaMemcpyAsync(d_in, h_in, in_len, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return set_error(SVB_ECUDA);

@@ -237,6 +237,7 @@ struct TiledArgs {
     DeviceResult *result;
     u64 spin_limit;
     u64 per_cta;        // kSums: tiles per CTA (contiguous ranges)
+    u64 tile0, tile1;   // decoding: the tiles [tile0, tile1) to decode
     uint32_t prev;
     uint32_t out_aligned;
 };
@@ -261,7 +262,8 @@ __device__ __forceinline__ u64 tile_of(const TiledArgs &a, u64 first, uint32_t k
         const u64 end = min(first + a.per_cta, a.ntiles);
         return first + k < end ? first + k : a.ntiles;
     }
-    return first + (u64)k * gridDim.x;
+    const u64 t = a.tile0 + first + (u64)k * gridDim.x;
+    return t < a.tile1 ? t : a.ntiles;
 }
 
 // Producer warp: fill stages with tiles until none is left, then post one
@@ -618,54 +620,89 @@ static int offsets_grid()
     return g;
 }
 
-int launch_decode_tiled(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, uint32_t prev,
-                        bool delta, void *ws, DeviceResult *result, cudaStream_t stream,
-                        u64 spin_limit)
+// Offsets pass alone: sub-tile offsets, stream size and the truncation
+// verdict into the workspace (the first half of launch_decode_tiled).
+int launch_offsets(const uint8_t *in, u64 in_len, u64 n, void *ws, cudaStream_t stream,
+                   u64 spin_limit)
 {
     const WsLayout L = ws_layout(n);
     const u64 nquads = (n + 3) / 4;
-    const u64 ntiles = (nquads + kTileQuads - 1) / kTileQuads;
-    const u64 nsubs = (nquads + kSubQuads - 1) / kSubQuads;
-    WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
-    u64 *offs = reinterpret_cast<u64 *>(static_cast<char *>(ws) + L.offs);
-    uint32_t *carries = reinterpret_cast<uint32_t *>(static_cast<char *>(ws) + L.carries);
-    TileStatus *st = reinterpret_cast<TileStatus *>(static_cast<char *>(ws) + L.status);
-
     OffsetsArgs o;
     o.in = in;
     o.in_len = in_len;
     o.n = n;
     o.nquads = nquads;
-    o.nsubs = nsubs;
+    o.nsubs = (nquads + kSubQuads - 1) / kSubQuads;
     o.groups = (nquads + kOffGroupQuads - 1) / kOffGroupQuads;
     u64 ogrid = min((u64)offsets_grid(), o.groups);
     o.per_cta = (o.groups + ogrid - 1) / ogrid;
     ogrid = (o.groups + o.per_cta - 1) / o.per_cta;  // no CTA without groups
-    o.offs = offs;
-    o.hdr = hdr;
-    o.st = st;
+    o.offs = reinterpret_cast<u64 *>(static_cast<char *>(ws) + L.offs);
+    o.hdr = reinterpret_cast<WsHeader *>(ws);
+    o.st = reinterpret_cast<TileStatus *>(static_cast<char *>(ws) + L.status);
     o.spin_limit = spin_limit;
     o.in_aligned = (((uintptr_t)in) & 15u) == 0;
     prof_begin("offsets_kernel", stream);
     offsets_kernel<<<(unsigned)ogrid, kThreads, 0, stream>>>(o);
     prof_end(stream);
+    return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
 
+static TiledArgs tiled_args(const uint8_t *in, u64 n, uint32_t *out, uint32_t prev, void *ws,
+                            DeviceResult *result, u64 spin_limit)
+{
+    const WsLayout L = ws_layout(n);
+    const u64 nquads = (n + 3) / 4;
     TiledArgs t;
     t.in = in;
     t.n = n;
     t.nquads = nquads;
-    t.ntiles = ntiles;
-    t.nsubs = nsubs;
+    t.ntiles = (nquads + kTileQuads - 1) / kTileQuads;
+    t.nsubs = (nquads + kSubQuads - 1) / kSubQuads;
     t.out = out;
-    t.offs = offs;
-    t.carries = carries;
-    t.hdr = hdr;
-    t.st = st;
+    t.offs = reinterpret_cast<u64 *>(static_cast<char *>(ws) + L.offs);
+    t.carries = reinterpret_cast<uint32_t *>(static_cast<char *>(ws) + L.carries);
+    t.hdr = reinterpret_cast<WsHeader *>(ws);
+    t.st = reinterpret_cast<TileStatus *>(static_cast<char *>(ws) + L.status);
     t.result = result;
     t.spin_limit = spin_limit;
     t.per_cta = 0;
+    t.tile0 = 0;
+    t.tile1 = t.ntiles;
     t.prev = prev;
     t.out_aligned = (((uintptr_t)out) & 15u) == 0;
+    return t;
+}
+
+u64 decode_tile_ints()
+{
+    return 4 * (u64)kTileQuads;
+}
+
+// Plain decode of the tiles [tile0, tile1) after launch_offsets; out is the
+// whole array's output.  Each launch finishes the workspace's launch record,
+// so give each its own result.
+int launch_decode_range(const uint8_t *in, u64 n, uint32_t *out, void *ws, DeviceResult *result,
+                        cudaStream_t stream, u64 tile0, u64 tile1)
+{
+    TiledArgs t = tiled_args(in, n, out, 0, ws, result, 0);
+    t.tile0 = tile0;
+    t.tile1 = min(tile1, t.ntiles);
+    const u64 grid = max((u64)1, min((u64)tiled_grid<kPlain>(), t.tile1 - min(tile0, t.tile1)));
+    prof_begin("decode_tiled_kernel<plain>", stream);
+    decode_tiled_kernel<kPlain><<<(unsigned)grid, kDecBlock, sizeof(Pipe), stream>>>(t);
+    prof_end(stream);
+    return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+int launch_decode_tiled(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, uint32_t prev,
+                        bool delta, void *ws, DeviceResult *result, cudaStream_t stream,
+                        u64 spin_limit)
+{
+    if (launch_offsets(in, in_len, n, ws, stream, spin_limit) != 0)
+        return 3;
+    TiledArgs t = tiled_args(in, n, out, prev, ws, result, spin_limit);
+    const u64 ntiles = t.ntiles;
     if (delta) {
         // Sums pass over contiguous ranges, then the decode with carries.
         u64 sgrid = min((u64)tiled_grid<kSums>(), ntiles);

@@ -24,6 +24,15 @@ int launch_decode_tiled(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, uin
                         bool delta, void *ws, DeviceResult *result, cudaStream_t stream,
                         u64 spin_limit);
 
+// Its two halves, for decoding in pieces: the offsets pass (sub-tile offsets,
+// stream size and truncation verdict into the workspace), then plain decodes
+// of tile ranges [tile0, tile1) of decode_tile_ints() integers each tile.
+int launch_offsets(const uint8_t *in, u64 in_len, u64 n, void *ws, cudaStream_t stream,
+                   u64 spin_limit);
+int launch_decode_range(const uint8_t *in, u64 n, uint32_t *out, void *ws, DeviceResult *result,
+                        cudaStream_t stream, u64 tile0, u64 tile1);
+u64 decode_tile_ints();
+
 int launch_encode(const uint32_t *in, u64 n, uint8_t *out, uint32_t prev, bool delta, void *ws,
                   DeviceResult *result, cudaStream_t stream, u64 spin_limit);
 u64 encode_tiles(u64 n);

@@ -269,3 +269,33 @@ def test_repeated_runs_are_identical(delta, variant):
         assert bool(torch.equal(got, want_d))
         back = svb.decode(want_d, x.size, delta=delta, checked=False)
         assert bool(torch.equal(back, d_x))
+
+
+def test_host_decode_in_pieces():
+    """A plain stream of 40 M integers through svb_decode_host takes the
+    overlapped path (copies in and out and the decode in pieces of 4096
+    tiles); the result and the size equal the oracle's, and a truncated
+    stream reports SVB_ETRUNCATED and leaves the library usable."""
+    n = 40_000_003
+    x = W.skewed_lengths(91, n)
+    want = oracle.encode(x)
+    h_in = torch.from_numpy(want).pin_memory()
+    h_out = torch.empty(n, dtype=torch.int32).pin_memory()
+    d_in = torch.empty(want.size, dtype=torch.uint8, device=DEV)
+    d_out = torch.empty(n, dtype=torch.int32, device=DEV)
+    for _ in range(2):
+        k = svb.svb_decode_host(h_in, want.size, n, h_out, 0, 0, d_in, d_out)
+        assert k == want.size
+        assert np.array_equal(h_out.numpy().view(np.uint32), x)
+    with pytest.raises(svb.SvbError) as e:
+        svb.svb_decode_host(h_in, want.size - 5, n, h_out, 0, 0, d_in, d_out)
+    assert e.value.status == svb.SVB_ETRUNCATED
+    h_out.zero_()
+    assert svb.svb_decode_host(h_in, want.size, n, h_out, 0, 0, d_in, d_out) == want.size
+    assert np.array_equal(h_out.numpy().view(np.uint32), x)
+    # differential streams take the one-piece path
+    xs = np.cumsum(x.astype(np.uint64)).astype(np.uint32)
+    ws = oracle.encode(xs, delta=True)
+    h_in2 = torch.from_numpy(ws).pin_memory()
+    assert svb.svb_decode_host(h_in2, ws.size, n, h_out, 0, 1, d_in, d_out) == ws.size
+    assert np.array_equal(h_out.numpy().view(np.uint32), xs)
