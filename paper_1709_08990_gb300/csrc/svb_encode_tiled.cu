@@ -284,7 +284,11 @@ __device__ void et_consume(const EncTiledArgs &a, EtPipe &P, EtChunks &C, u64 et
         uint32_t nints[kEncRounds], d[kEncRounds][4], ctrl[kEncRounds], cb[kEncRounds];
         const uint32_t tail = q0 + nq == a.nquads ? last_nints : 4u;
         auto before = [&]() { return q0 == 0 ? a.prev : __ldg(a.in + 4 * q0 - 1); };
-        if (fast)
+        const bool sizing = P.pass[s] == 0;
+        if (fast && sizing)
+            subenc_load<true, decltype(before), true>(V, sq0, nq, tail, a.delta, before, nints, d,
+                                                      ctrl, cb);
+        else if (fast)
             subenc_load<true>(V, sq0, nq, tail, a.delta, before, nints, d, ctrl, cb);
         else
             subenc_load<false>(V, sq0, nq, tail, a.delta, before, nints, d, ctrl, cb);

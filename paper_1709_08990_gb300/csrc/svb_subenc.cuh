@@ -22,7 +22,9 @@
 namespace svb {
 
 constexpr int kEncRounds = kSubQuads / 32;                  // quads per lane per sub-tile
-constexpr int kEncSliceWords = (16 * kSubQuads + 32) / 4;   // one warp's data bytes + phase
+// One warp's data bytes (at most 16 per quad) at a phase of up to 15 bytes,
+// rounded to 16-byte chunks, plus a spare word no data byte reaches.
+constexpr int kEncSliceWords = (16 * kSubQuads + 32) / 4;
 
 // L(v) - 1 (Sec. 3) with 0 -> 0: the index of the highest set bit over 8.
 __device__ __forceinline__ uint32_t extra_bytes(uint32_t v)
@@ -47,8 +49,9 @@ __device__ __forceinline__ void shl128(uint32_t &s0, uint32_t &s1, uint32_t &s2,
 // sq0 == 0; otherwise the preceding integer is V[4 * sq0 - 1]).  kFast: all
 // 128 quads hold 4 integers and V is 16-byte aligned.  Out: per round the
 // integers of the lane's quad (0 past the end), the coded values (0 past the
-// end), the control byte and the quad's data bytes.
-template <bool kFast, class Before>
+// end), the control byte (left 0 with kSizeOnly, when only sizes are
+// needed) and the quad's data bytes.
+template <bool kFast, class Before, bool kSizeOnly = false>
 __device__ __forceinline__ void subenc_load(const uint32_t *V, uint32_t sq0, uint32_t nq,
                                             uint32_t tail, bool delta, Before before,
                                             uint32_t (&nints)[kEncRounds],
@@ -97,10 +100,11 @@ __device__ __forceinline__ void subenc_load(const uint32_t *V, uint32_t sq0, uin
 #pragma unroll
         for (int j = 0; j < 4; j++) {
             const uint32_t e = extra_bytes(d[r][j]);
-            c |= e << (2 * j);
+            if (!kSizeOnly)
+                c |= e << (2 * j);
             C += e;
         }
-        ctrl[r] = c;
+        ctrl[r] = c;   // kSizeOnly: 0, only the byte counts are needed
         cb[r] = C;
     }
 }
@@ -130,6 +134,7 @@ __device__ __forceinline__ void subenc_write(uint32_t *slice, uint8_t *ctrl_dst,
                                              const uint32_t (&d)[kEncRounds][4])
 {
     constexpr uint32_t kNone = 0xffffffffu;
+    constexpr uint32_t kSpare = kEncSliceWords - 1;   // never holds data bytes
     const int lane = threadIdx.x & 31;
     const uint32_t h = (uint32_t)((uintptr_t)dst & 15u);
     const uint32_t nvq = kFast ? (uint32_t)kSubQuads : nvq_any;
@@ -172,29 +177,29 @@ __device__ __forceinline__ void subenc_write(uint32_t *slice, uint8_t *ctrl_dst,
             pt = carry;
         carry = __shfl_sync(0xffffffffu, last, 31);
         const uint32_t w0 = t0 | pt;
-        uint32_t *wp = slice + (pos >> 2);
-        if (nfull > 0)
-            wp[0] = w0;
-        if (nfull > 1)
-            wp[1] = t1;
-        if (nfull > 2)
-            wp[2] = t2;
-        if (nfull > 3)
-            wp[3] = t3;
-        if (lq + 1 == nvq && ((pos + C) & 3u)) {   // the sub-tile's last, partial word
-            fidx = (pos + C) >> 2;
-            fword = nfull ? last : w0;
-        }
+        // The words this lane completes; stores it need not make go to the
+        // slice's spare last word instead, so there is no branch.
+        const uint32_t wi = pos >> 2;
+        slice[nfull > 0 ? wi : kSpare] = w0;
+        slice[nfull > 1 ? wi + 1 : kSpare] = t1;
+        slice[nfull > 2 ? wi + 2 : kSpare] = t2;
+        slice[nfull > 3 ? wi + 3 : kSpare] = t3;
+        const bool fin = lq + 1 == nvq && ((pos + C) & 3u);   // the sub-tile's last, partial word
+        fidx = fin ? (pos + C) >> 2 : fidx;
+        fword = fin ? (nfull ? last : w0) : fword;
     }
-    if (fidx != kNone)
-        slice[fidx] = fword;
+    slice[fidx != kNone ? fidx : kSpare] = fword;
     __syncwarp();
     const uint8_t *sb = reinterpret_cast<const uint8_t *>(slice);
     uint8_t *adst = dst - h;
     const uint32_t end = h + run;
     const uint32_t c0 = (h + 15) >> 4, c1 = end >> 4;   // whole 16-byte chunks [c0, c1)
-    for (uint32_t c = c0 + lane; c < c1; c += 32)
-        stg_stream128(adst + 16 * c, *reinterpret_cast<const uint4 *>(sb + 16 * c));
+#pragma unroll
+    for (int k = 0; k < (kEncSliceWords * 4 / 16 + 31) / 32; k++) {
+        const uint32_t c = c0 + lane + 32 * k;
+        if (c < c1)
+            stg_stream128(adst + 16 * c, *reinterpret_cast<const uint4 *>(sb + 16 * c));
+    }
     if (lane < 16) {
         const uint32_t i = h + lane;
         if (i < min(16 * c0, end))
