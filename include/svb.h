@@ -134,12 +134,19 @@ void svb_set_spin_limit(uint64_t iterations);
  *                              finds its data offset by a decoupled look-back
  *                              over its predecessors, then decodes;
  *   SVB_DECODE_TWO_PASS (2)    an offsets pass over the control stream, then
- *                              a persistent decode with bulk-copy staging.
- * Both give identical results.  Returns SVB_EINVAL for an unknown variant. */
+ *                              a persistent decode with bulk-copy staging;
+ *                              for differential streams the offsets pass
+ *                              also sums each 512-integer sub-tile's gaps
+ *                              into its carry-in;
+ *   SVB_DECODE_SUMS_PASS (3)   as SVB_DECODE_TWO_PASS, but differential
+ *                              streams learn their carry-ins from a separate
+ *                              pass over the staged tiles (three launches).
+ * All give identical results.  Returns SVB_EINVAL for an unknown variant. */
 enum svb_decode_variant {
     SVB_DECODE_AUTO = 0,
     SVB_DECODE_SINGLE_PASS = 1,
-    SVB_DECODE_TWO_PASS = 2
+    SVB_DECODE_TWO_PASS = 2,
+    SVB_DECODE_SUMS_PASS = 3
 };
 int svb_set_decode_variant(int variant);
 

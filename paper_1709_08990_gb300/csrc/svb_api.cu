@@ -45,9 +45,11 @@ u64 spin_limit()
 int decode_dispatch(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, uint32_t prev,
                     bool delta, void *ws, svb::DeviceResult *r, cudaStream_t s)
 {
-    if (g_decode_variant.load(std::memory_order_relaxed) == SVB_DECODE_SINGLE_PASS)
+    const int v = g_decode_variant.load(std::memory_order_relaxed);
+    if (v == SVB_DECODE_SINGLE_PASS)
         return svb::launch_decode(in, in_len, n, out, prev, delta, ws, r, s, spin_limit());
-    return svb::launch_decode_tiled(in, in_len, n, out, prev, delta, ws, r, s, spin_limit());
+    return svb::launch_decode_tiled(in, in_len, n, out, prev, delta, ws, r, s, spin_limit(),
+                                    v == SVB_DECODE_SUMS_PASS);
 }
 
 int encode_dispatch(const uint32_t *in, u64 n, uint8_t *out, uint32_t prev, bool delta,
@@ -486,7 +488,7 @@ const char *svb_error_string(int status)
 
 int svb_set_decode_variant(int variant)
 {
-    if (variant < SVB_DECODE_AUTO || variant > SVB_DECODE_TWO_PASS)
+    if (variant < SVB_DECODE_AUTO || variant > SVB_DECODE_SUMS_PASS)
         return SVB_EINVAL;
     g_decode_variant.store(variant, std::memory_order_relaxed);
     return SVB_OK;

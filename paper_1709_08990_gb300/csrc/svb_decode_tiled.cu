@@ -69,6 +69,8 @@ struct OffsetsArgs {
     TileStatus *st;
     u64 spin_limit;
     uint32_t in_aligned;
+    uint32_t prev;       // delta_prep_kernel: the value before the first integer
+    uint32_t *carries;   // delta_prep_kernel: per sub-tile carry-in
 };
 
 // Data bytes covered by the control bytes of quads [q, q + 16) taken from
@@ -128,21 +130,21 @@ __device__ __forceinline__ uint32_t sum64(const OffsetsArgs &a, u64 q, uint32_t 
     return sum;
 }
 
-__global__ void __launch_bounds__(kThreads) offsets_kernel(OffsetsArgs a)
-{
-    __shared__ uint32_t s_w[2][kWarps];
-    __shared__ u64 s_cta, s_etag, s_base;
+// This CTA's range of groups [g0, g1): the offsets of its sub-tiles relative
+// to the range go to offs, warp 0 chains the range total with the ranges
+// before by one look-back, then the base is added.  The CTA holding the last
+// group also writes the stream size and the truncation verdict.  Ends with a
+// block barrier (the range's offsets are then visible to the whole CTA).
+struct RangeBytes {
+    u64 base;   // data offset where the range starts
+    u64 bytes;  // data bytes of the range
+};
 
+__device__ RangeBytes range_offsets(const OffsetsArgs &a, u64 cta, u64 etag, u64 g0, u64 g1,
+                                    uint32_t (*s_w)[kWarps], u64 *s_base)
+{
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) {
-        s_cta = atomicAdd(&a.hdr->a_counter, 1ull);
-        s_etag = (ld_relaxed(&a.hdr->epoch) + 1) << 2;
-    }
-    __syncthreads();
-    const u64 cta = s_cta, etag = s_etag;
     const uint32_t last_nints = (uint32_t)(a.n - 4 * (a.nquads - 1));
-    const u64 g0 = cta * a.per_cta;
-    const u64 g1 = min(g0 + a.per_cta, a.groups);
 
     // Each iteration: 64 quads per thread, two threads per sub-tile.
     u64 running = 0;  // this CTA's data bytes so far (every thread)
@@ -196,24 +198,435 @@ __global__ void __launch_bounds__(kThreads) offsets_kernel(OffsetsArgs a)
                 if (stream > a.in_len)
                     raise_error(a.hdr, kErrTruncated);
             }
-            s_base = base;
+            *s_base = base;
         }
     }
     __syncthreads();
-    const u64 base = s_base;
+    const u64 base = *s_base;
     if (base) {
         const u64 s0 = g0 * kOffGroupSubs, s1 = min(g1 * kOffGroupSubs, a.nsubs);
         for (u64 s = s0 + tid; s < s1; s += kThreads)
             a.offs[s] += base;
     }
     __syncthreads();
-    if (tid == 0) {
+    return RangeBytes{base, running};
+}
+
+// The last CTA of an offsets launch resets its claim and done counters.
+__device__ __forceinline__ void offsets_done(const OffsetsArgs &a)
+{
+    if (threadIdx.x == 0) {
         __threadfence();
         u64 done = atomicAdd(&a.hdr->a_done, 1ull);
         if (done == (u64)gridDim.x - 1) {
             st_relaxed(&a.hdr->a_counter, 0);
             st_relaxed(&a.hdr->a_done, 0);
         }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) offsets_kernel(OffsetsArgs a)
+{
+    __shared__ uint32_t s_w[2][kWarps];
+    __shared__ u64 s_cta, s_etag, s_base;
+
+    if (threadIdx.x == 0) {
+        s_cta = atomicAdd(&a.hdr->a_counter, 1ull);
+        s_etag = (ld_relaxed(&a.hdr->epoch) + 1) << 2;
+    }
+    __syncthreads();
+    const u64 cta = s_cta;
+    const u64 g0 = cta * a.per_cta;
+    const u64 g1 = min(g0 + a.per_cta, a.groups);
+    range_offsets(a, cta, s_etag, g0, g1, s_w, &s_base);
+    offsets_done(a);
+}
+
+// Sum of the 512 one-byte integers at staged positions [base, base + 512) of
+// D (a sub-tile whose control bytes are all zero: Sec. 4, an all-zero control
+// byte covers 4 bytes), a word at a time with the bytes outside masked; the
+// warp's total in every lane.
+__device__ __forceinline__ uint32_t zero_ctrl_sum(const uint8_t *D, uint32_t base)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t *Wd = reinterpret_cast<const uint32_t *>(D);
+    const uint32_t b0 = base >> 2, b1 = (base + 4 * kSubQuads + 3) >> 2;
+    const uint32_t head = base & 3u, tail = (base + 4 * kSubQuads) & 3u;
+    uint32_t t = 0;
+    for (uint32_t i = b0 + lane; i < b1; i += 32) {
+        uint32_t x = Wd[i];
+        if (i == b0)
+            x &= 0xffffffffu << (8 * head);
+        if (i == b1 - 1 && tail)
+            x &= 0xffffffffu >> (8 * (4 - tail));
+        const uint32_t y = (x & 0x00ff00ffu) + ((x >> 8) & 0x00ff00ffu);
+        t += (y & 0xffffu) + (y >> 16);
+    }
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1)
+        t += __shfl_xor_sync(0xffffffffu, t, d);
+    return t;
+}
+
+// Turns the gap sums carries[s0 .. s1) of the sub-tiles of range `cta` into
+// carry-ins, computed by one whole warp: each lane takes a contiguous run of
+// the sums (its loads all in flight at once), the lane totals are scanned,
+// the range total is chained with the ranges before by one look-back (prev
+// starts the first range), and each lane writes its run's carries.
+__device__ void range_carries(uint32_t *carries, u64 s0, u64 s1, u64 cta, uint32_t prev,
+                              TileStatus *st, u64 etag, u64 spin_limit, WsHeader *hdr)
+{
+    const int lane = threadIdx.x & 31;
+    const u64 per = (s1 - s0 + 31) / 32;
+    const u64 b = min(s0 + lane * per, s1), e = min(b + per, s1);
+    uint32_t tot = 0;
+#pragma unroll 4
+    for (u64 i = b; i < e; i++)
+        tot += carries[i];
+    const uint32_t inc = warp_incl_scan(tot);
+    const uint32_t run = __shfl_sync(0xffffffffu, inc, 31);
+    TileStatus *me = &st[cta];
+    u64 base = prev;
+    bool ok = true;
+    if (cta == 0) {
+        if (lane == 0)
+            publish(&me->val_tag, &me->val_pre, (uint32_t)(prev + run), kFlagPrefix, etag);
+    } else {
+        if (lane == 0)
+            publish(&me->val_tag, &me->val_agg, run, kFlagAgg, etag);
+        base = lookback<true>(st, cta, etag, spin_limit, hdr, ok);
+        if (ok && lane == 0)
+            publish(&me->val_tag, &me->val_pre, (uint32_t)(base + run), kFlagPrefix, etag);
+    }
+    if (!ok && lane == 0)
+        raise_error(hdr, kErrTimeout);
+    uint32_t c = (uint32_t)base + inc - tot;
+    for (u64 i = b; i < e; i++) {
+        const uint32_t v = carries[i];
+        carries[i] = c;
+        c += v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pass 1 for differential streams: sub-tile offsets and carry-ins in one
+// launch.  Each CTA takes a contiguous range of groups in claim order, finds
+// its sub-tiles' data offsets as offsets_kernel does, then sums each
+// sub-tile's gaps and turns the sums into carry-ins within the range; the
+// last CTA to finish scans the range totals (prev first) into each range's
+// carry-in, which the decode pass adds (Sec. 2's prefix sum continued across
+// sub-tiles and ranges).
+//
+// Gap sums: warp w takes 32 consecutive sub-tiles of the range at a time, one
+// per lane.  A full sub-tile whose data is 512 bytes has only zero control
+// bytes (Sec. 4: a control byte covers 4 + the sum of its codes bytes), so
+// it holds 512 one-byte gaps, the common case of sorted lists with small
+// gaps.  For each such sub-tile the warp loads the 16-byte-aligned run that
+// holds its bytes, one chunk per lane, coalesced, and each lane byte-sums its
+// chunk with dp4a; a reduce-scatter over the warp (31 shuffles for 32
+// sub-tiles) leaves sub-tile l's run total in lane l, and lane l corrects it
+// for the run's ragged ends.  Every other sub-tile is taken by the whole
+// warp: staged into one of the warp's two shared slots with cp.async (the
+// next one's copies in flight) and decoded with the decode pass's sub-tile
+// code.  The loads keep the stream in L2 (evict-last) for the decode pass,
+// which reads it again.  Reads stay inside the stream as far as the CTA's
+// own data ends and inside [in, in + in_len): on a stream cut short the sums
+// are meaningless, the truncation verdict is set and the decode pass does
+// nothing.
+
+constexpr int kPrepCtrl = 144;                        // 15-byte phase + 128 control bytes
+constexpr int kPrepData = 16 * kSubQuads + 48;        // phase + 2048 + round-up + read slack
+constexpr int kPrepSlot = kPrepCtrl + kPrepData;      // one staged sub-tile
+constexpr int kPrepUnroll = 8;                        // sub-tile runs a warp loads together
+
+static_assert(kPrepUnroll == 8, "the reduce-scatter spans lane bits 4, 3, 2");
+
+static_assert(kPrepCtrl % 16 == 0 && kPrepSlot % 16 == 0, "cp.async needs 16-byte slots");
+
+// Copies the bytes of global [g, g + len) that lie inside [lo, hi) so that
+// byte g + i lands at dst + (g mod 16) + i (dst 16-byte aligned): whole
+// 16-byte chunks by cp.async, a chunk that straddles lo or hi byte by byte
+// (none of its bytes outside [lo, hi) is read).  One whole warp; the caller
+// commits and waits.
+__device__ __forceinline__ void warp_stage(const uint8_t *g, uint32_t len, uint8_t *dst,
+                                           uintptr_t lo, uintptr_t hi, uint64_t policy)
+{
+    const int lane = threadIdx.x & 31;
+    const uintptr_t a0 = (uintptr_t)g & ~(uintptr_t)15;
+    const uint32_t nch = (uint32_t)((((uintptr_t)g + len + 15) & ~(uintptr_t)15) - a0) >> 4;
+    for (uint32_t c = lane; c < nch; c += 32) {
+        const uintptr_t src = a0 + 16 * (uintptr_t)c;
+        if (src >= lo && src + 16 <= hi) {
+            cp_async16(dst + 16 * c, reinterpret_cast<const void *>(src), policy);
+        } else {
+            for (int i = 0; i < 16; i++)
+                if (src + i >= lo && src + i < hi)
+                    dst[16 * c + i] = __ldg(reinterpret_cast<const uint8_t *>(src + i));
+        }
+    }
+}
+
+// 16-byte read-only load whose line L2 keeps with the given policy.
+__device__ __forceinline__ uint4 ld_keep128(const void *p, uint64_t policy)
+{
+    uint4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p), "l"(policy));
+    return v;
+}
+
+// Mask of the low `kept` bytes of a word (kept clamped to [0, 4]).
+__device__ __forceinline__ uint32_t low_bytes_mask(int kept)
+{
+    return kept <= 0 ? 0u : (kept >= 4 ? ~0u : ~0u >> (8 * (4 - kept)));
+}
+
+// Sum of the bytes of x that the byte mask m keeps, added to acc.
+__device__ __forceinline__ uint32_t bytesum4(uint4 x, uint4 m, uint32_t acc)
+{
+    acc = __dp4a(x.x & m.x, 0x01010101u, acc);
+    acc = __dp4a(x.y & m.y, 0x01010101u, acc);
+    acc = __dp4a(x.z & m.z, 0x01010101u, acc);
+    return __dp4a(x.w & m.w, 0x01010101u, acc);
+}
+
+__device__ __forceinline__ uint32_t bytesum4(uint4 x, uint32_t acc)
+{
+    acc = __dp4a(x.x, 0x01010101u, acc);
+    acc = __dp4a(x.y, 0x01010101u, acc);
+    acc = __dp4a(x.z, 0x01010101u, acc);
+    return __dp4a(x.w, 0x01010101u, acc);
+}
+
+// Gap sums carries[s0 .. s1) of one range into carry-ins relative to the
+// range (exclusive prefix); returns the range total.  One whole warp: each
+// lane takes a contiguous run of the sums, the lane totals are scanned.
+__device__ uint32_t range_local_carries(uint32_t *carries, u64 s0, u64 s1)
+{
+    const int lane = threadIdx.x & 31;
+    const u64 per = (s1 - s0 + 31) / 32;
+    const u64 b = min(s0 + lane * per, s1), e = min(b + per, s1);
+    uint32_t tot = 0;
+#pragma unroll 4
+    for (u64 i = b; i < e; i++)
+        tot += carries[i];
+    const uint32_t inc = warp_incl_scan(tot);
+    uint32_t c = inc - tot;
+    for (u64 i = b; i < e; i++) {
+        const uint32_t v = carries[i];
+        carries[i] = c;
+        c += v;
+    }
+    return __shfl_sync(0xffffffffu, inc, 31);
+}
+
+__global__ void __launch_bounds__(kThreads) delta_prep_kernel(OffsetsArgs a)
+{
+    __shared__ uint32_t s_w[2][kWarps];
+    __shared__ u64 s_cta, s_etag, s_base;
+    __shared__ uint32_t s_last;
+    __shared__ uint4 s_lowm[16];  // s_lowm[p] keeps the bytes below p of a 16-byte chunk
+    __shared__ __align__(16) uint8_t s_slot[kWarps][2][kPrepSlot];
+    __shared__ __align__(16) uint16_t s_pos[kWarps][kSubQuads];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        s_cta = atomicAdd(&a.hdr->a_counter, 1ull);
+        s_etag = (ld_relaxed(&a.hdr->epoch) + 1) << 2;
+    }
+    if (tid < 16)
+        s_lowm[tid] = make_uint4(low_bytes_mask(tid), low_bytes_mask(tid - 4),
+                                 low_bytes_mask(tid - 8), low_bytes_mask(tid - 12));
+    __syncthreads();
+    const u64 cta = s_cta, etag = s_etag;
+    const u64 g0 = cta * a.per_cta;
+    const u64 g1 = min(g0 + a.per_cta, a.groups);
+    const RangeBytes r = range_offsets(a, cta, etag, g0, g1, s_w, &s_base);
+
+    const u64 s0 = g0 * kOffGroupSubs, s1 = min(g1 * kOffGroupSubs, a.nsubs);
+    const u64 range_end = r.base + r.bytes;
+    const uint32_t last_nints = (uint32_t)(a.n - 4 * (a.nquads - 1));
+    const uint8_t *data = a.in + a.nquads;
+    const uint8_t *rdata = data + r.base;  // the range's first data byte
+    // Bytes this CTA may read: its control and data bytes lie below the end
+    // of its data, and nothing at or past in + in_len is read (in_len may
+    // be the "unbounded" ~0 of the unchecked calls: saturate).
+    const uintptr_t lo = (uintptr_t)a.in;
+    const uintptr_t in_end = a.in_len > ~(uintptr_t)0 - lo ? ~(uintptr_t)0 : lo + a.in_len;
+    const uintptr_t hi = min(in_end, (uintptr_t)(data + range_end));
+    const uint64_t policy = l2_policy_evict_last();
+    uint16_t *pos = s_pos[warp];
+
+    // Warp-wide: stage sub-tile j (data bytes [d0, d1)) into slot b.
+    auto stage = [&](u64 j, u64 d0, u64 d1, uint8_t *b) {
+        const u64 q0 = j * kSubQuads;
+        const uint32_t nq = (uint32_t)min((u64)kSubQuads, a.nquads - q0);
+        warp_stage(a.in + q0, nq, b, lo, hi, policy);
+        warp_stage(data + d0, (uint32_t)(d1 - d0), b + kPrepCtrl, lo, hi, policy);
+    };
+    // Warp-wide: the decoded gaps of staged sub-tile j summed (every lane).
+    auto staged_sum = [&](u64 j, u64 d0, const uint8_t *b) -> uint32_t {
+        const u64 q0 = j * kSubQuads;
+        SubTile t;
+        t.C = b + ((uintptr_t)(a.in + q0) & 15u);
+        t.D = b + kPrepCtrl;
+        t.base = (uint32_t)((uintptr_t)(data + d0) & 15u);
+        t.nq = (uint32_t)min((u64)kSubQuads, a.nquads - q0);
+        t.tail = q0 + t.nq == a.nquads ? last_nints : 4u;
+        const uint32_t w = subtile_ctrl_word(t);
+        subtile_positions(t, w, pos);
+        __syncwarp();
+        uint32_t v[kSubRounds][4];
+        subtile_gather(t, pos, v);
+        uint32_t sum = 0;
+#pragma unroll
+        for (int rr = 0; rr < kSubRounds; rr++)
+            sum += v[rr][0] + v[rr][1] + v[rr][2] + v[rr][3];
+#pragma unroll
+        for (int d = 16; d >= 1; d >>= 1)
+            sum += __shfl_xor_sync(0xffffffffu, sum, d);
+        __syncwarp();  // the slot and pos are read before they are refilled
+        return sum;
+    };
+
+    for (u64 rb = s0 + (u64)warp * 32; rb < s1; rb += (u64)kWarps * 32) {
+        const u64 j = rb + lane;
+        const bool valid = j < s1;
+        uint32_t e0 = 0, e1 = 0;  // the sub-tile's data bytes, from the range's first
+        if (valid) {
+            e0 = (uint32_t)(a.offs[j] - r.base);
+            e1 = (uint32_t)((j + 1 < s1 ? a.offs[j + 1] : range_end) - r.base);
+        }
+        const u64 q0 = j * kSubQuads;
+        const bool full = valid && (q0 + kSubQuads < a.nquads ||
+                                    (q0 + kSubQuads == a.nquads && last_nints == 4));
+        const uintptr_t g = (uintptr_t)(rdata + e0);
+        const uintptr_t a0 = g & ~(uintptr_t)15;
+        // The run's chunk 32 (its first g mod 16 bytes end the sub-tile's
+        // 512) must lie inside the readable bytes too.
+        const bool fast = full && e1 - e0 == 4u * kSubQuads && a0 >= lo && a0 + 16 * 33 <= hi;
+        const unsigned F = __ballot_sync(0xffffffffu, fast);
+        // Batches of 8 runs: each lane byte-sums its chunk of each run, a
+        // reduce-scatter over lane bits 4, 3, 2 and a butterfly over bits
+        // 1, 0 leave run u0 + k's total in lanes 4k .. 4k + 3, and lane
+        // u0 + k takes it from lane 4k.
+        uint32_t sum = 0;  // chunks 0..31 of this lane's run
+#pragma unroll
+        for (int u0 = 0; u0 < 32; u0 += kPrepUnroll) {
+            uint4 v[kPrepUnroll];
+#pragma unroll
+            for (int i = 0; i < kPrepUnroll; i++) {
+                const int u = u0 + i;
+                const uint32_t eu = __shfl_sync(0xffffffffu, e0, u);
+                v[i] = make_uint4(0u, 0u, 0u, 0u);
+                if ((F >> u) & 1u) {
+                    const uint4 *run = reinterpret_cast<const uint4 *>(
+                        (uintptr_t)(rdata + eu) & ~(uintptr_t)15);
+                    v[i] = ld_keep128(run + lane, policy);
+                }
+            }
+            uint32_t q[kPrepUnroll];
+#pragma unroll
+            for (int i = 0; i < kPrepUnroll; i++)
+                q[i] = bytesum4(v[i], 0u);
+#pragma unroll
+            for (int h = kPrepUnroll / 2, bit = 16; h >= 1; h >>= 1, bit >>= 1) {
+                const bool upper = (lane & bit) != 0;
+#pragma unroll
+                for (int i = 0; i < h; i++) {
+                    const uint32_t send = upper ? q[i] : q[i + h];
+                    const uint32_t keep = upper ? q[i + h] : q[i];
+                    q[i] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
+                }
+            }
+            q[0] += __shfl_xor_sync(0xffffffffu, q[0], 2);
+            q[0] += __shfl_xor_sync(0xffffffffu, q[0], 1);
+            const uint32_t t = __shfl_sync(0xffffffffu, q[0], ((lane - u0) & 7) << 2);
+            if ((lane & ~7) == u0)
+                sum = t;
+        }
+        if (fast) {
+            // Bytes [g, g + 512): less the first ph bytes of chunk 0, plus
+            // the first ph bytes of chunk 32.
+            const uint32_t ph = (uint32_t)(g & 15u);
+            if (ph) {
+                const uint4 m = s_lowm[ph];
+                const uint4 *run = reinterpret_cast<const uint4 *>(a0);
+                const uint4 c0 = ld_keep128(run, policy), c32 = ld_keep128(run + 32, policy);
+                sum += bytesum4(c32, m, 0u) - bytesum4(c0, m, 0u);
+            }
+        }
+        // The rest, a whole warp per sub-tile, the next one's copies in
+        // flight while the current one is summed.
+        unsigned slow = __ballot_sync(0xffffffffu, valid && !fast);
+        if (slow) {
+            const u64 d0 = r.base + e0, d1 = r.base + e1;
+            int l = __ffs(slow) - 1;
+            uint32_t k = 0;
+            stage(__shfl_sync(0xffffffffu, j, l), __shfl_sync(0xffffffffu, d0, l),
+                  __shfl_sync(0xffffffffu, d1, l), s_slot[warp][0]);
+            cp_async_commit();
+            while (slow) {
+                slow &= slow - 1;
+                const int nl = slow ? __ffs(slow) - 1 : -1;
+                if (nl >= 0)
+                    stage(__shfl_sync(0xffffffffu, j, nl), __shfl_sync(0xffffffffu, d0, nl),
+                          __shfl_sync(0xffffffffu, d1, nl), s_slot[warp][(k + 1) & 1]);
+                cp_async_commit();
+                cp_async_wait<1>();
+                __syncwarp();
+                const uint32_t t = staged_sum(__shfl_sync(0xffffffffu, j, l),
+                                              __shfl_sync(0xffffffffu, d0, l),
+                                              s_slot[warp][k & 1]);
+                if (lane == l)
+                    sum = t;
+                l = nl;
+                k++;
+            }
+            cp_async_wait<0>();
+        }
+        if (valid)
+            a.carries[j] = sum;
+    }
+    __syncthreads();  // every gap sum of the range is written
+    if (warp == 0 && s0 < s1) {
+        const uint32_t total = range_local_carries(a.carries, s0, s1);
+        if (lane == 0)
+            a.st[cta].val_agg = total;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        s_last = atomicAdd(&a.hdr->a_done, 1ull) == (u64)gridDim.x - 1 ? 1u : 0u;
+    }
+    __syncthreads();
+    if (!s_last)
+        return;
+    // The last CTA: carry-in of every range = prev + the totals before it.
+    // Thread t scans a contiguous run of the ranges.
+    __threadfence();
+    const u64 nr = gridDim.x;
+    const u64 per = (nr + kThreads - 1) / kThreads;
+    const u64 b = min((u64)tid * per, nr), e = min(b + per, nr);
+    uint32_t tot = 0;
+    for (u64 i = b; i < e; i++)
+        tot += (uint32_t)ld_relaxed(&a.st[i].val_agg);
+    const uint32_t inc = warp_incl_scan(tot);
+    if (lane == 31)
+        s_w[0][warp] = inc;
+    __syncthreads();
+    uint32_t c = a.prev + inc - tot;
+    for (int w = 0; w < warp; w++)
+        c += s_w[0][w];
+    for (u64 i = b; i < e; i++) {
+        const uint32_t v = (uint32_t)ld_relaxed(&a.st[i].val_agg);
+        a.st[i].val_pre = c;
+        c += v;
+    }
+    if (tid == 0) {
+        st_relaxed(&a.hdr->a_counter, 0);
+        st_relaxed(&a.hdr->a_done, 0);
     }
 }
 
@@ -237,6 +650,9 @@ struct TiledArgs {
     DeviceResult *result;
     u64 spin_limit;
     u64 per_cta;        // kSums: tiles per CTA (contiguous ranges)
+    u64 range_subs;     // kDelta: carries are relative to ranges of this many
+                        // sub-tiles, whose carry-ins are st[range].val_pre
+                        // (0: the carries are absolute)
     u64 tile0, tile1;   // decoding: the tiles [tile0, tile1) to decode
     uint32_t prev;
     uint32_t out_aligned;
@@ -277,8 +693,11 @@ __device__ void produce(const TiledArgs &a, Pipe &P, u64 first, int lane)
         if (t < a.ntiles && lane <= kSubs) {
             const u64 sb = min(t * kSubs + lane, a.nsubs);
             off = a.offs[sb];
-            if (kMode == kDelta && lane < kSubs && sb < a.nsubs)
+            if (kMode == kDelta && lane < kSubs && sb < a.nsubs) {
                 car = a.carries[sb];
+                if (a.range_subs)
+                    car += (uint32_t)a.st[sb / a.range_subs].val_pre;
+            }
         }
     };
     const uint8_t *stream_end = a.in + a.nquads + a.offs[a.nsubs];
@@ -396,29 +815,13 @@ __device__ void consume(const TiledArgs &a, Pipe &P, uint16_t *s_pos)
         const uint32_t carry_in = kMode == kDelta ? P.carry[s][warp] : 0u;
         const uint32_t w = subtile_ctrl_word(t);
         if (kMode == kSums && full && __all_sync(0xffffffffu, w == 0)) {
-            // All 512 integers take one byte (Sec. 4: an all-zero control byte
-            // covers 4 bytes): the gaps are the data bytes [base, base + 512).
-            // Sum them a word at a time, masking the bytes outside the range.
-            const uint32_t *Wd = reinterpret_cast<const uint32_t *>(D);
-            const uint32_t b0 = base >> 2, b1 = (base + 4 * kSubQuads + 3) >> 2;
-            const uint32_t head = base & 3u, tail = (base + 4 * kSubQuads) & 3u;
-            uint32_t t = 0;
-            for (uint32_t i = b0 + lane; i < b1; i += 32) {
-                uint32_t x = Wd[i];
-                if (i == b0)
-                    x &= 0xffffffffu << (8 * head);
-                if (i == b1 - 1 && tail)
-                    x &= 0xffffffffu >> (8 * (4 - tail));
-                const uint32_t y = (x & 0x00ff00ffu) + ((x >> 8) & 0x00ff00ffu);
-                t += (y & 0xffffu) + (y >> 16);
-            }
+            // All 512 integers take one byte: the gaps are the data bytes
+            // [base, base + 512).
+            const uint32_t t = zero_ctrl_sum(D, base);
             fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0)
                 mbar_arrive(&P.empty[s]);
-#pragma unroll
-            for (int d = 16; d >= 1; d >>= 1)
-                t += __shfl_xor_sync(0xffffffffu, t, d);
             if (lane == 0)
                 a.carries[sb] = t;
             continue;
@@ -485,45 +888,12 @@ __device__ void consume(const TiledArgs &a, Pipe &P, uint16_t *s_pos)
 }
 
 // kSums epilogue, warp 0: turn this CTA's sub-tile gap sums into carries.
-// Each lane takes a contiguous run of the range's sums (its loads all in
-// flight at once), the lane totals are scanned, the range total is chained
-// with the ranges before by one look-back (prev starts the first range), and
-// each lane writes its run's carries.
 __device__ void sums_to_carries(const TiledArgs &a, u64 first, u64 etag)
 {
-    const int lane = threadIdx.x & 31;
     const u64 s0 = first * kSubs;
     const u64 s1 = min(min(first + a.per_cta, a.ntiles) * kSubs, a.nsubs);
-    const u64 per = (s1 - s0 + 31) / 32;
-    const u64 b = min(s0 + lane * per, s1), e = min(b + per, s1);
-    uint32_t tot = 0;
-#pragma unroll 4
-    for (u64 i = b; i < e; i++)
-        tot += a.carries[i];
-    const uint32_t inc = warp_incl_scan(tot);
-    const uint32_t run = __shfl_sync(0xffffffffu, inc, 31);
     const u64 cta = first / (a.per_cta ? a.per_cta : 1);
-    TileStatus *me = &a.st[cta];
-    u64 base = a.prev;
-    bool ok = true;
-    if (cta == 0) {
-        if (lane == 0)
-            publish(&me->val_tag, &me->val_pre, (uint32_t)(a.prev + run), kFlagPrefix, etag);
-    } else {
-        if (lane == 0)
-            publish(&me->val_tag, &me->val_agg, run, kFlagAgg, etag);
-        base = lookback<true>(a.st, cta, etag, a.spin_limit, a.hdr, ok);
-        if (ok && lane == 0)
-            publish(&me->val_tag, &me->val_pre, (uint32_t)(base + run), kFlagPrefix, etag);
-    }
-    if (!ok && lane == 0)
-        raise_error(a.hdr, kErrTimeout);
-    uint32_t c = (uint32_t)base + inc - tot;
-    for (u64 i = b; i < e; i++) {
-        const uint32_t v = a.carries[i];
-        a.carries[i] = c;
-        c += v;
-    }
+    range_carries(a.carries, s0, s1, cta, a.prev, a.st, etag, a.spin_limit, a.hdr);
 }
 
 template <int kMode>
@@ -620,10 +990,21 @@ static int offsets_grid()
     return g;
 }
 
-// Offsets pass alone: sub-tile offsets, stream size and the truncation
-// verdict into the workspace (the first half of launch_decode_tiled).
-int launch_offsets(const uint8_t *in, u64 in_len, u64 n, void *ws, cudaStream_t stream,
-                   u64 spin_limit)
+static int prep_grid()
+{
+    static int g = 0;
+    if (!g) {
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, delta_prep_kernel, kThreads, 0);
+        g = sm_count() * (occ > 0 ? occ : 1);
+    }
+    return g;
+}
+
+// Arguments of a range-per-CTA pass over the control stream with at most
+// max_grid CTAs; *grid receives the launch's CTA count (each has groups).
+static OffsetsArgs offsets_args(const uint8_t *in, u64 in_len, u64 n, void *ws, u64 spin_limit,
+                                u64 max_grid, u64 *grid)
 {
     const WsLayout L = ws_layout(n);
     const u64 nquads = (n + 3) / 4;
@@ -634,18 +1015,44 @@ int launch_offsets(const uint8_t *in, u64 in_len, u64 n, void *ws, cudaStream_t 
     o.nquads = nquads;
     o.nsubs = (nquads + kSubQuads - 1) / kSubQuads;
     o.groups = (nquads + kOffGroupQuads - 1) / kOffGroupQuads;
-    u64 ogrid = min((u64)offsets_grid(), o.groups);
+    u64 ogrid = min(max_grid, o.groups);
     o.per_cta = (o.groups + ogrid - 1) / ogrid;
-    ogrid = (o.groups + o.per_cta - 1) / o.per_cta;  // no CTA without groups
+    *grid = (o.groups + o.per_cta - 1) / o.per_cta;  // no CTA without groups
     o.offs = reinterpret_cast<u64 *>(static_cast<char *>(ws) + L.offs);
     o.hdr = reinterpret_cast<WsHeader *>(ws);
     o.st = reinterpret_cast<TileStatus *>(static_cast<char *>(ws) + L.status);
     o.spin_limit = spin_limit;
     o.in_aligned = (((uintptr_t)in) & 15u) == 0;
+    o.prev = 0;
+    o.carries = reinterpret_cast<uint32_t *>(static_cast<char *>(ws) + L.carries);
+    return o;
+}
+
+// Offsets pass alone: sub-tile offsets, stream size and the truncation
+// verdict into the workspace (the first half of launch_decode_tiled).
+int launch_offsets(const uint8_t *in, u64 in_len, u64 n, void *ws, cudaStream_t stream,
+                   u64 spin_limit)
+{
+    u64 grid = 0;
+    const OffsetsArgs o = offsets_args(in, in_len, n, ws, spin_limit, offsets_grid(), &grid);
     prof_begin("offsets_kernel", stream);
-    offsets_kernel<<<(unsigned)ogrid, kThreads, 0, stream>>>(o);
+    offsets_kernel<<<(unsigned)grid, kThreads, 0, stream>>>(o);
     prof_end(stream);
     return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+// Offsets and carry-ins of a differential stream in one launch; returns the
+// sub-tiles per range (the carries are relative to ranges), 0 on failure.
+static u64 launch_delta_prep(const uint8_t *in, u64 in_len, u64 n, uint32_t prev, void *ws,
+                             cudaStream_t stream, u64 spin_limit)
+{
+    u64 grid = 0;
+    OffsetsArgs o = offsets_args(in, in_len, n, ws, spin_limit, prep_grid(), &grid);
+    o.prev = prev;
+    prof_begin("delta_prep_kernel", stream);
+    delta_prep_kernel<<<(unsigned)grid, kThreads, 0, stream>>>(o);
+    prof_end(stream);
+    return cudaGetLastError() == cudaSuccess ? o.per_cta * kOffGroupSubs : 0;
 }
 
 static TiledArgs tiled_args(const uint8_t *in, u64 n, uint32_t *out, uint32_t prev, void *ws,
@@ -667,6 +1074,7 @@ static TiledArgs tiled_args(const uint8_t *in, u64 n, uint32_t *out, uint32_t pr
     t.result = result;
     t.spin_limit = spin_limit;
     t.per_cta = 0;
+    t.range_subs = 0;
     t.tile0 = 0;
     t.tile1 = t.ntiles;
     t.prev = prev;
@@ -697,12 +1105,23 @@ int launch_decode_range(const uint8_t *in, u64 n, uint32_t *out, void *ws, Devic
 
 int launch_decode_tiled(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, uint32_t prev,
                         bool delta, void *ws, DeviceResult *result, cudaStream_t stream,
-                        u64 spin_limit)
+                        u64 spin_limit, bool sums_pass)
 {
-    if (launch_offsets(in, in_len, n, ws, stream, spin_limit) != 0)
-        return 3;
     TiledArgs t = tiled_args(in, n, out, prev, ws, result, spin_limit);
     const u64 ntiles = t.ntiles;
+    if (delta && !sums_pass) {
+        // Offsets and carries in one pass, then the decode with carries.
+        t.range_subs = launch_delta_prep(in, in_len, n, prev, ws, stream, spin_limit);
+        if (!t.range_subs)
+            return 3;
+        u64 grid = min((u64)tiled_grid<kDelta>(), ntiles);
+        prof_begin("decode_tiled_kernel<delta>", stream);
+        decode_tiled_kernel<kDelta><<<(unsigned)grid, kDecBlock, sizeof(Pipe), stream>>>(t);
+        prof_end(stream);
+        return cudaGetLastError() == cudaSuccess ? 0 : 3;
+    }
+    if (launch_offsets(in, in_len, n, ws, stream, spin_limit) != 0)
+        return 3;
     if (delta) {
         // Sums pass over contiguous ranges, then the decode with carries.
         u64 sgrid = min((u64)tiled_grid<kSums>(), ntiles);

@@ -19,10 +19,11 @@ int launch_decode(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, uint32_t 
 u64 decode_tiles(u64 n);
 
 // Reduce-then-decode: control-stream offsets pass, then a persistent decode
-// with bulk-copy staging.
+// with bulk-copy staging.  Differential streams get their carry-ins in the
+// offsets pass, or, with sums_pass, from a separate pass over staged tiles.
 int launch_decode_tiled(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, uint32_t prev,
                         bool delta, void *ws, DeviceResult *result, cudaStream_t stream,
-                        u64 spin_limit);
+                        u64 spin_limit, bool sums_pass = false);
 
 // Its two halves, for decoding in pieces: the offsets pass (sub-tile offsets,
 // stream size and truncation verdict into the workspace), then plain decodes

@@ -110,12 +110,24 @@ def main(argv=None) -> None:
                     help="total integers the list lengths are scaled to (list workload); "
                          "--lists 12500 --cap 134217728 is lists_100k at 1/8 scale")
     ap.add_argument("--reps", type=int, default=10)
+    ap.add_argument("--variant", type=int, default=0,
+                    help="decoder variant (svb_set_decode_variant), 0 = the default")
+    ap.add_argument("--kernels", action="store_true",
+                    help="also time each library kernel (CUDA events around every launch)")
     a = ap.parse_args(argv)
+    if svb.svb_set_decode_variant(a.variant) != 0:
+        raise SystemExit(f"unknown decoder variant {a.variant}")
+    if a.kernels:
+        svb.svb_profile_begin()
     if a.op.startswith("batch"):
         r = _lists(a.op, a.workload or "lists_100k", a.lists, a.reps, a.cap)
     else:
         name = a.workload or "skewed_1g"
         r = _array(a.op, name, a.n or W.WORKLOADS[name].n, a.reps)
+    if a.kernels:
+        torch.cuda.synchronize()
+        r["kernels_ms"] = {k: t / c for k, (c, t) in svb.profile_end().items()}
+    r["variant"] = a.variant
     print(json.dumps(r), flush=True)
     if not r["verified"]:
         raise SystemExit("result differs from the generated values")

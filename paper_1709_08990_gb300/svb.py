@@ -166,7 +166,7 @@ def svb_set_spin_limit(iterations: int) -> None:
     lib().svb_set_spin_limit(iterations)
 
 
-SVB_DECODE_AUTO, SVB_DECODE_SINGLE_PASS, SVB_DECODE_TWO_PASS = 0, 1, 2
+SVB_DECODE_AUTO, SVB_DECODE_SINGLE_PASS, SVB_DECODE_TWO_PASS, SVB_DECODE_SUMS_PASS = 0, 1, 2, 3
 
 
 def svb_set_decode_variant(variant: int) -> int:

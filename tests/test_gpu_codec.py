@@ -18,16 +18,23 @@ pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 
 
-@pytest.fixture(params=[1, 2], ids=["single_pass", "two_pass"])
+@pytest.fixture(params=[1, 2, 3], ids=["single_pass", "two_pass", "sums_pass"])
 def variant(request):
-    """Run a test under each decoder variant and, alongside, each encoder
+    """Run a test under each decoder variant and, alongside, an encoder
     variant (tile look-back with the single-pass decoder, chunked with the
-    two-pass decoder)."""
+    others).  The sums-pass variant differs from the two-pass one only for
+    differential streams."""
     assert svb.svb_set_decode_variant(request.param) == 0
-    assert svb.svb_set_encode_variant(request.param) == 0
+    assert svb.svb_set_encode_variant(min(request.param, 2)) == 0
     yield request.param
     svb.svb_set_decode_variant(0)
     svb.svb_set_encode_variant(0)
+
+
+def plain_only_repeat(delta: bool, variant: int) -> None:
+    """The sums-pass variant decodes plain streams exactly as the two-pass one."""
+    if variant == 3 and not delta:
+        pytest.skip("plain streams: same kernels as the two-pass variant")
 
 
 def to_dev(a: np.ndarray):
@@ -62,6 +69,7 @@ def values(kind: str, n: int, seed: int = 0) -> np.ndarray:
 @pytest.mark.parametrize("kind", ["uniform", "skewed", "sorted"])
 @pytest.mark.parametrize("delta", [False, True])
 def test_encode_decode_parity(n, kind, delta, variant):
+    plain_only_repeat(delta, variant)
     x = values(kind, n)
     prev = 0 if kind == "sorted" else 0x9E3779B9
     want = oracle.encode(x, prev=prev, delta=delta)
@@ -145,6 +153,17 @@ def test_truncated_stream_is_reported(variant):
     # and a complete stream still decodes afterwards
     assert svb.svb_decode_checked(d, s.size, n, out, 0, 0) == s.size
     assert np.array_equal(host_u32(out), x)
+    # differential streams: the carry pass reads only bytes inside in_len
+    xs = values("sorted", 3 * n + 5, 9)
+    ds = oracle.encode(xs, delta=True, prev=11)
+    dd = to_dev(ds)
+    out3 = torch.zeros(xs.size, dtype=torch.int32, device=DEV)
+    for cut in (ds.size - 1, ds.size - 600, (xs.size + 3) // 4 + 1):
+        with pytest.raises(svb.SvbError) as e:
+            svb.svb_decode_checked(dd, cut, xs.size, out3, 11, 1)
+        assert e.value.status == svb.SVB_ETRUNCATED
+    assert svb.svb_decode_checked(dd, ds.size, xs.size, out3, 11, 1) == ds.size
+    assert np.array_equal(host_u32(out3), xs)
 
 
 def test_null_pointers_rejected():
@@ -239,6 +258,7 @@ def test_full_size_workloads(name, variant):
 
 def test_full_size_skewed_1g(variant):
     """n = 2^30, the roofline workload: 2 GiB stream, offsets past 2^31."""
+    plain_only_repeat(False, variant)
     x = W.array_values("skewed_1g")
     want = oracle.encode(x)
     assert want.size > (1 << 31)
@@ -257,6 +277,7 @@ def test_repeated_runs_are_identical(delta, variant):
     against the oracle: a race between the readers of a shared-memory stage
     and the bulk copy that refills it shows up as a rare, run-dependent
     mismatch, so one run is not enough to rule it out."""
+    plain_only_repeat(delta, variant)
     x = W.skewed_lengths(77, 1 << 27)
     if delta:
         x = np.cumsum(x.astype(np.uint64)).astype(np.uint32)
