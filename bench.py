@@ -472,8 +472,19 @@ def time_codec(svb, W, name, dev, peaks):
     ok = torch.equal(d_o, d_x)
     alg = 4 * n + size
     hb = peaks["hbm_gbs"]
+    extra = {}
+    if w.delta:
+        # The three-launch form (offsets pass, sums pass over staged tiles,
+        # decode) beside the default one-pass offsets and carries.
+        svb.svb_set_decode_variant(svb.SVB_DECODE_SUMS_PASS)
+        ms_3 = _time(lambda: svb.svb_decode_async(d_s, size, n, d_o, 0, 1, res, ws, ws_bytes,
+                                                  stream), steps, stream)
+        svb.svb_set_decode_variant(svb.SVB_DECODE_AUTO)
+        ok = ok and torch.equal(d_o, d_x)
+        extra["decode_sums_pass"] = {"gints_per_s": n / ms_3 / 1e6, "us": ms_3 * 1e3,
+                                     "frac": alg / (ms_3 / 1e3) / 1e9 / hb}
     s_svb, s_vb = svb.size_report(d_x, delta=w.delta)
-    return {"n": n, "delta": w.delta, "stream_bytes": size, "verified": bool(ok),
+    return {**extra, "n": n, "delta": w.delta, "stream_bytes": size, "verified": bool(ok),
             "bits_per_int": {"svb": 8.0 * s_svb / n, "vbyte": 8.0 * s_vb / n,
                              "extra": 8.0 * (s_svb - s_vb) / n},
             "decode": {"gints_per_s": n / ms_d / 1e6, "us": ms_d * 1e3,
