@@ -421,7 +421,7 @@ __device__ uint32_t range_local_carries(uint32_t *carries, u64 s0, u64 s1)
     return __shfl_sync(0xffffffffu, inc, 31);
 }
 
-__global__ void __launch_bounds__(kThreads) delta_prep_kernel(OffsetsArgs a)
+__global__ void __launch_bounds__(kThreads, 4) delta_prep_kernel(OffsetsArgs a)
 {
     __shared__ uint32_t s_w[2][kWarps];
     __shared__ u64 s_cta, s_etag, s_base;
