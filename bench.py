@@ -201,6 +201,22 @@ def reference_arm(args, rank: int):
     print(json.dumps(line), flush=True)
 
 
+def aggregate_replicas(total_ms: float, ints_per_rank: int, steps: int, dist=None, device=None):
+    """Whole-job timing of N replicas: the longest rank's timed region (each
+    rank decodes its own copy of the workload, no data-path collective) and
+    the rate of all ranks' integers over it, in Gints/s.  dist is
+    torch.distributed with an initialised process group, or None for one
+    process."""
+    world = 1
+    if dist is not None:
+        import torch
+        world = dist.get_world_size()
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, ints_per_rank * steps * world / (total_ms / 1e3) / 1e9
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -273,13 +289,8 @@ def main():
         t_end.record(stream)
         torch.cuda.synchronize()
     barrier()
-    total_ms = t_start.elapsed_time(t_end)
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms, value = aggregate_replicas(t_start.elapsed_time(t_end), n, args.steps, dist, dev)
     step_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
-    value = n * args.steps * world / (total_ms / 1e3) / 1e9
     alg_bytes = in_len + 4 * n  # control + data read, 4n written
 
     # Per-kernel times, live: a second pass of the same K steps with the
