@@ -323,12 +323,14 @@ __device__ void range_carries(uint32_t *carries, u64 s0, u64 s1, u64 cta, uint32
 // it holds 512 one-byte gaps, the common case of sorted lists with small
 // gaps.  For each such sub-tile the warp loads the 16-byte-aligned run that
 // holds its bytes, one chunk per lane, coalesced, and each lane byte-sums its
-// chunk with dp4a; a reduce-scatter over the warp (31 shuffles for 32
-// sub-tiles) leaves sub-tile l's run total in lane l, and lane l corrects it
-// for the run's ragged ends.  Every other sub-tile is taken by the whole
-// warp: staged into one of the warp's two shared slots with cp.async (the
-// next one's copies in flight) and decoded with the decode pass's sub-tile
-// code.  The loads keep the stream in L2 (evict-last) for the decode pass,
+// chunk with dp4a; in batches of 8 runs, a reduce-scatter and a butterfly
+// over the warp (10 shuffles per batch) leave sub-tile l's run total in lane
+// l, and lane l corrects it for the run's ragged ends.  The kernel runs 4
+// CTAs per SM: its waits are chains of dependent loads and barriers, so more
+// resident warps pay more than deeper per-warp batches.  Every other
+// sub-tile is taken by the whole warp: staged into one of the warp's two
+// shared slots with cp.async (the next one's copies in flight) and decoded
+// with the decode pass's sub-tile code.  The loads keep the stream in L2 (evict-last) for the decode pass,
 // which reads it again.  Reads stay inside the stream as far as the CTA's
 // own data ends and inside [in, in + in_len): on a stream cut short the sums
 // are meaningless, the truncation verdict is set and the decode pass does
