@@ -131,8 +131,8 @@ __device__ __forceinline__ uint32_t sum64(const OffsetsArgs &a, u64 q, uint32_t 
 }
 
 // This CTA's range of groups [g0, g1): the offsets of its sub-tiles relative
-// to the range go to offs, warp 0 chains the range total with the ranges
-// before by one look-back, then the base is added.  The CTA holding the last
+// to the range go to offs, the CTA sums the published totals of the ranges
+// before (its base), then the base is added.  The CTA holding the last
 // group also writes the stream size and the truncation verdict.  Ends with a
 // block barrier (the range's offsets are then visible to the whole CTA).
 struct RangeBytes {
@@ -141,7 +141,7 @@ struct RangeBytes {
 };
 
 __device__ RangeBytes range_offsets(const OffsetsArgs &a, u64 cta, u64 etag, u64 g0, u64 g1,
-                                    uint32_t (*s_w)[kWarps], u64 *s_base)
+                                    uint32_t (*s_w)[kWarps], u64 *s_base, u64 *s_part)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t last_nints = (uint32_t)(a.n - 4 * (a.nquads - 1));
@@ -173,33 +173,67 @@ __device__ RangeBytes range_offsets(const OffsetsArgs &a, u64 cta, u64 etag, u64
         // and the barrier of that iteration orders this read before reuse.
     }
 
-    // Chain the CTA totals, then add this CTA's base to its sub-tiles.
-    if (warp == 0) {
-        TileStatus *me = &a.st[cta];
-        u64 base = 0;
-        bool ok = true;
-        if (cta == 0) {
-            if (lane == 0)
-                publish(&me->off_tag, &me->off_pre, running, kFlagPrefix, etag);
-        } else {
-            if (lane == 0)
-                publish(&me->off_tag, &me->off_agg, running, kFlagAgg, etag);
-            base = lookback<false>(a.st, cta, etag, a.spin_limit, a.hdr, ok);
-            if (ok && lane == 0)
-                publish(&me->off_tag, &me->off_pre, base + running, kFlagPrefix, etag);
-        }
-        if (lane == 0) {
-            if (!ok)
+    // The range's base: publish this range's total, then the whole CTA sums
+    // the totals of every range before it.  Ranges are claimed in order, so
+    // each earlier range belongs to a CTA that has started, and a CTA
+    // publishes its total without waiting on anyone: no chain of prefixes is
+    // needed.  Each thread inspects kBasePer records per pass, their tag
+    // loads in flight together; a release store of a tag, a relaxed load that
+    // sees it and an acquire fence order the total's load after it.  Every
+    // wait is bounded: after spin_limit polling rounds, or once another CTA
+    // has raised an error, the thread records a timeout and stops waiting.
+    constexpr int kBasePer = 4;
+    if (tid == 0)
+        publish(&a.st[cta].off_tag, &a.st[cta].off_agg, running, kFlagAgg, etag);
+    u64 part = 0;
+    for (u64 p0 = 0; p0 < cta; p0 += (u64)kThreads * kBasePer) {
+        u64 tags[kBasePer];
+        auto rec = [&](int i) { return p0 + (u64)tid + (u64)i * kThreads; };
+        auto ready = [&](u64 t) { return (t & ~3ull) == etag && (t & 3ull) != kFlagNone; };
+#pragma unroll
+        for (int i = 0; i < kBasePer; i++)
+            tags[i] = rec(i) < cta ? ld_relaxed(&a.st[rec(i)].off_tag) : (etag | kFlagAgg);
+        for (u64 spins = 0;;) {
+            bool all = true;
+#pragma unroll
+            for (int i = 0; i < kBasePer; i++)
+                all = all && ready(tags[i]);
+            if (all)
+                break;
+            if (++spins > a.spin_limit || ((spins & 31) == 0 && error_raised(a.hdr))) {
                 raise_error(a.hdr, kErrTimeout);
-            if (ok && g1 == a.groups && g0 < g1) {  // the CTA holding the last sub-tile
-                u64 stream = a.nquads + base + running;
-                a.offs[a.nsubs] = base + running;
-                st_relaxed(&a.hdr->total, stream);
-                if (stream > a.in_len)
-                    raise_error(a.hdr, kErrTruncated);
+                break;
             }
-            *s_base = base;
+            if (spins > 4)
+                __nanosleep(spins < 64 ? 32 : 256);
+#pragma unroll
+            for (int i = 0; i < kBasePer; i++)
+                if (!ready(tags[i]))
+                    tags[i] = ld_relaxed(&a.st[rec(i)].off_tag);
         }
+        fence_acq_rel_gpu();
+#pragma unroll
+        for (int i = 0; i < kBasePer; i++)
+            if (rec(i) < cta && ready(tags[i]))
+                part += ld_relaxed(&a.st[rec(i)].off_agg);
+    }
+    part = warp_sum64(part);
+    if (lane == 0)
+        s_part[warp] = part;
+    __syncthreads();
+    if (tid == 0) {
+        u64 base = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; w++)
+            base += s_part[w];
+        if (g1 == a.groups && g0 < g1) {  // the CTA holding the last sub-tile
+            const u64 stream = a.nquads + base + running;
+            a.offs[a.nsubs] = base + running;
+            st_relaxed(&a.hdr->total, stream);
+            if (stream > a.in_len)
+                raise_error(a.hdr, kErrTruncated);
+        }
+        *s_base = base;
     }
     __syncthreads();
     const u64 base = *s_base;
@@ -228,7 +262,7 @@ __device__ __forceinline__ void offsets_done(const OffsetsArgs &a)
 __global__ void __launch_bounds__(kThreads) offsets_kernel(OffsetsArgs a)
 {
     __shared__ uint32_t s_w[2][kWarps];
-    __shared__ u64 s_cta, s_etag, s_base;
+    __shared__ u64 s_cta, s_etag, s_base, s_part[kWarps];
 
     if (threadIdx.x == 0) {
         s_cta = atomicAdd(&a.hdr->a_counter, 1ull);
@@ -238,7 +272,7 @@ __global__ void __launch_bounds__(kThreads) offsets_kernel(OffsetsArgs a)
     const u64 cta = s_cta;
     const u64 g0 = cta * a.per_cta;
     const u64 g1 = min(g0 + a.per_cta, a.groups);
-    range_offsets(a, cta, s_etag, g0, g1, s_w, &s_base);
+    range_offsets(a, cta, s_etag, g0, g1, s_w, &s_base, s_part);
     offsets_done(a);
 }
 
@@ -426,7 +460,7 @@ __device__ uint32_t range_local_carries(uint32_t *carries, u64 s0, u64 s1)
 __global__ void __launch_bounds__(kThreads, 4) delta_prep_kernel(OffsetsArgs a)
 {
     __shared__ uint32_t s_w[2][kWarps];
-    __shared__ u64 s_cta, s_etag, s_base;
+    __shared__ u64 s_cta, s_etag, s_base, s_part[kWarps];
     __shared__ uint32_t s_last;
     __shared__ uint4 s_lowm[16];  // s_lowm[p] keeps the bytes below p of a 16-byte chunk
     __shared__ __align__(16) uint8_t s_slot[kWarps][2][kPrepSlot];
@@ -444,7 +478,7 @@ __global__ void __launch_bounds__(kThreads, 4) delta_prep_kernel(OffsetsArgs a)
     const u64 cta = s_cta, etag = s_etag;
     const u64 g0 = cta * a.per_cta;
     const u64 g1 = min(g0 + a.per_cta, a.groups);
-    const RangeBytes r = range_offsets(a, cta, etag, g0, g1, s_w, &s_base);
+    const RangeBytes r = range_offsets(a, cta, etag, g0, g1, s_w, &s_base, s_part);
 
     const u64 s0 = g0 * kOffGroupSubs, s1 = min(g1 * kOffGroupSubs, a.nsubs);
     const u64 range_end = r.base + r.bytes;
