@@ -8,9 +8,10 @@
 //   offsets_kernel   reads only the control stream (2 bits per integer) and
 //                    writes the data-stream offset of every sub-tile of
 //                    kSubQuads quads (512 integers).  Persistent CTAs each sum
-//                    a contiguous range, chain the range totals with one
-//                    decoupled look-back, then add their base.  It also writes
-//                    the stream's size and checks it against in_len.
+//                    a contiguous range, claimed in order, publish the range
+//                    total and find their base as the sum of all earlier
+//                    ranges' totals, then add it.  It also writes the
+//                    stream's size and checks it against in_len.
 //   decode_tiled     persistent CTAs with one producer warp and eight
 //                    consumer warps.  The producer takes tiles of eight
 //                    sub-tiles round-robin, reads their offsets and has the TMA
@@ -21,12 +22,13 @@
 //                    the other warps - and releases it on the stage's "empty"
 //                    mbarrier.  Nothing waits on another CTA.
 // Differential streams need each sub-tile's carry-in: prev plus the sum of all
-// earlier gaps (Sec. 2's prefix sum continued across sub-tiles).  A sums pass
-// runs the same pipeline without stores: persistent CTAs take contiguous tile
-// ranges, each warp sums its sub-tile's gaps, and one look-back per CTA
-// chains the range totals into per-sub-tile carries.  The decode pass then adds
-// a known carry.  For streams that fit in L2 (129 MB) the second read of the
-// stream is served by L2.
+// earlier gaps (Sec. 2's prefix sum continued across sub-tiles).  By default
+// delta_prep_kernel takes the offsets pass's place and also sums each
+// sub-tile's gaps into carry-ins (see its own comment); the decode pass then
+// adds a known carry.  The earlier form, kept as a decoder variant, runs a
+// sums pass after offsets_kernel: the decode pipeline without stores over
+// contiguous tile ranges, each warp summing its sub-tile's gaps and one
+// look-back per CTA chaining the range totals into per-sub-tile carries.
 //
 // Bytes outside the stream are never read: each tile's range is copied as its
 // 16-byte-aligned interior by the bulk engine plus a ragged head and tail of
