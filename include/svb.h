@@ -357,6 +357,19 @@ int svb_testhook_lookback_timeout(const uint8_t *stream_in, size_t n, uint32_t *
                                   uint64_t spin_limit, svb_result *d_result, void *ws,
                                   size_t ws_bytes, svb_stream_t stream);
 
+/* Failure-detection check of the offsets pass (the reduce-then-decode
+ * decoder's first kernel): its one CTA takes the second range of control
+ * bytes and waits for the first range's byte total, which nothing publishes,
+ * so the wait runs out after spin_limit polls.  A decode of all tiles
+ * follows, which decodes nothing.  d_result must then hold SVB_ETIMEOUT, and
+ * the workspace and context stay usable.  stream_in holds a stream of
+ * n > 65,536 integers (at least two ranges of 16,384 control bytes);
+ * ws is an initialised workspace of svb_workspace_size(n) bytes.  Returns
+ * SVB_OK, SVB_EINVAL or SVB_ECUDA. */
+int svb_testhook_offsets_timeout(const uint8_t *stream_in, size_t n, uint32_t *out,
+                                 uint64_t spin_limit, svb_result *d_result, void *ws,
+                                 size_t ws_bytes, svb_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

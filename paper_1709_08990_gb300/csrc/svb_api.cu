@@ -615,4 +615,18 @@ int svb_testhook_lookback_timeout(const uint8_t *stream_in, size_t n, uint32_t *
                               reinterpret_cast<cudaStream_t>(stream), spin_limit_, 1, 1);
 }
 
+int svb_testhook_offsets_timeout(const uint8_t *stream_in, size_t n, uint32_t *out,
+                                 uint64_t spin_limit_, svb_result *d_result, void *ws,
+                                 size_t ws_bytes, svb_stream_t stream)
+{
+    if (!stream_in || !out || !d_result || !ws || ws_bytes < svb_workspace_size(n))
+        return SVB_EINVAL;
+    if (n <= 64 * (u64)svb::kThreads * 4)  // at least two ranges of the offsets pass
+        return SVB_EINVAL;
+    return svb::launch_offsets_timeout_check(stream_in, n, out, ws,
+                                             reinterpret_cast<svb::DeviceResult *>(d_result),
+                                             reinterpret_cast<cudaStream_t>(stream),
+                                             spin_limit_);
+}
+
 }  // extern "C"

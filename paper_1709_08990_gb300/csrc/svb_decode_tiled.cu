@@ -1120,6 +1120,30 @@ static TiledArgs tiled_args(const uint8_t *in, u64 n, uint32_t *out, uint32_t pr
     return t;
 }
 
+__global__ void set_claim_counter_kernel(WsHeader *hdr, u64 v)
+{
+    hdr->a_counter = v;
+}
+
+// Failure-detection check of the offsets pass's wait for earlier ranges'
+// totals: the claim counter starts at 1, so the one CTA launched takes range
+// 1 and waits for range 0's total, which no CTA publishes; the wait runs out
+// after spin_limit polls and records SVB_ETIMEOUT.  A decode over all tiles
+// follows: it sees the error, decodes nothing and readies the workspace
+// (counters reset, epoch advanced) for the next call.
+int launch_offsets_timeout_check(const uint8_t *in, u64 n, uint32_t *out, void *ws,
+                                 DeviceResult *result, cudaStream_t stream, u64 spin_limit)
+{
+    u64 grid = 0;
+    OffsetsArgs o = offsets_args(in, ~0ull, n, ws, spin_limit, 1, &grid);
+    set_claim_counter_kernel<<<1, 1, 0, stream>>>(o.hdr, 1);
+    offsets_kernel<<<1, kThreads, 0, stream>>>(o);
+    TiledArgs t = tiled_args(in, n, out, 0, ws, result, spin_limit);
+    const u64 g = max((u64)1, min((u64)tiled_grid<kPlain>(), t.ntiles));
+    decode_tiled_kernel<kPlain><<<(unsigned)g, kDecBlock, sizeof(Pipe), stream>>>(t);
+    return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
 u64 decode_tile_ints()
 {
     return 4 * (u64)kTileQuads;

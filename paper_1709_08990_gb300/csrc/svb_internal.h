@@ -32,6 +32,10 @@ int launch_offsets(const uint8_t *in, u64 in_len, u64 n, void *ws, cudaStream_t 
                    u64 spin_limit);
 int launch_decode_range(const uint8_t *in, u64 n, uint32_t *out, void *ws, DeviceResult *result,
                         cudaStream_t stream, u64 tile0, u64 tile1);
+// Failure-detection check of the offsets pass's bounded wait (see
+// svb_testhook_offsets_timeout).
+int launch_offsets_timeout_check(const uint8_t *in, u64 n, uint32_t *out, void *ws,
+                                 DeviceResult *result, cudaStream_t stream, u64 spin_limit);
 u64 decode_tile_ints();
 
 int launch_encode(const uint32_t *in, u64 n, uint8_t *out, uint32_t prev, bool delta, void *ws,

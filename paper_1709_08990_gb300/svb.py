@@ -62,6 +62,7 @@ def lib() -> ctypes.CDLL:
             "svb_encode_async": ([vp, sz, vp, u32, i32, vp, vp, sz, vp], i32),
             "svb_decode_async": ([vp, sz, sz, vp, u32, i32, vp, vp, sz, vp], i32),
             "svb_testhook_lookback_timeout": ([vp, sz, vp, u64, vp, vp, sz, vp], i32),
+            "svb_testhook_offsets_timeout": ([vp, sz, vp, u64, vp, vp, sz, vp], i32),
             "svb_decode_noalloc": ([vp, sz, sz, vp, u32, i32, vp], sz),
             "svb_query_batch": ([vp, sz, vp, i32, vp, sz, vp, vp], i32),
             "svb_append": ([vp, sz, vp, sz, sz, sz, vp, sz, u32, i32], sz),
@@ -314,6 +315,12 @@ def svb_testhook_lookback_timeout(stream_in, n, out, spin_limit, d_result, ws, w
                                   stream=None) -> int:
     return lib().svb_testhook_lookback_timeout(_p(stream_in), n, _p(out), spin_limit,
                                                _p(d_result), _p(ws), ws_bytes, _stream(stream))
+
+
+def svb_testhook_offsets_timeout(stream_in, n, out, spin_limit, d_result, ws, ws_bytes,
+                                 stream=None) -> int:
+    return lib().svb_testhook_offsets_timeout(_p(stream_in), n, _p(out), spin_limit,
+                                              _p(d_result), _p(ws), ws_bytes, _stream(stream))
 
 
 # ---- tensor conveniences (allocation through torch, compute in the library) --

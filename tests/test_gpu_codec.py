@@ -230,6 +230,39 @@ def test_lookback_timeout_is_reported_and_context_survives():
     assert np.array_equal(host_u32(out), x)
 
 
+def test_offsets_pass_timeout_is_reported_and_context_survives():
+    """The offsets pass's one CTA takes the second range and waits for the
+    first range's byte total, which nothing publishes: the wait gives up after
+    its spin limit, SVB_ETIMEOUT comes back, and the same workspace then
+    decodes normally, plain and differential."""
+    n = 3 * 65536 + 5
+    x = values("uniform", n, 6)
+    s = oracle.encode(x)
+    d = to_dev(s)
+    ws_bytes = svb.svb_workspace_size(n)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=DEV)
+    svb.svb_workspace_init(ws, ws_bytes)
+    res = torch.zeros(2, dtype=torch.int64, device=DEV)
+    out = torch.zeros(n, dtype=torch.int32, device=DEV)
+    assert svb.svb_testhook_offsets_timeout(d, n, out, 2000, res, ws, ws_bytes) == 0
+    r = res.cpu().numpy()
+    assert r[1] == svb.SVB_ETIMEOUT
+    assert r[0] == -1  # SVB_ERROR as int64
+    assert svb.svb_decode_async(d, s.size, n, out, 0, 0, res, ws, ws_bytes) == 0
+    r = res.cpu().numpy()
+    assert r[1] == 0 and r[0] == s.size
+    assert np.array_equal(host_u32(out), x)
+    xs = values("sorted", n, 6)
+    ds = oracle.encode(xs, delta=True)
+    assert svb.svb_decode_async(to_dev(ds), ds.size, n, out, 0, 1, res, ws, ws_bytes) == 0
+    r = res.cpu().numpy()
+    assert r[1] == 0 and r[0] == ds.size
+    assert np.array_equal(host_u32(out), xs)
+    # too few integers for two ranges
+    assert svb.svb_testhook_offsets_timeout(d, 65536, out, 2000, res, ws, ws_bytes) == \
+        svb.SVB_EINVAL
+
+
 def test_host_buffer_forms():
     n = 123_457
     x = values("sorted", n, 5)
