@@ -57,3 +57,47 @@ def test_list_lengths_and_lists():
         assert np.all(np.diff(lst) > 0) and lst.max() < 1 << 31 and lst.min() >= 1
     one = W.posting_list(4, int(first[37]), int(sub[37]))
     assert np.array_equal(one, v[int(first[37]):int(first[37]) + int(sub[37])])
+
+
+def test_serve_requests_follow_the_recipe():
+    """Poisson arrivals, 5 % encodes of fresh sorted lists, decodes of pool
+    lists chosen Zipf(1.1) over ranks mapped to ids by a permutation."""
+    k = 2000
+    pool = W.list_lengths(11, k, 8, 5000)
+    count, rate = 20000, 1e5
+    r = W.serve_requests(pool, count, rate, seed=5)
+    assert np.all(np.diff(r.arrival) >= 0)
+    gaps = np.diff(np.concatenate([[0.0], r.arrival]))
+    assert abs(gaps.mean() * rate - 1) < 0.05          # mean 1/rate
+    assert abs(np.std(gaps) * rate - 1) < 0.05         # exponential: sd = mean
+    frac = r.is_encode.mean()
+    assert abs(frac - 0.05) < 0.01
+    dec = ~r.is_encode
+    assert np.all((r.list_id[dec] >= 0) & (r.list_id[dec] < k))
+    assert np.array_equal(r.n[dec], pool[r.list_id[dec]])
+    assert np.all(r.list_id[r.is_encode] == -1) and np.all(r.enc_first[dec] == -1)
+    # Zipf(1.1): the most requested list takes 1 / H_{k,1.1} of the decodes
+    counts = np.bincount(r.list_id[dec], minlength=k)
+    h = np.sum(np.arange(1, k + 1, dtype=np.float64) ** -1.1)
+    assert abs(counts.max() / dec.sum() - 1 / h) < 0.02
+    top, second = np.sort(counts)[-1], np.sort(counts)[-2]
+    assert 1.8 < top / second < 2.6                    # rank 1 / rank 2 = 2^1.1 = 2.14
+    # fresh lists: back to back, each strictly increasing below 2^31
+    e = np.flatnonzero(r.is_encode)
+    ends = r.enc_first[e] + r.n[e]
+    assert r.enc_first[e[0]] == 0 and np.array_equal(r.enc_first[e[1:]], ends[:-1])
+    assert r.enc_values.size == ends[-1]
+    for j in e[:50]:
+        v = r.enc_values[r.enc_first[j]:r.enc_first[j] + r.n[j]].astype(np.int64)
+        assert np.all(np.diff(v) > 0) and v[-1] < (1 << 31)
+
+
+def test_serve_requests_are_reproducible_and_burst_at_time_zero():
+    pool = W.list_lengths(12, 100, 8, 1000)
+    a = W.serve_requests(pool, 500, None, seed=7)
+    b = W.serve_requests(pool, 500, None, seed=7)
+    assert np.all(a.arrival == 0)
+    for f in ("is_encode", "list_id", "n", "enc_first", "enc_values"):
+        assert np.array_equal(getattr(a, f), getattr(b, f))
+    c = W.serve_requests(pool, 500, None, seed=8)
+    assert not np.array_equal(a.list_id, c.list_id)
