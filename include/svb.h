@@ -129,7 +129,9 @@ const char *svb_error_string(int status);
 void svb_set_spin_limit(uint64_t iterations);
 
 /* Decoder variant used by every decode call of this process:
- *   SVB_DECODE_AUTO (0)        the default, currently SVB_DECODE_TWO_PASS;
+ *   SVB_DECODE_AUTO (0)        the default: SVB_DECODE_SINGLE_PASS for plain
+ *                              streams of at most 2^20 integers (launch-
+ *                              bound), SVB_DECODE_TWO_PASS otherwise;
  *   SVB_DECODE_SINGLE_PASS (1) one kernel: each tile sums its control bytes,
  *                              finds its data offset by a decoupled look-back
  *                              over its predecessors, then decodes;
