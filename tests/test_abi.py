@@ -71,3 +71,39 @@ def test_size_from_control_matches_oracle(lib):
 def test_error_strings(lib):
     for code in range(6):
         assert svb.error_string(code)
+
+
+def test_binding_dtypes_match_the_header_structs(tmp_path):
+    """The numpy dtypes svb.py hands to the batched and query calls have the
+    field offsets and sizes of the C structs in include/svb.h (checked by a
+    small C program compiled against the header)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"svb_list": svb.list_dtype(), "svb_query": svb.query_dtype(),
+               "svb_answer": svb.answer_dtype(),
+               "svb_result": np.dtype([("bytes", "<u8"), ("status", "<u8")])}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "svb.h"', "int main(void) {"]
+    for name, dt in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for f in dt.names:
+            lines.append(f'printf("{name} {f} %zu %zu\\n", offsetof({name}, {f}), '
+                         f'sizeof((({name} *)0)->{f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    assert len(out.splitlines()) == sum(len(dt.names) + 1 for dt in structs.values())
+    for line in out.splitlines():
+        parts = line.split()
+        dt = structs[parts[0]]
+        if parts[1] == "size":
+            assert dt.itemsize == int(parts[2]), line
+        else:
+            off, size = dt.fields[parts[1]][1], dt.fields[parts[1]][0].itemsize
+            assert (off, size) == (int(parts[2]), int(parts[3])), line
