@@ -218,6 +218,56 @@ def nonminimal_codes(c) -> list[str]:
     return []
 
 
+def data_bytes_from_control(c) -> list[str]:
+    """Sec. 4: a control byte covers C = 4 + (sum of its codes) data bytes,
+    so 0x00 covers 4 and 0xFF covers 16; Fig. 3's two control bytes C1 40
+    (eight integers) cover its 13 data bytes; the pad fields of an
+    incomplete last control byte cover none (they code no integer).  Also,
+    for random length patterns, the control bytes built here from the
+    pattern cover exactly the pattern's sum of lengths."""
+    errs = []
+    g = _read_golden("fig3_stream.txt")
+    fig3 = bytes(int(b, 16) for b in g["stream"][0].split())
+    cases = [(fig3[:2], 8, 13), (b"\x00", 4, 4), (b"\xff", 4, 16),
+             (b"\xff", 1, 4), (b"\xff", 2, 8), (b"\xff", 3, 12),
+             (b"\xfc", 1, 1), (b"\xf0", 2, 2), (b"\xc0", 3, 3),
+             (b"\xff\xff\xfc", 9, 33)]
+    for ctrl, n, want in cases:
+        got = c.data_bytes(np.frombuffer(ctrl, dtype=np.uint8), n)
+        if got != want:
+            errs.append(f"data bytes of {ctrl.hex()} for n={n}: {got}, want {want}")
+    rng = np.random.default_rng(41)
+    for n in (1, 2, 3, 5, 6, 7, 31, 1001):
+        lens = rng.integers(1, 5, n)
+        ctrl = np.zeros((n + 3) // 4, dtype=np.uint8)
+        for i, L in enumerate(lens):
+            ctrl[i // 4] |= np.uint8((int(L) - 1) << (2 * (i % 4)))
+        if n % 4:  # pad fields set: they must still count nothing
+            ctrl[-1] |= np.uint8((0xFF << (2 * (n % 4))) & 0xFF)
+        got = c.data_bytes(ctrl, n)
+        if got != int(lens.sum()):
+            errs.append(f"data bytes of a random pattern, n={n}: {got}, want {int(lens.sum())}")
+    return errs
+
+
+def max_size_is_reached(c) -> list[str]:
+    """The largest stream has every integer four bytes long (Sec. 3: values
+    of 2^24 and above take four bytes; Sec. 4: ceil(n/4) control bytes before
+    the data).  Encoding n such values, for every n mod 4, gives exactly
+    svb_ref_max_compressed_size(n) bytes, and no stream of n values is longer."""
+    errs = []
+    rng = np.random.default_rng(42)
+    for n in (0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 63, 1000, 4097):
+        x = rng.integers(1 << 24, 1 << 32, n, dtype=np.uint64).astype(np.uint32)
+        s = c.encode(x)
+        if c.max_compressed_size(n) != s.size:
+            errs.append(f"max size n={n}: {c.max_compressed_size(n)}, four-byte values take {s.size}")
+        y = rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32)
+        if c.encode(y).size > c.max_compressed_size(n):
+            errs.append(f"max size n={n}: a random stream is longer")
+    return errs
+
+
 def _paper_query_list(rng, bits: int, n: int = 256) -> np.ndarray:
     """The setup of Sec. 5's seek/select test: n random deltas in [0, 2^b),
     prefix-summed."""
@@ -304,7 +354,8 @@ def seek_select_truncation(c) -> list[str]:
 
 ALL = [fig3_stream, fig1_blocks, sec2_prefix_sum, zero_control, control_range,
        length_boundaries, round_trips, definition_agrees, truncation,
-       pad_fields_ignored, nonminimal_codes, seek_matches_searchsorted,
+       pad_fields_ignored, nonminimal_codes, data_bytes_from_control, max_size_is_reached,
+       seek_matches_searchsorted,
        seek_first_match_unsorted, select_matches_definition, seek_select_truncation]
 
 

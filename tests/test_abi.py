@@ -61,6 +61,7 @@ def test_size_from_control_matches_oracle(lib):
         s = oracle.encode(x)
         ctrl = np.ascontiguousarray(s[: (n + 3) // 4])
         assert svb.svb_compressed_size_from_control(ctrl, n) == s.size
+        assert s.size == oracle.control_bytes(n) + oracle.data_bytes(ctrl, n)
         # pad fields of the last control byte carry no bytes
         if n % 4:
             ctrl2 = ctrl.copy()

@@ -2,8 +2,10 @@
 
 Pins: Fig. 3's exact bytes, Fig. 1's block sizes, Sec. 2's prefix-sum
 example, the all-zero control byte (Sec. 4), C in [4, 16] (Fig. 4), the
-length boundaries (Sec. 3), the size formula (Sec. 4), brute force over
-every length pattern for n <= 12, and an independent Python definition.
+length boundaries (Sec. 3), the size formula (Sec. 4), the data bytes a run
+of control bytes covers (Sec. 4, Fig. 3), the largest stream (four-byte
+values, Sec. 3-4), brute force over every length pattern for n <= 12, and an
+independent Python definition.
 Mutation tests plant plausible mistakes in copies of the oracle source and
 check that the pins catch each one.
 """
@@ -80,10 +82,16 @@ def test_size_formula_on_workload(ref):
     assert k == s.size and np.array_equal(back, x)
 
 
-def test_max_compressed_size(ref):
-    for n in [0, 1, 3, 4, 5, 1000, 1 << 30]:
-        assert ref.max_compressed_size(n) == (n + 3) // 4 + 4 * n
-        assert ref.control_bytes(n) == (2 * n + 7) // 8
+def test_control_bytes_per_tail(ref):
+    """Sec. 4: one control byte per four integers, rounded up; the count
+    grows by one exactly at n = 1, 5, 9, ... (checked against encoded
+    all-one-byte streams, whose size is control bytes + n)."""
+    prev = 0
+    for n in range(0, 41):
+        k = ref.control_bytes(n)
+        assert k - prev == (1 if n % 4 == 1 else 0)
+        assert ref.encode(np.zeros(n, dtype=np.uint32)).size == k + n
+        prev = k
 
 
 def test_empty(ref):
@@ -119,6 +127,16 @@ MUTANTS = {
     "seek_strict_greater": [("if (v >= target)", "if (v > target)")],
     # select returns the integer before the one asked for
     "select_off_by_one": [("for (size_t i = 0; i <= index; i++)", "for (size_t i = 0; i < index; i++)")],
+    # data bytes counted over the pad fields of the last control byte too
+    "data_bytes_counts_pads": [("for (size_t i = 0; i < n; i++)\n        total +=",
+                                "for (size_t i = 0; i < 4 * ((n + 3) / 4); i++)\n        total +=")],
+    # data bytes taken as the sum of the codes, lengths minus one
+    "data_bytes_codes_only": [("total += ((ctrl[i / 4] >> (2 * (i % 4))) & 3u) + 1;",
+                               "total += ((ctrl[i / 4] >> (2 * (i % 4))) & 3u);")],
+    # largest size with three bytes per integer at most
+    "max_size_three_bytes": [("svb_ref_control_bytes(n) + 4 * n", "svb_ref_control_bytes(n) + 3 * n")],
+    # largest size with the control count rounded down
+    "max_size_floor_control": [("svb_ref_control_bytes(n) + 4 * n", "n / 4 + 4 * n")],
     # decoder forgets the truncation check
     "no_truncation_check": [("if (len > in_len - pos)\n            return SVB_REF_ERROR;", "")],
 }
