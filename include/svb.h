@@ -258,17 +258,18 @@ int svb_batch_encode(const void *d_plan, const svb_list *d_lists, const uint32_t
  * allocator, or a latency-bound path that cannot afford cudaMalloc/cudaFree,
  * which may synchronize the device.
  *
- * Scratch: a fixed device array of about 1.4 MB inside the library, enough
+ * Scratch: a fixed device array of about 1.5 MB inside the library, enough
  * for n <= SVB_NOALLOC_MAX_N; every GPU that loads the library holds it until
  * the process exits.  n > SVB_NOALLOC_MAX_N returns SVB_ERROR with
  * SVB_EINVAL.  The first call on a device looks up the array's device
- * address (make that first call before any stream capture).  All calls share
- * the array: calls that overlap on the GPU race, so order them on one stream
- * or serialize them on the host.
+ * address.  All calls share the array: calls that overlap on the GPU race,
+ * so order them on one stream or serialize them on the host.
  *
  * in[0..in_len) is the stream, out[0..n) receives the integers, delta and prev
- * as in svb_decode_checked.  Runs on `stream` and waits for it.  Returns the
- * bytes consumed, or SVB_ERROR with svb_last_error() set. */
+ * as in svb_decode_checked.  Runs on `stream` and synchronizes it (the byte
+ * count comes back through a host copy), so it cannot be called while
+ * `stream` is being captured into a CUDA graph.  Returns the bytes consumed,
+ * or SVB_ERROR with svb_last_error() set; n = 0 returns 0 with SVB_OK. */
 size_t svb_decode_noalloc(const uint8_t *in, size_t in_len, size_t n, uint32_t *out,
                           uint32_t prev, int delta, svb_stream_t stream);
 

@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kThreads, 4) decode_kernel(DecodeArgs a)
 
     if (tid == 0) {
         s_tile = atomicAdd(&a.hdr->tile_counter, 1ull) + a.tile_base;
-        s_etag = (ld_relaxed(&a.hdr->epoch) + 1) << 2;
+        s_etag = epoch_tag(a.hdr);
         s_skip = (s_tile >= a.ntiles || error_raised(a.hdr)) ? 1u : 0u;
     }
     __syncthreads();

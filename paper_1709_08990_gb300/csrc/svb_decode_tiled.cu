@@ -72,7 +72,7 @@ struct OffsetsArgs {
     u64 spin_limit;
     uint32_t in_aligned;
     uint32_t prev;       // delta_prep_kernel: the value before the first integer
-    uint32_t *carries;   // delta_prep_kernel: per sub-tile carry-in
+    u64 *carries;        // delta_prep_kernel: per sub-tile carry-in (zero-extended)
 };
 
 // Data bytes covered by the control bytes of quads [q, q + 16) taken from
@@ -101,8 +101,10 @@ __device__ __forceinline__ uint32_t chunk_bytes(uint4 v, u64 q, u64 nquads, uint
     return t;
 }
 
-// Sum of the data bytes of 64 quads starting at q (one thread's share).
-__device__ __forceinline__ uint32_t sum64(const OffsetsArgs &a, u64 q, uint32_t last_nints)
+// Sum of the data bytes of 64 quads starting at q (one thread's share); a
+// has in, nquads and in_aligned.
+template <class Args>
+__device__ __forceinline__ uint32_t sum64(const Args &a, u64 q, uint32_t last_nints)
 {
     uint32_t sum = 0;
     if (q >= a.nquads)
@@ -130,6 +132,22 @@ __device__ __forceinline__ uint32_t sum64(const OffsetsArgs &a, u64 q, uint32_t 
         }
     }
     return sum;
+}
+
+// 16 control bytes (quads q .. q + 15) as one chunk, zero past nquads.
+template <class Args>
+__device__ __forceinline__ uint4 ctrl_chunk(const Args &a, u64 q)
+{
+    if (q >= a.nquads)
+        return make_uint4(0u, 0u, 0u, 0u);
+    if (a.in_aligned && q + 16 <= a.nquads)
+        return __ldg(reinterpret_cast<const uint4 *>(a.in + q));
+    uint32_t w[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int b = 0; b < 16; b++)
+        if (q + b < a.nquads)
+            w[b >> 2] |= (uint32_t)__ldg(a.in + q + b) << (8 * (b & 3));
+    return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
 // This CTA's range of groups [g0, g1): the offsets of its sub-tiles relative
@@ -268,7 +286,7 @@ __global__ void __launch_bounds__(kThreads) offsets_kernel(OffsetsArgs a)
 
     if (threadIdx.x == 0) {
         s_cta = atomicAdd(&a.hdr->a_counter, 1ull);
-        s_etag = (ld_relaxed(&a.hdr->epoch) + 1) << 2;
+        s_etag = epoch_tag(a.hdr);
     }
     __syncthreads();
     const u64 cta = s_cta;
@@ -309,7 +327,7 @@ __device__ __forceinline__ uint32_t zero_ctrl_sum(const uint8_t *D, uint32_t bas
 // the sums (its loads all in flight at once), the lane totals are scanned,
 // the range total is chained with the ranges before by one look-back (prev
 // starts the first range), and each lane writes its run's carries.
-__device__ void range_carries(uint32_t *carries, u64 s0, u64 s1, u64 cta, uint32_t prev,
+__device__ void range_carries(u64 *carries, u64 s0, u64 s1, u64 cta, uint32_t prev,
                               TileStatus *st, u64 etag, u64 spin_limit, WsHeader *hdr)
 {
     const int lane = threadIdx.x & 31;
@@ -318,7 +336,7 @@ __device__ void range_carries(uint32_t *carries, u64 s0, u64 s1, u64 cta, uint32
     uint32_t tot = 0;
 #pragma unroll 4
     for (u64 i = b; i < e; i++)
-        tot += carries[i];
+        tot += (uint32_t)carries[i];
     const uint32_t inc = warp_incl_scan(tot);
     const uint32_t run = __shfl_sync(0xffffffffu, inc, 31);
     TileStatus *me = &st[cta];
@@ -338,7 +356,7 @@ __device__ void range_carries(uint32_t *carries, u64 s0, u64 s1, u64 cta, uint32
         raise_error(hdr, kErrTimeout);
     uint32_t c = (uint32_t)base + inc - tot;
     for (u64 i = b; i < e; i++) {
-        const uint32_t v = carries[i];
+        const uint32_t v = (uint32_t)carries[i];
         carries[i] = c;
         c += v;
     }
@@ -440,7 +458,7 @@ __device__ __forceinline__ uint32_t bytesum4(uint4 x, uint32_t acc)
 // Gap sums carries[s0 .. s1) of one range into carry-ins relative to the
 // range (exclusive prefix); returns the range total.  One whole warp: each
 // lane takes a contiguous run of the sums, the lane totals are scanned.
-__device__ uint32_t range_local_carries(uint32_t *carries, u64 s0, u64 s1)
+__device__ uint32_t range_local_carries(u64 *carries, u64 s0, u64 s1)
 {
     const int lane = threadIdx.x & 31;
     const u64 per = (s1 - s0 + 31) / 32;
@@ -448,11 +466,11 @@ __device__ uint32_t range_local_carries(uint32_t *carries, u64 s0, u64 s1)
     uint32_t tot = 0;
 #pragma unroll 4
     for (u64 i = b; i < e; i++)
-        tot += carries[i];
+        tot += (uint32_t)carries[i];
     const uint32_t inc = warp_incl_scan(tot);
     uint32_t c = inc - tot;
     for (u64 i = b; i < e; i++) {
-        const uint32_t v = carries[i];
+        const uint32_t v = (uint32_t)carries[i];
         carries[i] = c;
         c += v;
     }
@@ -471,7 +489,7 @@ __global__ void __launch_bounds__(kThreads, 4) delta_prep_kernel(OffsetsArgs a)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
         s_cta = atomicAdd(&a.hdr->a_counter, 1ull);
-        s_etag = (ld_relaxed(&a.hdr->epoch) + 1) << 2;
+        s_etag = epoch_tag(a.hdr);
     }
     if (tid < 16)
         s_lowm[tid] = make_uint4(low_bytes_mask(tid), low_bytes_mask(tid - 4),
@@ -682,7 +700,7 @@ struct TiledArgs {
     u64 n, nquads, ntiles, nsubs;
     uint32_t *out;
     const u64 *offs;
-    uint32_t *carries;  // per sub-tile: written by kSums, read by kDelta
+    u64 *carries;       // per sub-tile: written by kSums, read by kDelta (zero-extended)
     WsHeader *hdr;
     TileStatus *st;
     DeviceResult *result;
@@ -732,30 +750,44 @@ __device__ void produce(const TiledArgs &a, Pipe &P, u64 first, int lane)
             const u64 sb = min(t * kSubs + lane, a.nsubs);
             off = a.offs[sb];
             if (kMode == kDelta && lane < kSubs && sb < a.nsubs) {
-                car = a.carries[sb];
+                car = (uint32_t)a.carries[sb];
                 if (a.range_subs)
                     car += (uint32_t)a.st[sb / a.range_subs].val_pre;
             }
         }
     };
     const uint8_t *stream_end = a.in + a.nquads + a.offs[a.nsubs];
-    u64 next = tile_of<kMode>(a, first, 0);
-    u64 noff = 0;
-    uint32_t ncar = 0;
-    fetch(next, noff, ncar);
-    for (uint32_t k = 0;; k++) {
+    // Offsets (and carries) of the next kAhead tiles are in flight at once,
+    // so a tile's metadata has kAhead stage fills to arrive in: one round
+    // trip per tile would bound a CTA whose tiles decode faster than that.
+    constexpr int kAhead = 4;
+    u64 qt[kAhead], qoff[kAhead];
+    uint32_t qcar[kAhead];
+#pragma unroll
+    for (int i = 0; i < kAhead; i++) {
+        qt[i] = tile_of<kMode>(a, first, i);
+        qoff[i] = 0;
+        qcar[i] = 0;
+        fetch(qt[i], qoff[i], qcar[i]);
+    }
+    bool done = false;
+    for (uint32_t k0 = 0; !done; k0 += kAhead) {
+#pragma unroll
+    for (int i = 0; i < kAhead; i++) {
+        const uint32_t k = k0 + i;
         const int s = k % kStages;
         if (k >= (uint32_t)kStages) {
             bool ok = mbar_wait_bounded(&P.empty[s], ((k / kStages) - 1) & 1u, kBarrierPolls);
             if (!__all_sync(0xffffffffu, ok)) {
                 if (lane == 0)
                     raise_error(a.hdr, kErrTimeout);
+                done = true;
                 break;
             }
         }
-        const u64 t = next;
-        const u64 off = noff;
-        const uint32_t car = ncar;
+        const u64 t = qt[i];
+        const u64 off = qoff[i];
+        const uint32_t car = qcar[i];
         if (t >= a.ntiles) {
             if (lane == 0) {
                 P.tile[s] = kNoTile;
@@ -764,11 +796,11 @@ __device__ void produce(const TiledArgs &a, Pipe &P, u64 first, int lane)
                 mbar_arrive(&P.full[s]);
             }
             issued = k + 1;
+            done = true;
             break;
         }
-        // Read the next tile's offsets now so that the loads overlap this one.
-        next = tile_of<kMode>(a, first, k + 1);
-        fetch(next, noff, ncar);
+        qt[i] = tile_of<kMode>(a, first, k + kAhead);
+        fetch(qt[i], qoff[i], qcar[i]);
         const u64 d0 = __shfl_sync(0xffffffffu, off, 0);
         const u64 d1 = __shfl_sync(0xffffffffu, off, kSubs);
         if (lane < kSubs) {
@@ -804,6 +836,7 @@ __device__ void produce(const TiledArgs &a, Pipe &P, u64 first, int lane)
         }
         issued = k + 1;
     }
+    }
     // Let every copy this warp started land before the CTA can exit: stage s
     // was filled (issued - 1 - s) / kStages + 1 times; wait for the last fill.
     if (lane == 0) {
@@ -814,6 +847,75 @@ __device__ void produce(const TiledArgs &a, Pipe &P, u64 first, int lane)
             }
     }
     __syncwarp();
+}
+
+// A full sub-tile of 512 one-byte gaps at staged position b, decoded into
+// running sums from carry_in: lane l holds quad 32r + l in v[r] (the layout
+// the stores take).  The in-quad sums of the four rounds are packed into
+// 16-bit fields of one 64-bit word (each at most 4 * 255, a warp's total at
+// most 32 * 1020 < 2^16), so one warp scan serves all four rounds.
+__device__ __forceinline__ void zero_ctrl_delta(const uint8_t *D, uint32_t b, uint32_t carry_in,
+                                                uint32_t (&v)[kSubRounds][4])
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t *W = reinterpret_cast<const uint32_t *>(D);
+#pragma unroll
+    for (int r = 0; r < kSubRounds; r++) {
+        const uint32_t p = b + 128u * r + 4u * lane;
+        const uint32_t x = __funnelshift_r(W[p >> 2], W[(p >> 2) + 1], p << 3);
+        v[r][0] = __byte_perm(x, 0, 0x4440);
+        v[r][1] = v[r][0] + __byte_perm(x, 0, 0x4441);
+        v[r][2] = v[r][1] + __byte_perm(x, 0, 0x4442);
+        v[r][3] = v[r][2] + __byte_perm(x, 0, 0x4443);
+    }
+    const u64 pk = (u64)(v[0][3] | (v[1][3] << 16)) | ((u64)(v[2][3] | (v[3][3] << 16)) << 32);
+    u64 inc = pk;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const u64 t = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d)
+            inc += t;
+    }
+    const u64 ex = inc - pk;
+    const u64 tot = __shfl_sync(0xffffffffu, inc, 31);
+    const uint32_t t0 = (uint32_t)tot & 0xffffu, t1 = (uint32_t)(tot >> 16) & 0xffffu,
+                   t2 = (uint32_t)(tot >> 32) & 0xffffu;
+    uint32_t add[kSubRounds];
+    add[0] = carry_in + ((uint32_t)ex & 0xffffu);
+    add[1] = carry_in + t0 + ((uint32_t)(ex >> 16) & 0xffffu);
+    add[2] = carry_in + t0 + t1 + ((uint32_t)(ex >> 32) & 0xffffu);
+    add[3] = carry_in + t0 + t1 + t2 + (uint32_t)(ex >> 48);
+#pragma unroll
+    for (int r = 0; r < kSubRounds; r++)
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            v[r][j] += add[r];
+}
+
+// Stores a sub-tile's integers (lane l: quad 32r + l in v[r]).
+__device__ __forceinline__ void store_subtile(uint32_t *out, u64 q0, uint32_t nq, bool full,
+                                              bool aligned, u64 nquads, uint32_t last_nints,
+                                              const uint32_t (&v)[kSubRounds][4])
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t *op = out + 4 * (q0 + lane);
+#pragma unroll
+    for (int r = 0; r < kSubRounds; r++) {
+        const uint32_t lq = r * 32 + lane;
+        uint32_t *dst = op + 128 * r;
+        if (full && aligned) {
+            stg_stream128(dst, make_uint4(v[r][0], v[r][1], v[r][2], v[r][3]));
+        } else if (lq < nq) {
+            const uint32_t nints = q0 + lq == nquads - 1 ? last_nints : 4u;
+            dst[0] = v[r][0];
+            if (nints > 1)
+                dst[1] = v[r][1];
+            if (nints > 2)
+                dst[2] = v[r][2];
+            if (nints > 3)
+                dst[3] = v[r][3];
+        }
+    }
 }
 
 // Consumer warp `warp`: decodes sub-tile `warp` of every tile, alone.
@@ -864,11 +966,22 @@ __device__ void consume(const TiledArgs &a, Pipe &P, uint16_t *s_pos)
                 a.carries[sb] = t;
             continue;
         }
+        uint32_t v[kSubRounds][4];
+        if (kMode == kDelta && full && __all_sync(0xffffffffu, w == 0)) {
+            // Every integer one byte (Sec. 4): no positions to find, one
+            // packed scan for the running sums.
+            zero_ctrl_delta(D, base, carry_in, v);
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(&P.empty[s]);
+            store_subtile(a.out, q0, t.nq, full, a.out_aligned != 0, a.nquads, last_nints, v);
+            continue;
+        }
         subtile_positions(t, w, pos);
         __syncwarp();
         uint32_t *op = a.out + 4 * (q0 + lane);
         const uint32_t nq = t.nq;
-        uint32_t v[kSubRounds][4];
         subtile_gather(t, pos, v);
         // This warp no longer reads stage s.
         fence_proxy_async_smem();
@@ -950,7 +1063,7 @@ __global__ void __launch_bounds__(kDecBlock, 3) decode_tiled_kernel(TiledArgs a)
             mbar_init(&P.empty[s], kWarps);   // one arrival per consumer warp
         }
         fence_mbar_init();
-        s_etag = (ld_relaxed(&a.hdr->epoch) + 1) << 2;
+        s_etag = epoch_tag(a.hdr);
         s_flag = error_raised(a.hdr) ? 1u : 0u;
         // The sums pass takes ranges in claim order, so every range before
         // this one belongs to a CTA that is running or done.
@@ -1062,7 +1175,7 @@ static OffsetsArgs offsets_args(const uint8_t *in, u64 in_len, u64 n, void *ws, 
     o.spin_limit = spin_limit;
     o.in_aligned = (((uintptr_t)in) & 15u) == 0;
     o.prev = 0;
-    o.carries = reinterpret_cast<uint32_t *>(static_cast<char *>(ws) + L.carries);
+    o.carries = reinterpret_cast<u64 *>(static_cast<char *>(ws) + L.carries);
     return o;
 }
 
@@ -1106,7 +1219,7 @@ static TiledArgs tiled_args(const uint8_t *in, u64 n, uint32_t *out, uint32_t pr
     t.nsubs = (nquads + kSubQuads - 1) / kSubQuads;
     t.out = out;
     t.offs = reinterpret_cast<u64 *>(static_cast<char *>(ws) + L.offs);
-    t.carries = reinterpret_cast<uint32_t *>(static_cast<char *>(ws) + L.carries);
+    t.carries = reinterpret_cast<u64 *>(static_cast<char *>(ws) + L.carries);
     t.hdr = reinterpret_cast<WsHeader *>(ws);
     t.st = reinterpret_cast<TileStatus *>(static_cast<char *>(ws) + L.status);
     t.result = result;

@@ -26,6 +26,8 @@ constexpr int kSubQuads = 128;                     // sub-tile: the quads one wa
 
 // Status word low bits: what the tile has published.
 constexpr u64 kFlagNone = 0, kFlagAgg = 1, kFlagPrefix = 2;
+// Set in every tag, never in any other word the kernels store in a workspace.
+constexpr u64 kTagMark = 1ull << 63;
 
 // Error codes written to the workspace (same values as svb_status).
 constexpr u64 kErrTruncated = 2, kErrTimeout = 4;
@@ -33,8 +35,13 @@ constexpr u64 kErrTruncated = 2, kErrTimeout = 4;
 // One tile's published values.  Each scan has a tag word and two slots; a
 // reader that has seen a tag reads a slot that is written once per launch
 // and before the tag, so it never sees a half-updated record.  The tag is
-// ((epoch + 1) << 2) | flag: records left by earlier launches on the same
-// workspace never match, so the array is zeroed only once.
+// kTagMark | ((epoch + 1) << 2) | flag: records left by earlier launches on
+// the same workspace never match, so the array is zeroed only once.  Where
+// the records lie depends on n (ws_layout), so a call may find in a record's
+// place the words an earlier call of another size or kind left there:
+// sub-tile offsets and byte totals (below 2^48), carries and gap sums
+// (stored zero-extended, below 2^32) or older tags.  None of those has bit
+// 63 set together with this launch's epoch, so none reads as ready.
 struct __align__(64) TileStatus {
     u64 off_tag, off_agg, off_pre;   // data-stream byte offsets
     u64 val_tag, val_agg, val_pre;   // running sum of deltas (mod 2^32)
@@ -59,26 +66,26 @@ constexpr size_t kOffsetsOffset = 256;
 
 struct WsLayout {
     size_t offs;     // byte offset of the tile-offset array (u64 x tiles + 1)
-    size_t carries;  // byte offset of the per-tile carry array (u32 x tiles)
+    size_t carries;  // byte offset of the per-sub-tile carry array (u64 x subs, zero-extended)
     size_t status;   // byte offset of the TileStatus array
     size_t total;    // workspace bytes
 };
 
 // Layout for up to `subs` sub-tiles (offsets and carries, one per kSubQuads
 // quads) and `tiles` tile records (one per kMinQuadsPerTile quads or more).
-inline WsLayout ws_layout_for(u64 subs, u64 tiles)
+constexpr WsLayout ws_layout_for(u64 subs, u64 tiles)
 {
-    WsLayout l;
+    WsLayout l{};
     l.offs = kOffsetsOffset;
     l.carries = (l.offs + 8 * (subs + 1) + 63) & ~(size_t)63;
-    l.status = (l.carries + 4 * (subs ? subs : 1) + 63) & ~(size_t)63;
+    l.status = (l.carries + 8 * (subs ? subs : 1) + 63) & ~(size_t)63;
     l.total = l.status + sizeof(TileStatus) * (tiles ? tiles : 1);
     return l;
 }
 
-inline WsLayout ws_layout(u64 n)
+constexpr WsLayout ws_layout(u64 n)
 {
-    u64 nq = (n + 3) / 4;
+    const u64 nq = (n + 3) / 4;
     return ws_layout_for((nq + kSubQuads - 1) / kSubQuads,
                          (nq + kMinQuadsPerTile - 1) / kMinQuadsPerTile);
 }
@@ -112,6 +119,12 @@ __device__ __forceinline__ void st_release(u64 *p, u64 v)
 __device__ __forceinline__ void st_relaxed(u64 *p, u64 v)
 {
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Tag base of the running launch (see TileStatus): or a flag into it.
+__device__ __forceinline__ u64 epoch_tag(const WsHeader *h)
+{
+    return kTagMark | ((ld_relaxed(&h->epoch) + 1) << 2);
 }
 
 // Read-only, not-allocating-in-L1 loads of the compressed input.

@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(kThreads, 4) encode_kernel(EncodeArgs a)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
         s_tile = atomicAdd(&a.hdr->tile_counter, 1ull);
-        s_etag = (ld_relaxed(&a.hdr->epoch) + 1) << 2;
+        s_etag = epoch_tag(a.hdr);
         s_skip = (s_tile >= a.ntiles || error_raised(a.hdr)) ? 1u : 0u;
     }
     __syncthreads();

@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(kEtBlock, 3) encode_tiled_kernel(EncTiledArgs 
             mbar_init(&P.base_ready[b], 1);
         }
         fence_mbar_init();
-        s_etag = (ld_relaxed(&a.hdr->epoch) + 1) << 2;
+        s_etag = epoch_tag(a.hdr);
     }
     __syncthreads();
     if (warp == kWarps)

@@ -11,7 +11,7 @@
 // and a pinned result buffer; this one never does.
 //
 // The scratch holds the workspace of one decode of up to SVB_NOALLOC_MAX_N
-// integers (about 1.4 MB).  Every GPU that loads the library keeps it until
+// integers (about 1.5 MB).  Every GPU that loads the library keeps it until
 // the process exits.  All calls share it, so calls that overlap on the GPU
 // race: order them on one stream or serialize them on the host.
 #include <cuda_runtime.h>
@@ -27,13 +27,8 @@ namespace {
 using svb::u64;
 
 // Workspace bytes of one decode of SVB_NOALLOC_MAX_N integers, laid out as
-// svb::ws_layout lays it out (header, tile offsets, tile records).
-constexpr u64 kNoAllocQuads = ((u64)SVB_NOALLOC_MAX_N + 3) / 4;
-constexpr u64 kNoAllocSubs = (kNoAllocQuads + svb::kSubQuads - 1) / svb::kSubQuads;
-constexpr u64 kNoAllocTiles = (kNoAllocQuads + svb::kMinQuadsPerTile - 1) / svb::kMinQuadsPerTile;
-constexpr u64 kNoAllocCarries = (svb::kOffsetsOffset + 8 * (kNoAllocSubs + 1) + 63) & ~(u64)63;
-constexpr u64 kNoAllocStatus = (kNoAllocCarries + 4 * kNoAllocSubs + 63) & ~(u64)63;
-constexpr u64 kNoAllocBytes = kNoAllocStatus + sizeof(svb::TileStatus) * kNoAllocTiles;
+// svb::ws_layout lays it out (header, sub-tile offsets and carries, records).
+constexpr u64 kNoAllocBytes = svb::ws_layout(SVB_NOALLOC_MAX_N).total;
 
 // Zero-initialised when the module loads; never freed.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
@@ -56,8 +51,10 @@ extern "C" size_t svb_decode_noalloc(const uint8_t *in, size_t in_len, size_t n,
                                      uint32_t *out, uint32_t prev, int delta,
                                      svb_stream_t stream)
 {
-    if (n == 0)
+    if (n == 0) {
+        svb::set_last_error(SVB_OK);
         return 0;
+    }
     if (!in || !out)
         return noalloc_fail(SVB_EINVAL);
     if ((u64)n > (u64)SVB_NOALLOC_MAX_N)
@@ -85,8 +82,11 @@ extern "C" size_t svb_decode_noalloc(const uint8_t *in, size_t in_len, size_t n,
 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     svb::WsHeader *hdr = static_cast<svb::WsHeader *>(ws);
-    // The counters must start at zero; the epoch must not (it keeps tile
-    // records of earlier calls from being mistaken for this call's).
+    // The counters and the error word must start at zero.  The epoch is left
+    // as the last call left it: records of earlier calls carry older epochs
+    // in their tags, and whatever else an earlier call of another size left
+    // where this call's records lie never has a tag's mark bit (see
+    // svb::TileStatus), so nothing stale reads as published.
     if (cudaMemsetAsync(&hdr->tile_counter, 0, 2 * sizeof(u64), s) != cudaSuccess ||
         cudaMemsetAsync(&hdr->error, 0, 4 * sizeof(u64), s) != cudaSuccess)
         return noalloc_fail(SVB_ECUDA);

@@ -55,6 +55,37 @@ def test_noalloc_decode_matches_checked_decode_twice():
             assert torch.equal(got, x)
 
 
+def test_noalloc_at_its_limit_then_smaller():
+    """n at the limit fills the scratch exactly; the calls after it, of other
+    sizes, find their tile records where the large call left offsets and
+    carries.  Each must still equal svb_decode_checked and the values."""
+    n_max = svb.SVB_NOALLOC_MAX_N
+    cases = [
+        (W.skewed_lengths(33, n_max), False, 0),
+        (W.sorted_geometric(34, 1 << 18, 16.0, 3), True, 3),
+        (W.skewed_lengths(35, (1 << 18) + 1), False, 0),
+        (W.sorted_geometric(36, n_max, 16.0, 0), True, 0),
+        (W.skewed_lengths(37, 777_777), True, 99),
+    ]
+    for values, delta, prev in cases:
+        x = torch.from_numpy(values.view(np.int32)).to(DEV)
+        s = svb.encode(x, delta=delta, prev=prev)
+        k_new, k_old, got, want = _decode_both(s, values.size, delta, prev)
+        assert k_new == k_old == s.numel()
+        assert torch.equal(got, want)
+        assert torch.equal(got, x)
+
+
+def test_noalloc_empty_call_clears_the_last_error():
+    lib = svb.lib()
+    dummy = torch.zeros(16, dtype=torch.uint8, device=DEV)
+    k = lib.svb_decode_noalloc(dummy.data_ptr(), 16, svb.SVB_NOALLOC_MAX_N + 1,
+                               dummy.data_ptr(), 0, 0, _stream())
+    assert k == svb.ERROR and lib.svb_last_error() == svb.SVB_EINVAL
+    assert lib.svb_decode_noalloc(dummy.data_ptr(), 16, 0, dummy.data_ptr(), 0, 0, _stream()) == 0
+    assert lib.svb_last_error() == svb.SVB_OK
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch():
     lib = svb.lib()
     n = svb.SVB_NOALLOC_MAX_N + 1
