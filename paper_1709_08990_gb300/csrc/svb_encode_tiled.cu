@@ -285,13 +285,19 @@ __device__ void et_consume(const EncTiledArgs &a, EtPipe &P, EtChunks &C, u64 et
         const uint32_t tail = q0 + nq == a.nquads ? last_nints : 4u;
         auto before = [&]() { return q0 == 0 ? a.prev : __ldg(a.in + 4 * q0 - 1); };
         const bool sizing = P.pass[s] == 0;
-        if (fast && sizing)
-            subenc_load<true, decltype(before), true>(V, sq0, nq, tail, a.delta, before, nints, d,
-                                                      ctrl, cb);
-        else if (fast)
-            subenc_load<true>(V, sq0, nq, tail, a.delta, before, nints, d, ctrl, cb);
-        else
+        // A whole sub-tile of one-byte values (the common case of sorted
+        // lists with small gaps) needs no lengths: 512 data bytes, control 0.
+        bool small = false;
+        if (fast) {
+            subenc_values<true>(V, sq0, nq, tail, a.delta, before, nints, d);
+            small = subenc_all_small(d);
+            if (!small && sizing)
+                subenc_lengths<true>(nints, d, ctrl, cb);
+            else if (!small)
+                subenc_lengths<false>(nints, d, ctrl, cb);
+        } else {
             subenc_load<false>(V, sq0, nq, tail, a.delta, before, nints, d, ctrl, cb);
+        }
         // The control bytes use every staged value this warp loaded, so its
         // loads are complete; the fence orders them before the refill.
         fence_proxy_async_smem();
@@ -302,7 +308,7 @@ __device__ void et_consume(const EncTiledArgs &a, EtPipe &P, EtChunks &C, u64 et
         const u64 chunk = tile / kChunkTiles;
 
         if (pass == 0) {
-            const uint32_t t = subenc_bytes(cb);
+            const uint32_t t = small ? 4u * kSubQuads : subenc_bytes(cb);
             const int b = sized & 1;
             if (lane == 0) {
                 C.size[b][ti * kEtSubs + warp] = t;
@@ -329,7 +335,9 @@ __device__ void et_consume(const EncTiledArgs &a, EtPipe &P, EtChunks &C, u64 et
             break;
         }
         uint8_t *dst = data_base + C.base[b] + C.excl[b][ti * kEtSubs + warp];
-        if (fast)
+        if (small)
+            subenc_write_small(P.slice[warp], a.out + q0 + sq0, dst, d);
+        else if (fast)
             subenc_write<true>(P.slice[warp], a.out + q0 + sq0, dst, nvq, nints, ctrl, cb, d);
         else
             subenc_write<false>(P.slice[warp], a.out + q0 + sq0, dst, nvq, nints, ctrl, cb, d);

@@ -51,13 +51,11 @@ __device__ __forceinline__ void shl128(uint32_t &s0, uint32_t &s1, uint32_t &s2,
 // integers of the lane's quad (0 past the end), the coded values (0 past the
 // end), the control byte (left 0 with kSizeOnly, when only sizes are
 // needed) and the quad's data bytes.
-template <bool kFast, class Before, bool kSizeOnly = false>
-__device__ __forceinline__ void subenc_load(const uint32_t *V, uint32_t sq0, uint32_t nq,
-                                            uint32_t tail, bool delta, Before before,
-                                            uint32_t (&nints)[kEncRounds],
-                                            uint32_t (&d)[kEncRounds][4],
-                                            uint32_t (&ctrl)[kEncRounds],
-                                            uint32_t (&cb)[kEncRounds])
+template <bool kFast, class Before>
+__device__ __forceinline__ void subenc_values(const uint32_t *V, uint32_t sq0, uint32_t nq,
+                                              uint32_t tail, bool delta, Before before,
+                                              uint32_t (&nints)[kEncRounds],
+                                              uint32_t (&d)[kEncRounds][4])
 {
     const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -93,6 +91,15 @@ __device__ __forceinline__ void subenc_load(const uint32_t *V, uint32_t sq0, uin
             d[r][0] = nints[r] > 0 ? x0 - pv : 0u;
         }
     }
+}
+
+// Control bytes and byte counts of the coded values d (see subenc_load).
+template <bool kSizeOnly = false>
+__device__ __forceinline__ void subenc_lengths(const uint32_t (&nints)[kEncRounds],
+                                               const uint32_t (&d)[kEncRounds][4],
+                                               uint32_t (&ctrl)[kEncRounds],
+                                               uint32_t (&cb)[kEncRounds])
+{
     // Fields past the end are 0 and add nothing.
 #pragma unroll
     for (int r = 0; r < kEncRounds; r++) {
@@ -109,6 +116,29 @@ __device__ __forceinline__ void subenc_load(const uint32_t *V, uint32_t sq0, uin
     }
 }
 
+template <bool kFast, class Before, bool kSizeOnly = false>
+__device__ __forceinline__ void subenc_load(const uint32_t *V, uint32_t sq0, uint32_t nq,
+                                            uint32_t tail, bool delta, Before before,
+                                            uint32_t (&nints)[kEncRounds],
+                                            uint32_t (&d)[kEncRounds][4],
+                                            uint32_t (&ctrl)[kEncRounds],
+                                            uint32_t (&cb)[kEncRounds])
+{
+    subenc_values<kFast>(V, sq0, nq, tail, delta, before, nints, d);
+    subenc_lengths<kSizeOnly>(nints, d, ctrl, cb);
+}
+
+// Whether every coded value of the warp's sub-tile takes one byte (Sec. 3:
+// below 2^8); fields past the end are 0.
+__device__ __forceinline__ bool subenc_all_small(const uint32_t (&d)[kEncRounds][4])
+{
+    uint32_t o = 0;
+#pragma unroll
+    for (int r = 0; r < kEncRounds; r++)
+        o |= d[r][0] | d[r][1] | d[r][2] | d[r][3];
+    return __all_sync(0xffffffffu, o < 256u);
+}
+
 // Data bytes of the sub-tile (all lanes), from subenc_load's byte counts.
 __device__ __forceinline__ uint32_t subenc_bytes(const uint32_t (&cb)[kEncRounds])
 {
@@ -120,6 +150,34 @@ __device__ __forceinline__ uint32_t subenc_bytes(const uint32_t (&cb)[kEncRounds
     for (int k = 16; k >= 1; k >>= 1)
         t += __shfl_xor_sync(0xffffffffu, t, k);
     return t;
+}
+
+// Stores the warp's data bytes [h, h + run) of slice (phased like dst) to
+// dst: 16-byte streaming stores, ragged ends byte by byte.
+__device__ __forceinline__ void subenc_flush(uint32_t *slice, uint8_t *dst, uint32_t h, uint32_t run)
+{
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    const uint8_t *sb = reinterpret_cast<const uint8_t *>(slice);
+    uint8_t *adst = dst - h;
+    const uint32_t end = h + run;
+    const uint32_t c0 = (h + 15) >> 4, c1 = end >> 4;   // whole 16-byte chunks [c0, c1)
+#pragma unroll
+    for (int k = 0; k < (kEncSliceWords * 4 / 16 + 31) / 32; k++) {
+        const uint32_t c = c0 + lane + 32 * k;
+        if (c < c1)
+            stg_stream128(adst + 16 * c, *reinterpret_cast<const uint4 *>(sb + 16 * c));
+    }
+    if (lane < 16) {
+        const uint32_t i = h + lane;
+        if (i < min(16 * c0, end))
+            adst[i] = sb[i];
+    } else {
+        const uint32_t i = 16 * c1 + (lane - 16);
+        if (c1 >= c0 && i < end)
+            adst[i] = sb[i];
+    }
+    __syncwarp();
 }
 
 // Writes the sub-tile's nvq quads: control byte of quad i to ctrl_dst[i],
@@ -189,27 +247,41 @@ __device__ __forceinline__ void subenc_write(uint32_t *slice, uint8_t *ctrl_dst,
         fword = fin ? (nfull ? last : w0) : fword;
     }
     slice[fidx != kNone ? fidx : kSpare] = fword;
-    __syncwarp();
-    const uint8_t *sb = reinterpret_cast<const uint8_t *>(slice);
-    uint8_t *adst = dst - h;
-    const uint32_t end = h + run;
-    const uint32_t c0 = (h + 15) >> 4, c1 = end >> 4;   // whole 16-byte chunks [c0, c1)
-#pragma unroll
-    for (int k = 0; k < (kEncSliceWords * 4 / 16 + 31) / 32; k++) {
-        const uint32_t c = c0 + lane + 32 * k;
-        if (c < c1)
-            stg_stream128(adst + 16 * c, *reinterpret_cast<const uint4 *>(sb + 16 * c));
-    }
-    if (lane < 16) {
-        const uint32_t i = h + lane;
-        if (i < min(16 * c0, end))
-            adst[i] = sb[i];
+    subenc_flush(slice, dst, h, run);
+}
+
+// A full sub-tile (128 quads) whose 512 coded values all take one byte:
+// every control byte is 0 and the data bytes are the values' low bytes in
+// order (Sec. 4), so no lengths, scan or shifts per value are needed.  Each
+// lane packs its quad's four bytes into a word, shifted to the destination's
+// phase with the previous quad's word.
+__device__ __forceinline__ void subenc_write_small(uint32_t *slice, uint8_t *ctrl_dst, uint8_t *dst,
+                                                   const uint32_t (&d)[kEncRounds][4])
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t h = (uint32_t)((uintptr_t)dst & 15u);
+    const uint32_t hw = h >> 2, sh = 8 * (h & 3);
+    if (((uintptr_t)ctrl_dst & 3u) == 0) {
+        reinterpret_cast<uint32_t *>(ctrl_dst)[lane] = 0u;
     } else {
-        const uint32_t i = 16 * c1 + (lane - 16);
-        if (c1 >= c0 && i < end)
-            adst[i] = sb[i];
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            ctrl_dst[4 * lane + j] = 0;
     }
-    __syncwarp();
+    uint32_t carry = 0;  // the word of the quad before this round's first
+#pragma unroll
+    for (int r = 0; r < kEncRounds; r++) {
+        const uint32_t w = __byte_perm(__byte_perm(d[r][0], d[r][1], 0x0040),
+                                       __byte_perm(d[r][2], d[r][3], 0x0040), 0x5410);
+        uint32_t pw = __shfl_up_sync(0xffffffffu, w, 1);
+        if (lane == 0)
+            pw = carry;
+        carry = __shfl_sync(0xffffffffu, w, 31);
+        slice[hw + 32 * r + lane] = sh ? __funnelshift_l(pw, w, sh) : w;
+    }
+    if (lane == 31 && sh)
+        slice[hw + kSubQuads] = carry >> (32 - sh);
+    subenc_flush(slice, dst, h, 4u * kSubQuads);
 }
 
 }  // namespace svb
