@@ -32,6 +32,9 @@ LIB = os.path.join(HERE, "libsvb_ref.so")
 VSRC = os.path.join(HERE, "vbyte_ref.c")
 VLIB = os.path.join(HERE, "libvbyte_ref.so")
 
+PSRC = os.path.join(HERE, "par_ref.c")
+PLIB = os.path.join(HERE, "libpar_ref.so")
+
 ERROR = (1 << 64) - 1  # SVB_REF_ERROR, (size_t)-1
 
 
@@ -46,6 +49,11 @@ def build() -> None:
         if os.path.exists(lib) and os.path.getmtime(lib) >= os.path.getmtime(src):
             continue
         subprocess.run(build_cmd(src, lib), check=True)
+    # The multi-threaded timing harness links the oracle's own source.
+    if not (os.path.exists(PLIB) and os.path.getmtime(PLIB) >= max(
+            os.path.getmtime(PSRC), os.path.getmtime(SRC))):
+        subprocess.run(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread", "-o", PLIB,
+                        PSRC, SRC], check=True)
 
 
 class Codec:
@@ -190,8 +198,40 @@ class VByte:
         return out[:n], k
 
 
+class Parallel:
+    """The oracle's decoder run on several host threads (``par_ref.c``): a
+    timing harness whose every byte count and integer comes from the oracle."""
+
+    def __init__(self, path: str = PLIB):
+        L = ctypes.CDLL(path)
+        sz, vp = ctypes.c_size_t, ctypes.c_void_p
+        L.svb_par_decode.argtypes = [vp, sz, sz, vp, ctypes.c_uint32, ctypes.c_int, ctypes.c_int]
+        L.svb_par_decode.restype = sz
+        self.lib = L
+
+    def decode(self, stream, n: int, prev: int = 0, delta: bool = False, threads: int = 1,
+               out=None):
+        """(decoded uint32 array, bytes consumed or ERROR)."""
+        stream = np.ascontiguousarray(stream, dtype=np.uint8)
+        buf = stream if stream.size else np.zeros(1, dtype=np.uint8)
+        if out is None:
+            out = np.zeros(max(1, n), dtype=np.uint32)
+        k = self.lib.svb_par_decode(buf.ctypes.data, stream.size, n, out.ctypes.data,
+                                    prev & 0xFFFFFFFF, int(delta), threads)
+        return out[:n], k
+
+
 _default: Codec | None = None
 _vbyte: VByte | None = None
+_par: Parallel | None = None
+
+
+def parallel() -> Parallel:
+    global _par
+    if _par is None:
+        build()
+        _par = Parallel(PLIB)
+    return _par
 
 
 def vbyte() -> VByte:

@@ -155,3 +155,25 @@ def test_planted_mistake_is_caught(name, tmp_path):
     failures = {k: v for k, v in pins.run_all(oracle.Codec(str(mlib))).items() if v}
     brute = _run_brute(str(msrc), 6)
     assert failures or brute.returncode != 0, f"mutant {name} passed every pin"
+
+
+def test_parallel_harness_equals_the_oracle(ref):
+    """The multi-threaded timing harness returns the oracle's own decode, bit
+    for bit, for every thread count, tail, start value and both codings, and
+    reports truncation like it."""
+    par = oracle.parallel()
+    rng = np.random.default_rng(51)
+    for n in [1, 2, 3, 4, 5, 7, 8, 9, 31, 32, 33, 1000, 4097, 100_003]:
+        L = rng.integers(1, 5, n)
+        x = (rng.integers(0, 1 << 32, n, dtype=np.uint64) >> (8 * (4 - L)).astype(np.uint64)).astype(np.uint32)
+        for delta in (False, True):
+            prev = int(rng.integers(0, 1 << 32)) if delta else 0
+            s = ref.encode(x, prev=prev, delta=delta)
+            want, wk = ref.decode(s, n, prev=prev, delta=delta)
+            for threads in (1, 2, 3, 7, 16, 64):
+                got, k = par.decode(s, n, prev=prev, delta=delta, threads=threads)
+                assert k == wk == s.size
+                assert np.array_equal(got, want)
+            cut = s.size - 1
+            _, k = par.decode(s[:cut], n, prev=prev, delta=delta, threads=4)
+            assert k == oracle.ERROR
