@@ -678,7 +678,9 @@ serve_levels = True
 
 def time_lists(svb, W, dev, peaks, count: int):
     """Batched delta decode/encode of the lists_100k workload (one persistent
-    launch, replayed from a CUDA graph) against one launch per list."""
+    launch, replayed from a CUDA graph) against one call per list: from a
+    Python loop, from the library's host loop, and that loop replayed from a
+    CUDA graph."""
     import torch
     from paper_1709_08990_gb300 import autotune
     from paper_1709_08990_gb300.batch import ListPool
@@ -716,6 +718,47 @@ def time_lists(svb, W, dev, peaks, count: int):
     b.record(stream)
     torch.cuda.synchronize()
     ms_enc_per_list = a.elapsed_time(b)
+    # One call per list issued by the library's own host loop (no interpreter
+    # between launches), eager and captured once into a CUDA graph.
+    ews = pool.each_workspace()
+    d_res = torch.zeros(2 * pool.k, dtype=torch.int64, device=dev)
+    d_out3 = torch.zeros_like(d_out)
+    pool.decode_each(d_out3, ews, d_res)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    a.record(stream)
+    pool.decode_each(d_out3, ews, d_res)
+    b.record(stream)
+    host_ms_each = (time.perf_counter() - t0) * 1e3
+    torch.cuda.synchronize()
+    ms_each = a.elapsed_time(b)
+    ok_each = bool(torch.equal(d_out3, d_vals)) and int(d_res.view(-1, 2)[:, 1].max()) == 0
+    a.record(stream)
+    pool.encode_each(d_enc, ews, d_res)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_enc_each = a.elapsed_time(b)
+    ok_enc_each = bool(torch.equal(d_enc, pool.pool))
+    each_graph = {}
+    try:
+        gd = pool.graph(lambda: pool.decode_each(d_out3, ews, d_res))
+        ms_each_graph = _time(lambda: gd.replay(), 3, stream)
+        ok_g = bool(torch.equal(d_out3, d_vals))
+        del gd
+        ge = pool.graph(lambda: pool.encode_each(d_enc, ews, d_res))
+        ms_enc_each_graph = _time(lambda: ge.replay(), 3, stream)
+        ok_ge = bool(torch.equal(d_enc, pool.pool))
+        del ge
+        each_graph = {
+            "decode_per_list_graph": {"gints_per_s": total / ms_each_graph / 1e6,
+                                      "ms": ms_each_graph, "verified": ok_g},
+            "decode_speedup_vs_per_list_graph": ms_each_graph / ms_graph,
+            "encode_per_list_graph": {"gints_per_s": total / ms_enc_each_graph / 1e6,
+                                      "ms": ms_enc_each_graph, "verified": ok_ge},
+            "encode_speedup_vs_per_list_graph": ms_enc_each_graph / ms_benc}
+    except RuntimeError as e:  # capture of ~2 launches per list may not fit
+        each_graph = {"per_list_graph_error": str(e)[:200]}
+    del ews, d_res, d_out3
     alg = pool.pool_bytes + 4 * total
     hb = peaks["hbm_gbs"]
     serve = time_serve(pool, W) if serve_levels else None
@@ -729,6 +772,13 @@ def time_lists(svb, W, dev, peaks, count: int):
            "decode_batched_launch": {"gints_per_s": total / ms_batch / 1e6, "ms": ms_batch},
            "decode_per_list": {"gints_per_s": total / ms_per_list / 1e6, "ms": ms_per_list},
            "decode_speedup_vs_per_list": ms_per_list / ms_graph,
+           "decode_per_list_c_loop": {"gints_per_s": total / ms_each / 1e6, "ms": ms_each,
+                                      "host_issue_ms": host_ms_each, "verified": ok_each},
+           "decode_speedup_vs_per_list_c_loop": ms_each / ms_graph,
+           "encode_per_list_c_loop": {"gints_per_s": total / ms_enc_each / 1e6,
+                                      "ms": ms_enc_each, "verified": ok_enc_each},
+           "encode_speedup_vs_per_list_c_loop": ms_enc_each / ms_benc,
+           **each_graph,
            "encode_batched": {"gints_per_s": total / ms_benc / 1e6, "ms": ms_benc,
                               "frac": alg / (ms_benc / 1e3) / 1e9 / hb},
            "encode_per_list": {"gints_per_s": total / ms_enc_per_list / 1e6,

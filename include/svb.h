@@ -244,6 +244,62 @@ int svb_batch_encode(const void *d_plan, const svb_list *d_lists, const uint32_t
                      uint8_t *out_base, int delta, uint64_t *d_sizes, svb_result *d_result,
                      void *ws, size_t ws_bytes, int grid, svb_stream_t stream);
 
+/* The same lists coded one list at a time: each list gets its own
+ * single-stream call (svb_decode_async / svb_encode_async, the kernels and
+ * launches a caller of those gets), all issued from one host loop on
+ * `stream`, in table order, sharing one workspace sized for the longest list
+ * (svb_workspace_size of it, zeroed once).  h_lists is the HOST copy of the
+ * list table, laid out as for svb_batch_decode / svb_batch_encode; the
+ * result of list j goes to d_results[j] (DEVICE, num_lists entries).  This
+ * is the baseline the batched launch is measured against (Sec. 5 decodes
+ * posting lists one at a time).  Returns SVB_OK, or the status of the first
+ * call that could not be enqueued (the lists after it are not coded). */
+int svb_decode_each(const svb_list *h_lists, size_t num_lists, const uint8_t *in_base,
+                    uint32_t *out_base, int delta, svb_result *d_results, void *ws,
+                    size_t ws_bytes, svb_stream_t stream);
+int svb_encode_each(const svb_list *h_lists, size_t num_lists, const uint32_t *in_base,
+                    uint8_t *out_base, int delta, svb_result *d_results, void *ws,
+                    size_t ws_bytes, svb_stream_t stream);
+
+/* ---- one array split across several parties ---------------------------- */
+
+/* The per-shard steps of coding one array whose integers are split across P
+ * parties (GPUs, or shards on one GPU) at control-byte boundaries: shard p
+ * holds integers [4 q_p, min(4 q_{p+1}, n)), i.e. control bytes [q_p,
+ * q_{p+1}).  Because the control bytes are kept apart from the data (Sec. 4),
+ * one exchange of P byte totals places every shard's data:
+ *   decode  (1) svb_control_range_bytes gives the data bytes each shard's
+ *           control bytes cover; (2) their exclusive prefix, exchanged, is
+ *           each shard's data offset; the shard's control bytes followed by
+ *           its data bytes are a stream of its own integers; (3) for
+ *           differential streams, svb_gap_sum of each shard's stream, and
+ *           prev plus the exclusive prefix of those sums, exchanged, is each
+ *           shard's start value (Sec. 2's prefix sum across shards); (4) each
+ *           shard decodes its stream (svb_decode_async) from that start.
+ *   encode  (1) svb_size_report_async of each shard's integers (for
+ *           differential coding from the integer before the shard) less its
+ *           control bytes; (2) the exclusive prefix of those, exchanged; (3)
+ *           each shard encodes its integers (svb_encode_async); the shards'
+ *           control bytes in order, then their data bytes in order, are the
+ *           array's stream.
+ *
+ * svb_control_range_bytes: data bytes that control bytes [q0, q1) of a
+ * stream of n integers cover (4 + the sum of codes each; the pad fields of
+ * the stream's last control byte count nothing), into *d_bytes (DEVICE) on
+ * stream.  Reads in[q0 .. q1) only.  SVB_EINVAL when q0 > q1 or q1 >
+ * ceil(n/4).
+ *
+ * svb_gap_sum: sum mod 2^32 of the n coded values of the stream in[0..in_len)
+ * (for a differential stream, the sum of its gaps) into d_out[0], the status
+ * into d_out[1] and the stream's bytes into d_out[2] (DEVICE, three
+ * uint64_t), on stream, with a caller workspace as for svb_decode_async.
+ * Returns SVB_ETRUNCATED at once when in_len < ceil(n/4); a stream cut short
+ * inside its data is reported in d_out[1]. */
+int svb_control_range_bytes(const uint8_t *in, size_t n, size_t q0, size_t q1,
+                            uint64_t *d_bytes, svb_stream_t stream);
+int svb_gap_sum(const uint8_t *in, size_t in_len, size_t n, uint64_t *d_out, void *ws,
+                size_t ws_bytes, svb_stream_t stream);
+
 /* ---- decoding without allocation --------------------------------------- */
 
 /* Largest n that svb_decode_noalloc accepts. */

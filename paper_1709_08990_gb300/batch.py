@@ -146,6 +146,22 @@ class ListPool:
         torch.cuda.synchronize(self.device)
         return g
 
+    # -- one call per list, from the library's own host loop -------------------
+    def each_workspace(self) -> Workspace:
+        return Workspace(svb.svb_workspace_size(int(self.lengths.max())), self.device)
+
+    def decode_each(self, d_out: torch.Tensor, ws: Workspace, d_results: torch.Tensor):
+        st = svb.svb_decode_each(self.dec_table, self.k, self.pool, d_out, int(self.delta),
+                                 d_results, ws.buf, ws.nbytes)
+        if st != 0:
+            raise svb.SvbError(st, "svb_decode_each")
+
+    def encode_each(self, d_out: torch.Tensor, ws: Workspace, d_results: torch.Tensor):
+        st = svb.svb_encode_each(self.enc_table, self.k, self.d_values, d_out, int(self.delta),
+                                 d_results, ws.buf, ws.nbytes)
+        if st != 0:
+            raise svb.SvbError(st, "svb_encode_each")
+
     # -- one launch per list (the comparison the batched path is measured against)
     def decode_per_list(self, d_out: torch.Tensor, lists=None, ws: Workspace | None = None):
         lib = svb.lib()

@@ -558,6 +558,62 @@ int svb_decode_async(const uint8_t *in, size_t in_len, size_t n, uint32_t *out,
                            reinterpret_cast<svb::DeviceResult *>(d_result), s);
 }
 
+int svb_gap_sum(const uint8_t *in, size_t in_len, size_t n, uint64_t *d_out, void *ws,
+                size_t ws_bytes, svb_stream_t stream)
+{
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (!d_out)
+        return SVB_EINVAL;
+    if (n == 0)
+        return cudaMemsetAsync(d_out, 0, 3 * sizeof(uint64_t), s) == cudaSuccess ? SVB_OK
+                                                                               : SVB_ECUDA;
+    if (!in || !ws || ws_bytes < svb_workspace_size(n))
+        return SVB_EINVAL;
+    if (in_len < ((u64)n + 3) / 4)
+        return SVB_ETRUNCATED;
+    return svb::launch_gap_sum(in, in_len, n, ws, reinterpret_cast<u64 *>(d_out), s,
+                               spin_limit()) == 0
+               ? SVB_OK
+               : SVB_ECUDA;
+}
+
+int svb_decode_each(const svb_list *h_lists, size_t num_lists, const uint8_t *in_base,
+                    uint32_t *out_base, int delta, svb_result *d_results, void *ws,
+                    size_t ws_bytes, svb_stream_t stream)
+{
+    if (num_lists == 0)
+        return SVB_OK;
+    if (!h_lists || !in_base || !out_base || !d_results)
+        return SVB_EINVAL;
+    for (size_t j = 0; j < num_lists; j++) {
+        const svb_list &l = h_lists[j];
+        const int st = svb_decode_async(in_base + l.in_off, (size_t)l.in_len, l.n,
+                                        out_base + l.out_off, l.prev, delta, d_results + j, ws,
+                                        ws_bytes, stream);
+        if (st != SVB_OK)
+            return st;
+    }
+    return SVB_OK;
+}
+
+int svb_encode_each(const svb_list *h_lists, size_t num_lists, const uint32_t *in_base,
+                    uint8_t *out_base, int delta, svb_result *d_results, void *ws,
+                    size_t ws_bytes, svb_stream_t stream)
+{
+    if (num_lists == 0)
+        return SVB_OK;
+    if (!h_lists || !in_base || !out_base || !d_results)
+        return SVB_EINVAL;
+    for (size_t j = 0; j < num_lists; j++) {
+        const svb_list &l = h_lists[j];
+        const int st = svb_encode_async(in_base + l.in_off, l.n, out_base + l.out_off, l.prev,
+                                        delta, d_results + j, ws, ws_bytes, stream);
+        if (st != SVB_OK)
+            return st;
+    }
+    return SVB_OK;
+}
+
 size_t svb_batch_plan_bytes(size_t num_lists)
 {
     return svb::batch_plan_bytes(num_lists);

@@ -1206,6 +1206,48 @@ static u64 launch_delta_prep(const uint8_t *in, u64 in_len, u64 n, uint32_t prev
     return cudaGetLastError() == cudaSuccess ? o.per_cta * kOffGroupSubs : 0;
 }
 
+// After delta_prep_kernel run from 0: the stream's sum of coded values
+// (mod 2^32) is the sum of its ranges' gap totals.  One warp writes out[0] =
+// that sum, out[1] = the status, out[2] = the stream's bytes, and readies the
+// workspace for the next launch as finish_launch does.
+__global__ void gap_total_kernel(WsHeader *hdr, const TileStatus *st, u64 nranges,
+                                 unsigned long long *out)
+{
+    uint32_t sum = 0;
+    for (u64 i = threadIdx.x; i < nranges; i += 32)
+        sum += (uint32_t)ld_relaxed(&st[i].val_agg);
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1)
+        sum += __shfl_xor_sync(0xffffffffu, sum, d);
+    if (threadIdx.x == 0) {
+        const u64 err = ld_relaxed(&hdr->error), total = ld_relaxed(&hdr->total);
+        out[0] = err ? 0ull : sum;
+        out[1] = err;
+        out[2] = err ? ~0ull : total;
+        st_relaxed(&hdr->error, 0);
+        st_relaxed(&hdr->total, 0);
+        st_relaxed(&hdr->tile_counter, 0);
+        st_relaxed(&hdr->done_counter, 0);
+        st_relaxed(&hdr->a_counter, 0);
+        st_relaxed(&hdr->a_done, 0);
+        st_relaxed(&hdr->epoch, ld_relaxed(&hdr->epoch) + 1);
+    }
+}
+
+int launch_gap_sum(const uint8_t *in, u64 in_len, u64 n, void *ws, u64 *d_out,
+                   cudaStream_t stream, u64 spin_limit)
+{
+    u64 grid = 0;
+    OffsetsArgs o = offsets_args(in, in_len, n, ws, spin_limit, prep_grid(), &grid);
+    o.prev = 0;
+    prof_begin("delta_prep_kernel", stream);
+    delta_prep_kernel<<<(unsigned)grid, kThreads, 0, stream>>>(o);
+    prof_end(stream);
+    gap_total_kernel<<<1, 32, 0, stream>>>(o.hdr, o.st, grid,
+                                           reinterpret_cast<unsigned long long *>(d_out));
+    return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
 static TiledArgs tiled_args(const uint8_t *in, u64 n, uint32_t *out, uint32_t prev, void *ws,
                             DeviceResult *result, u64 spin_limit)
 {

@@ -25,6 +25,12 @@ int launch_decode_tiled(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, uin
                         bool delta, void *ws, DeviceResult *result, cudaStream_t stream,
                         u64 spin_limit, bool sums_pass = false);
 
+// Sum of a stream's n coded values (mod 2^32) into d_out[0], its status into
+// d_out[1] and its bytes into d_out[2] (the differential offsets pass run from
+// 0, then one warp totals the ranges).
+int launch_gap_sum(const uint8_t *in, u64 in_len, u64 n, void *ws, u64 *d_out,
+                   cudaStream_t stream, u64 spin_limit);
+
 // Its two halves, for decoding in pieces: the offsets pass (sub-tile offsets,
 // stream size and truncation verdict into the workspace), then plain decodes
 // of tile ranges [tile0, tile1) of decode_tile_ints() integers each tile.

@@ -75,6 +75,10 @@ def lib() -> ctypes.CDLL:
             "svb_batch_workspace_size": ([], sz),
             "svb_batch_decode": ([vp, vp, vp, vp, i32, vp, vp, sz, i32, vp], i32),
             "svb_batch_encode": ([vp, vp, vp, vp, i32, vp, vp, vp, sz, i32, vp], i32),
+            "svb_decode_each": ([vp, sz, vp, vp, i32, vp, vp, sz, vp], i32),
+            "svb_control_range_bytes": ([vp, sz, sz, sz, vp, vp], i32),
+            "svb_gap_sum": ([vp, sz, sz, vp, vp, sz, vp], i32),
+            "svb_encode_each": ([vp, sz, vp, vp, i32, vp, vp, sz, vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -235,6 +239,26 @@ def svb_batch_encode(d_plan, d_lists, in_base, out_base, delta, d_sizes, d_resul
     return lib().svb_batch_encode(_p(d_plan), _p(d_lists), _p(in_base), _p(out_base), int(delta),
                                   _p(d_sizes), _p(d_result), _p(ws), ws_bytes, grid,
                                   _stream(stream))
+
+
+def svb_decode_each(h_lists, num_lists, in_base, out_base, delta, d_results, ws, ws_bytes,
+                    stream=None) -> int:
+    return lib().svb_decode_each(_p(h_lists), num_lists, _p(in_base), _p(out_base), int(delta),
+                                 _p(d_results), _p(ws), ws_bytes, _stream(stream))
+
+
+def svb_encode_each(h_lists, num_lists, in_base, out_base, delta, d_results, ws, ws_bytes,
+                    stream=None) -> int:
+    return lib().svb_encode_each(_p(h_lists), num_lists, _p(in_base), _p(out_base), int(delta),
+                                 _p(d_results), _p(ws), ws_bytes, _stream(stream))
+
+
+def svb_control_range_bytes(in_, n, q0, q1, d_bytes, stream=None) -> int:
+    return lib().svb_control_range_bytes(_p(in_), n, q0, q1, _p(d_bytes), _stream(stream))
+
+
+def svb_gap_sum(in_, in_len, n, d_out, ws, ws_bytes, stream=None) -> int:
+    return lib().svb_gap_sum(_p(in_), in_len, n, _p(d_out), _p(ws), ws_bytes, _stream(stream))
 
 
 def svb_profile_begin() -> int:

@@ -223,3 +223,34 @@ def test_list_pool_graph_and_per_list_agree():
     pool.encode_per_list(enc)
     torch.cuda.synchronize()
     assert torch.equal(enc, pool.pool)
+
+
+@pytest.mark.parametrize("delta", [False, True])
+def test_one_call_per_list_matches_the_oracle(delta):
+    """svb_decode_each / svb_encode_each (one single-stream call per list from
+    the library's host loop, one shared workspace) give every list's oracle
+    values and stream, with each list's result in its own slot."""
+    lengths = [0, 1, 3, 4, 5, 511, 513, 4095, 4097, 12_289, 50_001, 7]
+    b = Batch(lengths, delta, seed=41, prevs=[(97 * j) % 1000 for j in range(len(lengths))],
+              gap_bytes=5)
+    k = len(lengths)
+    wsb = svb.svb_workspace_size(int(max(lengths)))
+    ws = torch.empty(wsb, dtype=torch.uint8, device=DEV)
+    assert svb.svb_workspace_init(ws, wsb) == 0
+    res = torch.zeros(2 * k, dtype=torch.int64, device=DEV)
+    out = torch.full((max(1, b.total_ints),), -1, dtype=torch.int32, device=DEV)
+    assert svb.svb_decode_each(b.dec_lists, k, to_dev(b.pool), out, int(delta), res, ws, wsb) == 0
+    r = res.view(-1, 2).cpu().numpy()
+    assert np.array_equal(r[:, 1], np.zeros(k))
+    assert np.array_equal(r[:, 0], np.array([s.size for s in b.streams]))
+    assert np.array_equal(out.cpu().numpy().view(np.uint32)[: b.total_ints], b.all_values)
+    cap = opos_enc(k, b.lengths)
+    enc = torch.zeros(max(1, cap), dtype=torch.uint8, device=DEV)
+    assert svb.svb_encode_each(b.enc_lists, k, to_dev(b.all_values), enc, int(delta), res, ws,
+                               wsb) == 0
+    r = res.view(-1, 2).cpu().numpy()
+    e = enc.cpu().numpy()
+    for j in range(k):
+        off = int(b.enc_lists[j]["out_off"])
+        assert r[j, 1] == 0 and r[j, 0] == b.streams[j].size
+        assert np.array_equal(e[off: off + b.streams[j].size], b.streams[j])
