@@ -649,28 +649,38 @@ def time_append(svb, W, dev, n0: int = 1 << 26, k: int = 1 << 20):
             "note": "append timed on the host around the synchronous call"}
 
 
-def time_serve(pool, W, seconds: float = 1.0):
-    """Serving loop over the pool: peak throughput with every request queued
-    at once, then Poisson arrivals at 10%..90% of that peak."""
+def time_serve(pool, W, seconds: float = 1.0, peak_requests: int = 400_000,
+               level_cap: int = 200_000):
+    """Serving loop over the pool: peak throughput with peak_requests queued
+    at once (tens of batches), then Poisson arrivals offering 10%..90% of that
+    peak in integers per second: each level's requests are drawn first and
+    their arrival rate set from their own mean size, for about `seconds` or
+    level_cap requests, whichever is fewer (the fresh lists of a level's
+    encode requests live in host memory)."""
     from paper_1709_08990_gb300.serve import Server, summarize
     srv = Server(pool, budget=16 << 30)
-    warm = W.serve_requests(pool.lengths, 2000, None, seed=105)
+    warm = W.serve_requests(pool.lengths, 20_000, None, seed=105)
     srv.run(warm)
-    req = W.serve_requests(pool.lengths, 30000, None, seed=5)
+    req = W.serve_requests(pool.lengths, peak_requests, None, seed=5)
     peak = summarize(req, srv.run(req))
-    mean_n = float(req.n.mean())
-    peak_rate = peak["gints_per_s"] * 1e9 / mean_n
+    del req
+    peak_ints = peak["gints_per_s"] * 1e9
+    mean_n = peak["ints"] / peak["requests"]
     levels = []
     for i, f in enumerate([0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9]):
-        rate = f * peak_rate
-        count = max(500, int(rate * seconds))
-        r = W.serve_requests(pool.lengths, count, rate, seed=5 + 1000 * (i + 1))
+        count = min(level_cap, max(2000, int(seconds * f * peak_ints / mean_n)))
+        r = W.serve_requests(pool.lengths, count, 1.0, seed=5 + 1000 * (i + 1))
+        rate = f * peak_ints / float(r.n.mean())    # requests/s offering f x peak ints/s
+        r.arrival = r.arrival / rate
         s = summarize(r, srv.run(r))
         s["load"] = f
         s["offered_gints_per_s"] = rate * float(r.n.mean()) / 1e9
+        s["offered_frac_of_peak"] = s["offered_gints_per_s"] * 1e9 / peak_ints
+        s["achieved_frac_of_offered"] = s["gints_per_s"] / s["offered_gints_per_s"]
+        s["window_s"] = float(r.arrival[-1])
         levels.append(s)
-    return {"budget_bytes": 16 << 30, "slots": len(srv.slots), "mean_request_ints": mean_n,
-            "peak": peak, "levels": levels}
+    return {"budget_bytes": 16 << 30, "slots": len(srv.slots), "max_batch": srv.max_batch,
+            "mean_request_ints": mean_n, "peak": peak, "levels": levels}
 
 
 serve_levels = True

@@ -34,16 +34,23 @@ def _up(x, a=_ALIGN):
     return (x + a - 1) // a * a
 
 
-def host_plan(n: np.ndarray, threshold: int) -> np.ndarray:
+def host_plan(n: np.ndarray, threshold: int, out: np.ndarray | None = None) -> np.ndarray:
     """The batched kernels' plan: lists with n >= threshold first (longest
-    first), then the rest (longest first)."""
-    idx = np.arange(n.size, dtype=np.uint32)
-    big = idx[n >= threshold]
-    small = idx[n < threshold]
-    big = big[np.argsort(-n[big].astype(np.int64), kind="stable")]
-    small = small[np.argsort(-n[small].astype(np.int64), kind="stable")]
-    return np.concatenate([np.array([big.size, small.size, threshold, 0], dtype=np.uint32),
-                           big, small]).astype(np.uint32)
+    first), then the rest in request order (each takes one warp; their order
+    only shifts which warp starts first).  Written into out (uint32, at least
+    4 + n.size entries) when given."""
+    isbig = n >= threshold
+    big = np.flatnonzero(isbig).astype(np.uint32)
+    small = np.flatnonzero(~isbig).astype(np.uint32)
+    if big.size > 1:
+        big = big[np.argsort(-n[big].astype(np.int64), kind="stable")]
+    k = 4 + n.size
+    if out is None:
+        out = np.empty(k, dtype=np.uint32)
+    out[:4] = (big.size, small.size, threshold, 0)
+    out[4:4 + big.size] = big
+    out[4 + big.size:k] = small
+    return out[:k]
 
 
 class RingArena:
@@ -116,13 +123,81 @@ class Batch:
     enc_out: np.ndarray         # byte offsets of encode outputs in scratch
 
 
+def _excl(a: np.ndarray) -> np.ndarray:
+    out = np.zeros(a.size + 1, dtype=np.int64)
+    np.cumsum(a, out=out[1:])
+    return out
+
+
+class Prepared:
+    """Per-request quantities of a request stream, computed once.  A batch is
+    a run [lo, hi) of consecutive requests, so its scratch layout and its
+    list records are slices of these arrays shifted by a few scalars, and the
+    per-batch host work is a handful of slice copies.
+
+    Layout of a batch's scratch block (the rules of Server._layout): decode
+    outputs (16-byte aligned each) | encode inputs (packed) | encode outputs
+    (16-byte aligned each)."""
+
+    def __init__(self, req, pool_rows: np.ndarray, threshold: int):
+        n = np.asarray(req.n, dtype=np.int64)
+        enc = np.asarray(req.is_encode, dtype=bool)
+        self.n = n
+        dsz = np.where(enc, 0, (4 * n + 15) // 16 * 16)
+        ein = np.where(enc, 4 * n, 0)
+        osz = np.where(enc, ((n + 3) // 4 + 4 * n + 15) // 16 * 16, 0)
+        self.cd, self.ce, self.co = _excl(dsz), _excl(ein), _excl(osz)
+        # Admission bound: block bytes of requests [lo, hi) are at most
+        # need[hi] - need[lo] + 16 (the alignment of the encode outputs).
+        self.need = _excl(dsz + ein + osz)
+        self.dec = np.flatnonzero(~enc)
+        self.enc = np.flatnonzero(enc)
+        self.rd = _excl(~enc)       # decodes before each request
+        self.re = _excl(enc)
+        nd = n[self.dec]
+        self.drec = np.empty((self.dec.size, 4), dtype=np.uint64)
+        if self.dec.size:
+            self.drec[:, :2] = pool_rows[np.asarray(req.list_id)[self.dec]]
+        self.drec[:, 2] = self.cd[self.dec]
+        self.drec[:, 3] = nd
+        self.erec = np.empty((self.enc.size, 4), dtype=np.uint64)
+        self.erec[:, 0] = self.ce[self.enc]
+        self.erec[:, 1] = 0
+        self.erec[:, 2] = self.co[self.enc]
+        self.erec[:, 3] = n[self.enc]
+        self.ndec = nd.astype(np.uint32)
+        self.nenc = n[self.enc].astype(np.uint32)
+        self.threshold = threshold
+
+    def spans(self, lo: int, hi: int):
+        """(a, b, c, d): the batch's decodes are self.dec[a:b], its encodes
+        self.enc[c:d]; and the block's section starts and total bytes."""
+        a, b, c, d = int(self.rd[lo]), int(self.rd[hi]), int(self.re[lo]), int(self.re[hi])
+        p_ein = int(self.cd[hi] - self.cd[lo])
+        p_eo = _up(p_ein + int(self.ce[hi] - self.ce[lo]), 16)
+        total = p_eo + int(self.co[hi] - self.co[lo])
+        return a, b, c, d, p_ein, p_eo, total
+
+    def layout(self, lo: int, hi: int):
+        """The same tuple as Server._layout(req, lo, hi)."""
+        a, b, c, d, p_ein, p_eo, total = self.spans(lo, hi)
+        dec_out = self.cd[self.dec[a:b]] - self.cd[lo]
+        enc_in = p_ein + self.ce[self.enc[c:d]] - self.ce[lo]
+        enc_out = p_eo + self.co[self.enc[c:d]] - self.co[lo]
+        return self.dec[a:b] - lo, self.enc[c:d] - lo, dec_out, enc_in, enc_out, total
+
+
 class Server:
     """pool: a batch.ListPool (delta coded); budget: scratch bytes."""
 
-    def __init__(self, pool, budget: int = 16 << 30, max_batch: int = 8192, slots: int = 2,
+    def __init__(self, pool, budget: int = 16 << 30, max_batch: int = 32768, slots: int = 3,
                  threshold: int = 8192):
         self.pool = pool
         self.dev = pool.device
+        # Each pool list's (stream offset, stream bytes): the first two words
+        # of its decode record, gathered by list id per batch.
+        self.pool_rows = np.stack([np.asarray(pool.pool_off, dtype=np.uint64),
+                                   np.asarray(pool.sizes, dtype=np.uint64)], axis=1)
         self.max_batch = max_batch
         self.threshold = threshold
         self.scratch = torch.empty(budget, dtype=torch.uint8, device=self.dev)
@@ -200,48 +275,50 @@ class Server:
         p += int(osz.sum())
         return dec_idx, enc_idx, dec_out, enc_in, enc_out, p
 
-    def _launch(self, req, lo: int, hi: int, s: Slot, block, t_now: float) -> Batch:
-        n = req.n[lo:hi]
-        dec_idx, enc_idx, dec_out, enc_in, enc_out, _ = self._layout(req, lo, hi)
+    def _launch(self, req, prep: Prepared, lo: int, hi: int, s: Slot, block,
+                t_now: float) -> Batch:
+        a, b, c, d, p_ein, p_eo, _ = prep.spans(lo, hi)
+        nd, ne = b - a, d - c
         base = block[0]
-        dec_out = dec_out + base
-        enc_in = enc_in + base
-        enc_out = enc_out + base
-
         h = s.host.numpy()
-        dt = h[self.o_dt:self.o_dt + self.max_batch * self.rec].view(svb.list_dtype())
-        et = h[self.o_et:self.o_et + self.max_batch * self.rec].view(svb.list_dtype())
-        lid = req.list_id[lo:hi][dec_idx]
-        nd = dec_idx.size
-        dt[:nd]["in_off"] = self.pool.pool_off[lid]
-        dt[:nd]["in_len"] = self.pool.sizes[lid]
-        dt[:nd]["out_off"] = dec_out // 4
-        dt[:nd]["n"] = n[dec_idx]
-        dt[:nd]["prev"] = 0
-        ne = enc_idx.size
-        et[:ne]["in_off"] = enc_in // 4
-        et[:ne]["in_len"] = 0
-        et[:ne]["out_off"] = enc_out
-        et[:ne]["n"] = n[enc_idx]
-        et[:ne]["prev"] = 0
-        pd = host_plan(n[dec_idx].astype(np.uint32), self.threshold)
-        pe = host_plan(n[enc_idx].astype(np.uint32), self.threshold)
-        h[self.o_dp:self.o_dp + 4 * pd.size] = pd.view(np.uint8)
-        h[self.o_ep:self.o_ep + 4 * pe.size] = pe.view(np.uint8)
+        # The list records as rows of four 64-bit words: in_off, in_len,
+        # out_off, and n with prev = 0 in the high half (svb_list's layout),
+        # copied from the stream's records and moved into this block.
+        dt = h[self.o_dt:self.o_dt + self.max_batch * self.rec].view(np.uint64).reshape(-1, 4)
+        et = h[self.o_et:self.o_et + self.max_batch * self.rec].view(np.uint64).reshape(-1, 4)
+        # Shifts may be negative (the block starts below the stream's running
+        # offset); added modulo 2^64, they give the exact, non-negative result.
+        def shift(v: int):
+            return np.uint64(v % (1 << 64))
+
+        dt[:nd] = prep.drec[a:b]
+        dt[:nd, 2] += shift(base - int(prep.cd[lo]))
+        dt[:nd, 2] >>= np.uint64(2)
+        et[:ne] = prep.erec[c:d]
+        et[:ne, 0] += shift(base + p_ein - int(prep.ce[lo]))
+        et[:ne, 0] >>= np.uint64(2)
+        et[:ne, 2] += shift(base + p_eo - int(prep.co[lo]))
+        host_plan(prep.ndec[a:b], self.threshold,
+                  h[self.o_dp:self.o_dp + 4 * (4 + nd)].view(np.uint32))
+        host_plan(prep.nenc[c:d], self.threshold,
+                  h[self.o_ep:self.o_ep + 4 * (4 + ne)].view(np.uint32))
         with torch.cuda.stream(s.stream):
             s.dev.copy_(s.host, non_blocking=True)
             if ne:
                 # Fresh lists of this batch's encode requests: contiguous in
                 # enc_values because requests are admitted in order.
-                f0 = int(req.enc_first[lo + enc_idx[0]])
-                f1 = int(req.enc_first[lo + enc_idx[-1]] + n[enc_idx[-1]])
-                e0 = int(enc_in[0])
+                e_first, e_last = int(prep.enc[c]), int(prep.enc[d - 1])
+                f0 = int(req.enc_first[e_first])
+                f1 = int(req.enc_first[e_last]) + int(prep.n[e_last])
+                e0 = base + p_ein
                 self.scratch[e0:e0 + 4 * (f1 - f0)].view(torch.int32).copy_(
                     self.enc_values[f0:f1], non_blocking=True)
             s.graph.replay()
             s.event.record(s.stream)
         s.busy = True
-        return Batch(s, lo, hi, block, t_now, dec_idx, enc_idx, dec_out, enc_out)
+        return Batch(s, lo, hi, block, t_now, prep.dec[a:b] - lo, prep.enc[c:d] - lo,
+                     prep.cd[prep.dec[a:b]] - int(prep.cd[lo]) + base,
+                     prep.co[prep.enc[c:d]] - int(prep.co[lo]) + base + p_eo)
 
     @staticmethod
     def _block_bytes(n: np.ndarray, enc: np.ndarray) -> np.ndarray:
@@ -259,6 +336,7 @@ class Server:
         N = req.n.size
         self.enc_values = torch.from_numpy(req.enc_values.view(np.int32)).pin_memory() \
             if req.enc_values.size else torch.zeros(1, dtype=torch.int32)
+        prep = Prepared(req, self.pool_rows, self.threshold)
         admitted = np.full(N, np.nan)
         done = np.full(N, np.nan)
         inflight: list[Batch] = []
@@ -285,16 +363,19 @@ class Server:
             tail = int(np.searchsorted(req.arrival, now, side="right"))
             if free and head < tail:
                 hi = min(tail, head + self.max_batch)
-                need = self._block_bytes(req.n[head:hi], req.is_encode[head:hi])
-                k = int(np.searchsorted(need, self.arena.largest(), side="right"))
+                # The most requests from head whose block bound fits.
+                room = self.arena.largest() - 16 + int(prep.need[head])
+                k = int(np.searchsorted(prep.need[head + 1:hi + 1], room, side="right"))
                 if k == 0 and not inflight and not self.arena.blocks:
-                    raise ValueError(f"request {head} needs {int(need[0])} bytes of scratch, "
+                    first = int(prep.need[head + 1] - prep.need[head]) + 16
+                    raise ValueError(f"request {head} needs {first} bytes of scratch, "
                                      f"more than the budget of {self.arena.cap}")
                 if k > 0:
-                    blk = self.arena.alloc(self._layout(req, head, head + k)[-1])
+                    blk = self.arena.alloc(prep.spans(head, head + k)[-1])
                     if blk is not None:
                         admitted[head:head + k] = now
-                        inflight.append(self._launch(req, head, head + k, free[0], blk, now))
+                        inflight.append(self._launch(req, prep, head, head + k, free[0], blk,
+                                                     now))
                         head += k
                         batches += 1
                         continue

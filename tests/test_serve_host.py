@@ -92,7 +92,7 @@ def test_random_traffic_keeps_blocks_disjoint_and_largest_exact(seed):
 
 
 @pytest.mark.parametrize("threshold", [1, 8, 100, 10**9])
-def test_plan_orders_big_then_small_longest_first(threshold):
+def test_plan_orders_big_longest_first_then_small_in_request_order(threshold):
     rng = np.random.default_rng(threshold)
     n = rng.integers(1, 300, 257).astype(np.uint32)
     p = host_plan(n, threshold)
@@ -103,7 +103,10 @@ def test_plan_orders_big_then_small_longest_first(threshold):
     assert sorted(np.concatenate([big, small]).tolist()) == list(range(n.size))
     assert np.all(n[big] >= threshold) and np.all(n[small] < threshold)
     assert np.all(np.diff(n[big].astype(np.int64)) <= 0)
-    assert np.all(np.diff(n[small].astype(np.int64)) <= 0)
+    assert np.all(np.diff(small.astype(np.int64)) > 0)
+    out = np.full(4 + n.size + 3, 7, dtype=np.uint32)
+    q = host_plan(n, threshold, out)
+    assert np.array_equal(q, p) and np.all(out[4 + n.size:] == 7)
 
 
 class _Req:
@@ -135,3 +138,33 @@ def test_batch_layout_fits_the_admission_bound(seed):
         if enc_idx.size > 1:  # encode inputs are packed: one copy moves them
             assert all(int(enc_in[j + 1]) == int(enc_in[j]) + 4 * int(n[enc_idx[j]])
                        for j in range(enc_idx.size - 1))
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_prepared_stream_gives_the_same_layouts(seed):
+    """The per-stream precomputation (slices of running sums) gives every
+    batch of consecutive requests the layout Server._layout computes, within
+    the admission bound, and list records that point into that layout."""
+    from paper_1709_08990_gb300.serve import Prepared
+    from paper_1709_08990_gb300 import workloads as W
+    L = W.lists_lengths(300, cap=2_000_000)
+    req = W.serve_requests(L, 400, None, seed=seed, encode_fraction=0.2)
+    rows = np.stack([np.arange(L.size, dtype=np.uint64) * 1000,
+                     np.arange(L.size, dtype=np.uint64) + 7], axis=1)
+    prep = Prepared(req, rows, 8192)
+    rng = np.random.default_rng(seed)
+    for _ in range(100):
+        lo, hi = sorted(rng.integers(0, req.n.size + 1, 2).tolist())
+        if lo == hi:
+            continue
+        want = Server._layout(req, lo, hi)
+        got = prep.layout(lo, hi)
+        for w, g in zip(want[:5], got[:5]):
+            assert np.array_equal(np.asarray(w), np.asarray(g))
+        assert want[5] == got[5] <= prep.need[hi] - prep.need[lo] + 16
+        a, b, c, d, p_ein, p_eo, total = prep.spans(lo, hi)
+        assert total == want[5]
+        ids = np.asarray(req.list_id)[prep.dec[a:b]]
+        assert np.array_equal(prep.drec[a:b, 0], rows[ids, 0])
+        assert np.array_equal(prep.drec[a:b, 3], req.n[prep.dec[a:b]])
+        assert np.array_equal(prep.drec[a:b, 2] - prep.cd[lo], want[2])
