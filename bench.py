@@ -77,7 +77,7 @@ def kernel_source_hash() -> str:
     """Hash of the code (comments and layout aside) of the sources the decode
     kernels are built from."""
     h = hashlib.sha256()
-    for f in ("svb_decode_tiled.cu", "svb_quad.cuh", "svb_device.cuh"):
+    for f in ("svb_decode_tiled.cu", "svb_quad.cuh", "svb_device.cuh", "svb_subtile.cuh"):
         src = open(os.path.join(ROOT, "paper_1709_08990_gb300", "csrc", f)).read()
         h.update(code_only(src).encode())
     return h.hexdigest()[:16]
@@ -445,6 +445,7 @@ def main():
         if not args.no_lists:
             torch.cuda.empty_cache()
             sec["lists_100k"] = time_lists(svb, W, dev, peaks, args.list_count)
+            sec["lists_1000_unscaled"] = time_long_lists(svb, W, dev, peaks)
         line["secondary"] = sec
 
     if rank == 0:
@@ -796,6 +797,39 @@ def time_lists(svb, W, dev, peaks, count: int):
            "encode_speedup_vs_per_list": ms_enc_per_list / ms_benc,
            "serve": serve}
     del pool, d_out, d_out2, d_enc, d_vals
+    torch.cuda.empty_cache()
+    return out
+
+
+def time_long_lists(svb, W, dev, peaks, count: int = 1000):
+    """The list workload's lengths unscaled (log-uniform up to 4,194,304
+    integers): one batched decode with long lists cut into units decoded by
+    several CTAs, against the same batch with every big list decoded whole."""
+    import torch
+    from paper_1709_08990_gb300.batch import ListPool
+    L = W.lists_lengths(count, cap=1 << 40)
+    h = np.empty(int(L.sum()), dtype=np.uint32)
+    W.posting_lists(W.WORKLOADS["lists_100k"].seed, L, out=h)
+    d_vals = torch.from_numpy(h.view(np.int32)).to(dev)
+    del h
+    pool = ListPool(L, d_vals, delta=True, device=dev)
+    total = pool.total
+    d_out = torch.empty(total, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    out = {"lists": pool.k, "ints": total, "max_len": int(L.max()),
+           "stream_bytes": pool.pool_bytes}
+    alg = pool.pool_bytes + 4 * total
+    for name, seg in (("split", None), ("whole", 0)):
+        pool.replan(pool.threshold, 0, seg)
+        d_out.zero_()
+        g = pool.graph(lambda: pool.decode(d_out))
+        ms = _time(lambda: g.replay(), 20, stream)
+        ok = bool(pool.result()[1] == 0 and torch.equal(d_out, d_vals))
+        out[name] = {"gints_per_s": total / ms / 1e6, "ms": ms, "verified": ok,
+                     "frac": alg / (ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
+        del g
+    out["speedup_split_vs_whole"] = out["whole"]["ms"] / out["split"]["ms"]
+    del pool, d_out, d_vals
     torch.cuda.empty_cache()
     return out
 

@@ -220,12 +220,26 @@ typedef struct svb_list {
 size_t svb_batch_plan_bytes(size_t num_lists);
 
 /* Build a batch's work plan on the host from the list lengths in h_lists
- * (HOST memory) and copy it to d_plan (DEVICE, svb_batch_plan_bytes bytes)
- * on stream.  Lists with n >= big_threshold (0: the default, 8192) are each
- * decoded by one CTA, longest first; shorter ones by one warp each.  A plan
- * stays valid for any batch with the same list lengths. */
+ * (HOST memory) and copy it to d_plan (DEVICE, 16-byte aligned,
+ * svb_batch_plan_bytes bytes) on stream.  Lists with n >= big_threshold (0:
+ * the default, 8192) are decoded by CTAs tile by tile, longest first;
+ * shorter ones by one warp each.  A big list of more than 2 * segment_tiles
+ * tiles of 4096 integers, and more than a quarter of a CTA's fair share of
+ * all big lists' tiles (a GPU's resident decode CTAs sharing them evenly), is cut into
+ * units of segment_tiles tiles decoded by several CTAs at once: each batched
+ * decode first finds every such unit's
+ * data offset and carry-in within its list (one pass over the split lists'
+ * streams with a look-back over each list's units), then decodes.
+ * segment_tiles: 0 never splits; at most 32.  svb_batch_plan uses the
+ * default of 16.  A plan stays valid for any batch with the same list
+ * lengths; a plan with split lists holds the state of the call using it, so
+ * use it in one call at a time, always with the same workspace.  The batched
+ * encoder codes every big list whole, whatever the plan. */
 int svb_batch_plan(const svb_list *h_lists, size_t num_lists, uint32_t big_threshold,
                    void *d_plan, size_t plan_bytes, svb_stream_t stream);
+int svb_batch_plan_segments(const svb_list *h_lists, size_t num_lists, uint32_t big_threshold,
+                            uint32_t segment_tiles, void *d_plan, size_t plan_bytes,
+                            svb_stream_t stream);
 
 /* Workspace bytes of a batched call (its counters; zero it once with
  * svb_workspace_init, like the single-stream workspace). */

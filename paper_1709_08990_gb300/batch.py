@@ -39,7 +39,7 @@ class ListPool:
     value 0 for every list (the paper's posting-list setting)."""
 
     def __init__(self, lengths: np.ndarray, values, delta: bool = True, device="cuda:0",
-                 threshold: int = 0, grid: int = 0):
+                 threshold: int = 0, grid: int = 0, segment_tiles: int | None = None):
         self.device = torch.device(device)
         self.delta = delta
         self.lengths = np.ascontiguousarray(lengths, dtype=np.uint32)
@@ -50,6 +50,7 @@ class ListPool:
         self.total = int(self.lengths.sum(dtype=np.uint64))
         self.threshold = threshold
         self.grid = grid
+        self.segment_tiles = segment_tiles   # None: the library's default
         if isinstance(values, torch.Tensor):
             self.d_values = values
         else:
@@ -70,7 +71,10 @@ class ListPool:
     def _plan(self, table: np.ndarray, threshold: int) -> torch.Tensor:
         nb = svb.svb_batch_plan_bytes(self.k)
         d = torch.empty(nb, dtype=torch.uint8, device=self.device)
-        st = svb.svb_batch_plan(table, self.k, threshold, d, nb)
+        if self.segment_tiles is None:
+            st = svb.svb_batch_plan(table, self.k, threshold, d, nb)
+        else:
+            st = svb.svb_batch_plan_segments(table, self.k, threshold, self.segment_tiles, d, nb)
         if st != 0:
             raise svb.SvbError(st, "svb_batch_plan")
         return d
@@ -126,9 +130,10 @@ class ListPool:
     def result(self):
         return self.ws.res.cpu().numpy()
 
-    def replan(self, threshold: int, grid: int = 0):
+    def replan(self, threshold: int, grid: int = 0, segment_tiles: int | None = None):
         self.threshold = threshold
         self.grid = grid
+        self.segment_tiles = segment_tiles
         self.dec_plan = self._plan(self.dec_table, threshold)
         self.enc_plan = self._plan(self.enc_table, threshold)
 

@@ -619,14 +619,23 @@ size_t svb_batch_plan_bytes(size_t num_lists)
     return svb::batch_plan_bytes(num_lists);
 }
 
+int svb_batch_plan_segments(const svb_list *h_lists, size_t num_lists, uint32_t big_threshold,
+                            uint32_t segment_tiles, void *d_plan, size_t plan_bytes,
+                            svb_stream_t stream)
+{
+    if ((!h_lists && num_lists) || !d_plan || plan_bytes < svb::batch_plan_bytes(num_lists) ||
+        num_lists > 0xffffffffull || segment_tiles > 32 || ((uintptr_t)d_plan & 15u))
+        return SVB_EINVAL;
+    const int st = svb::build_batch_plan(h_lists, num_lists, big_threshold, segment_tiles, d_plan,
+                                         reinterpret_cast<cudaStream_t>(stream));
+    return st == 1 ? SVB_EINVAL : st;
+}
+
 int svb_batch_plan(const svb_list *h_lists, size_t num_lists, uint32_t big_threshold,
                    void *d_plan, size_t plan_bytes, svb_stream_t stream)
 {
-    if ((!h_lists && num_lists) || !d_plan || plan_bytes < svb::batch_plan_bytes(num_lists) ||
-        num_lists > 0xffffffffull)
-        return SVB_EINVAL;
-    return svb::build_batch_plan(h_lists, num_lists, big_threshold, d_plan,
-                                 reinterpret_cast<cudaStream_t>(stream));
+    return svb_batch_plan_segments(h_lists, num_lists, big_threshold,
+                                   svb::batch_default_seg_tiles(), d_plan, plan_bytes, stream);
 }
 
 size_t svb_batch_workspace_size(void)

@@ -39,10 +39,28 @@ constexpr uint32_t kDefaultBigThreshold = 8192;
 constexpr int kBSubs = kBQuads / kSubQuads;   // sub-tiles per tile = consumer warps
 static_assert(kBSubs == kWarps, "one consumer warp per sub-tile");
 
-// Plan layout in device memory: header, then big ids, then small ids.
+// Plan layout in device memory: header, big ids, small ids; then, when the
+// plan has units (nunits > 0), a units header, the units and one record per
+// unit.  A unit is a run of tiles of one big list; a list longer than the
+// split length is cut into several units so that several CTAs decode it at
+// once.  The split lists' units come first (units [0, nsplit)); a batch
+// decode first runs batch_prep_kernel over them to find each unit's data
+// offset and carry-in within its list, then decodes units as it would lists.
+// Plans without units (nunits = 0) decode each big list whole.
 struct PlanHeader {
-    uint32_t nbig, nsmall, threshold, pad;
+    uint32_t nbig, nsmall, threshold, nunits;
 };
+
+struct PlanUnit {
+    uint32_t list, t0, nt;   // tiles [t0, t0 + nt) of list `list`
+    uint32_t seg;            // the unit's index among its list's units
+    u64 d0;                  // data offset of tile t0 within the list's data (prep)
+    uint32_t c0;             // carry-in: the list's integer before tile t0 (prep)
+    uint32_t first;          // index of the list's first unit
+};
+
+constexpr uint32_t kSegTiles = 16;          // default tiles per unit of a split list
+constexpr size_t kExtraUnits = 32768;       // units a plan may add beyond one per list
 
 // ---------------------------------------------------------------------------
 // Decode
@@ -76,9 +94,12 @@ struct BPipe {
     uint32_t skip[kBStages];   // the list is truncated: decode nothing
     uint32_t hd[kBStages], hc[kBStages];
     uint32_t clist[kCRing], ctile[kCRing], chc[kCRing];   // what each ring slot holds
+    uint32_t cfirst[kCRing], cc0[kCRing];   // first tile of a unit; the unit's carry-in
+    u64 cd0[kCRing];                        // and its data offset within the list
     uint32_t soff[kBStages][kBSubs];   // each sub-tile's data offset inside the tile
     u64 out_off[kBStages];             // the tile's list: where its integers go,
-    uint32_t n[kBStages], prev[kBStages];   // how many, and its start value
+    uint32_t n[kBStages], prev[kBStages];   // how many, and the unit's carry-in
+    uint32_t first[kBStages];               // the stage holds a unit's first tile
 };
 
 __device__ __forceinline__ const uint32_t *plan_big(const PlanHeader *p)
@@ -89,6 +110,42 @@ __device__ __forceinline__ const uint32_t *plan_big(const PlanHeader *p)
 __device__ __forceinline__ const uint32_t *plan_small(const PlanHeader *p)
 {
     return plan_big(p) + p->nbig;
+}
+
+// Byte offsets within the plan of its units header (one u32: nsplit), its
+// units and its records, for a plan of `ids` big + small ids and up to
+// `units` units.
+__host__ __device__ __forceinline__ size_t plan_units_off(size_t ids)
+{
+    return (sizeof(PlanHeader) + 4 * ids + 15) / 16 * 16;
+}
+
+__host__ __device__ __forceinline__ size_t plan_recs_off(size_t ids, size_t units)
+{
+    return (plan_units_off(ids) + 16 + sizeof(PlanUnit) * units + 63) / 64 * 64;
+}
+
+__device__ __forceinline__ uint32_t plan_nsplit(const PlanHeader *p)
+{
+    if (p->nunits == 0)
+        return 0;
+    const size_t ids = (size_t)p->nbig + p->nsmall;
+    return *reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(p) +
+                                               plan_units_off(ids));
+}
+
+__device__ __forceinline__ PlanUnit *plan_units(const PlanHeader *p)
+{
+    const size_t ids = (size_t)p->nbig + p->nsmall;
+    return reinterpret_cast<PlanUnit *>(
+        const_cast<char *>(reinterpret_cast<const char *>(p)) + plan_units_off(ids) + 16);
+}
+
+__device__ __forceinline__ TileStatus *plan_recs(const PlanHeader *p)
+{
+    const size_t ids = (size_t)p->nbig + p->nsmall;
+    return reinterpret_cast<TileStatus *>(const_cast<char *>(reinterpret_cast<const char *>(p)) +
+                                          plan_recs_off(ids, p->nunits));
 }
 
 // Data bytes of the quads of one tile, from its staged control bytes
@@ -192,35 +249,58 @@ __device__ void bdec_produce(const BatchDecArgs &a, BPipe &P, int lane)
     const uint32_t *big = plan_big(plan);
     uint32_t issued = 0;   // stages posted
 
-    // Look-ahead cursor.
-    uint32_t la_li = kNoList, la_k = 0, la_ntl = 0, la_nql = 0;
-    u64 la_off = 0, la_len = 0;
-    bool la_have = false;
+    // Look-ahead cursor.  With units, it claims units (a list's tiles
+    // [t0, t0 + nt), starting at data offset d0 with carry-in c0, both from
+    // batch_prep_kernel for the units of split lists); without, whole lists.
+    const uint32_t nunits = plan->nunits;
+    const PlanUnit *units = nunits ? plan_units(plan) : nullptr;
+    uint32_t la_li = kNoList, la_k = 0, la_end = 0, la_nql = 0, la_c0 = 0;
+    u64 la_off = 0, la_len = 0, la_d0 = 0;
+    bool la_have = false, la_first = false;
     auto la_claim = [&]() {
         for (;;) {
             uint32_t j = 0;
             if (lane == 0)
                 j = (uint32_t)atomicAdd(&a.hdr->tile_counter, 1ull);
             j = __shfl_sync(0xffffffffu, j, 0);
-            if (j >= plan->nbig) {
+            if (j >= (nunits ? nunits : plan->nbig)) {
                 la_have = false;
                 return;
             }
-            const svb_list L = a.lists[big[j]];
+            uint32_t li, t0 = 0, nt = 0, c0 = 0;
+            u64 d0 = 0;
+            bool seg = false;
+            if (nunits) {
+                const PlanUnit U = units[j];
+                li = U.list;
+                t0 = U.t0;
+                nt = U.nt;
+                seg = U.seg != 0;
+                d0 = U.d0;
+                c0 = U.c0;
+            } else {
+                li = big[j];
+            }
+            const svb_list L = a.lists[li];
             const uint32_t nql = (L.n + 3) / 4;
             if (nql > L.in_len) {   // its control bytes do not fit: reported, skipped
                 if (lane == 0)
                     raise_error(a.hdr, kErrTruncated);
                 continue;
             }
-            la_li = big[j];
+            const uint32_t ntl = (nql + kBQuads - 1) / kBQuads;
+            la_li = li;
             la_nql = nql;
-            la_ntl = (nql + kBQuads - 1) / kBQuads;
             la_off = L.in_off;
             la_len = L.in_len;
-            la_k = 0;
-            la_have = true;
-            return;
+            la_k = nunits ? t0 : 0u;
+            la_end = nunits ? min(t0 + nt, ntl) : ntl;
+            la_d0 = seg ? d0 : 0;
+            la_c0 = seg ? c0 : L.prev;
+            la_first = true;
+            la_have = la_k < la_end;
+            if (la_have)
+                return;
         }
     };
     uint32_t c_issued = 0;   // tiles whose control bytes were fetched
@@ -237,6 +317,9 @@ __device__ void bdec_produce(const BatchDecArgs &a, BPipe &P, int lane)
         if (lane == 0) {
             P.clist[slot] = la_li;
             P.ctile[slot] = la_k;
+            P.cfirst[slot] = la_first ? 1u : 0u;
+            P.cd0[slot] = la_d0;
+            P.cc0[slot] = la_c0;
             P.chc[slot] = (uint32_t)((uintptr_t)gc & 15u);
             mbar_arrive_expect_tx(&P.cfull[slot], pc.bytes);
             if (pc.bytes)
@@ -245,7 +328,8 @@ __device__ void bdec_produce(const BatchDecArgs &a, BPipe &P, int lane)
             mbar_arrive(&P.cfull[slot]);
         }
         c_issued++;
-        if (++la_k == la_ntl)
+        la_first = false;
+        if (++la_k == la_end)
             la_claim();
     };
     auto wait_empty = [&](uint32_t g) -> bool {
@@ -264,6 +348,7 @@ __device__ void bdec_produce(const BatchDecArgs &a, BPipe &P, int lane)
     u64 running = 0;
     svb_list L = {};
     bool cut = false;
+    uint32_t c0 = 0;
     uint32_t g = 0;
     bool failed = false;
     for (; g < c_issued; g++) {
@@ -274,13 +359,15 @@ __device__ void bdec_produce(const BatchDecArgs &a, BPipe &P, int lane)
         }
         __syncwarp();
         const uint32_t tli = P.clist[slot], tk = P.ctile[slot];
-        if (tk == 0) {   // a new list
+        const bool first = P.cfirst[slot] != 0;
+        if (first) {   // a new unit (or list)
             li = tli;
             L = a.lists[li];
             nql = (L.n + 3) / 4;
             ntl = (nql + kBQuads - 1) / kBQuads;
             last_nints = L.n - 4 * (nql - 1);
-            running = 0;
+            running = P.cd0[slot];
+            c0 = P.cc0[slot];
             cut = false;
         }
         if (!wait_empty(g)) {
@@ -315,7 +402,8 @@ __device__ void bdec_produce(const BatchDecArgs &a, BPipe &P, int lane)
             P.tile[s] = tk;
             P.out_off[s] = L.out_off;
             P.n[s] = L.n;
-            P.prev[s] = L.prev;
+            P.prev[s] = c0;
+            P.first[s] = first ? 1u : 0u;
             P.skip[s] = cut ? 1u : 0u;
             P.hd[s] = (uint32_t)((uintptr_t)gd & 15u);
             P.hc[s] = P.chc[slot];
@@ -390,7 +478,7 @@ __device__ void bdec_consume(const BatchDecArgs &a, BPipe &P, uint16_t *s_pos,
         const uint32_t last_nints = n - 4 * (nql - 1);
         const uint32_t q0 = k * kBQuads + warp * kSubQuads;   // first quad of the sub-tile
         const bool skip = P.skip[s] != 0;
-        if (k == 0)
+        if (P.first[s])
             carry = P.prev[s];
         const bool have = !skip && q0 < nql;
         uint32_t v[kSubRounds][4] = {};
@@ -535,6 +623,240 @@ __device__ void bdec_small(const BatchDecArgs &a, uint32_t li, int lane)
     }
     if (lane == 0)
         atomicAdd(&a.hdr->total, (u64)nq + running);
+}
+
+// ---------------------------------------------------------------------------
+// Units of split lists: each one's data offset and carry-in within its list.
+//
+// One CTA per unit at a time, units claimed in order (a list's units are
+// consecutive), so every earlier unit of the list belongs to a CTA that is
+// running or done.  For unit u of list L:
+//   A  each sub-tile's data bytes from its control bytes (Sec. 4), scanned
+//      into offsets within the unit, and the unit's total B_u;
+//   B  d0 = the data bytes of L's earlier units: B_u is published and the
+//      prefix found by a look-back over L's units (prefix 0 at unit 0);
+//   C  each sub-tile's gap sum: a full sub-tile with 512 data bytes has only
+//      zero codes, so its sum is a byte sum (read straight from memory, in
+//      coalesced byte loads); any other sub-tile is staged and decoded;
+//   D  c0 = L.prev plus the gaps of L's earlier units, by a second
+//      look-back; d0 and c0 go into the unit for the decode launch.
+// A list whose stream is cut short publishes zeros (the decode reports it).
+
+constexpr int kBPrepCtrl = 144;                      // 15-byte phase + 128 control bytes
+constexpr int kBPrepData = 16 * kSubQuads + 48;      // phase + 2048 + read slack
+constexpr uint32_t kMaxSegTiles = 32;                // the most tiles a unit may have
+constexpr u64 kPrepSpins = 1ull << 22;
+
+struct BatchPrepArgs {
+    const svb_list *lists;
+    const PlanHeader *plan;
+    const uint8_t *in;
+    WsHeader *hdr;
+};
+
+__global__ void __launch_bounds__(kThreads) batch_prep_kernel(BatchPrepArgs a)
+{
+    __shared__ uint32_t s_off[kMaxSegTiles * kBSubs + 1];
+    __shared__ uint32_t s_gap[kMaxSegTiles * kBSubs];
+    __shared__ __align__(16) uint8_t s_slot[kWarps][2][kBPrepCtrl + kBPrepData];
+    __shared__ __align__(16) uint16_t s_pos[kWarps][kSubQuads];
+    __shared__ u64 s_unit, s_d0;
+    __shared__ uint32_t s_bad, s_last;
+
+    const uint32_t nsplit = plan_nsplit(a.plan);
+    if (nsplit == 0)
+        return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const u64 etag = epoch_tag(a.hdr);
+    PlanUnit *units = plan_units(a.plan);
+    TileStatus *recs = plan_recs(a.plan);
+    const uint64_t keep = l2_policy_evict_last();
+    for (;;) {
+        __syncthreads();
+        if (tid == 0)
+            s_unit = atomicAdd(&a.hdr->a_counter, 1ull);
+        __syncthreads();
+        const u64 u = s_unit;
+        if (u >= nsplit)
+            break;
+        const PlanUnit U = units[u];
+        const svb_list L = a.lists[U.list];
+        const uint32_t nql = (L.n + 3) / 4;
+        const uint32_t last_nints = L.n - 4 * (nql - 1);
+        const uint8_t *lo = a.in + L.in_off;
+        const uint8_t *hi = lo + L.in_len;
+        const uint8_t *data = lo + nql;
+        const uint32_t qb0 = U.t0 * kBQuads;
+        const uint32_t qe = min((U.t0 + U.nt) * kBQuads, nql);
+        const uint32_t ns = (qe - qb0 + kSubQuads - 1) / kSubQuads;
+        const bool ctrl_ok = (u64)nql <= L.in_len;
+        // A: data bytes of each sub-tile (byte loads, coalesced across the warp).
+        for (uint32_t j = warp; j < ns; j += kWarps) {
+            const uint32_t qb = qb0 + j * kSubQuads;
+            uint32_t t = 0;
+            if (ctrl_ok) {
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const uint32_t q = qb + 32 * k + lane;
+                    if (q < qe && q < qb + kSubQuads) {
+                        uint32_t c = __ldg(lo + q);
+                        const uint32_t nints = q == nql - 1 ? last_nints : 4u;
+                        if (nints < 4)
+                            c &= (1u << (2 * nints)) - 1u;
+                        t += quad_count(c, nints);
+                    }
+                }
+            }
+#pragma unroll
+            for (int d = 16; d >= 1; d >>= 1)
+                t += __shfl_xor_sync(0xffffffffu, t, d);
+            if (lane == 0)
+                s_off[j] = t;
+        }
+        __syncthreads();
+        // B: offsets within the unit (warp 0 scans), then the unit's data offset.
+        if (warp == 0) {
+            const uint32_t per = (ns + 31) / 32;
+            const uint32_t b = min(lane * per, ns), e = min(b + per, ns);
+            uint32_t tot = 0;
+            for (uint32_t i = b; i < e; i++)
+                tot += s_off[i];
+            const uint32_t inc = warp_incl_scan(tot);
+            uint32_t c = inc - tot;
+            for (uint32_t i = b; i < e; i++) {
+                const uint32_t v = s_off[i];
+                s_off[i] = c;
+                c += v;
+            }
+            const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
+            if (lane == 0)
+                s_off[ns] = total;
+            TileStatus *me = &recs[U.first + U.seg];
+            u64 d0 = 0;
+            bool ok = true;
+            if (U.seg == 0) {
+                if (lane == 0)
+                    publish(&me->off_tag, &me->off_pre, total, kFlagPrefix, etag);
+            } else {
+                if (lane == 0)
+                    publish(&me->off_tag, &me->off_agg, total, kFlagAgg, etag);
+                d0 = lookback<false>(recs + U.first, U.seg, etag, kPrepSpins, a.hdr, ok);
+                if (lane == 0)
+                    publish(&me->off_tag, &me->off_pre, d0 + total, kFlagPrefix, etag);
+            }
+            if (lane == 0) {
+                if (!ok)
+                    raise_error(a.hdr, kErrTimeout);
+                s_d0 = d0;
+                s_bad = (!ok || !ctrl_ok || (u64)nql + d0 + total > L.in_len) ? 1u : 0u;
+            }
+        }
+        __syncthreads();
+        const u64 d0 = s_d0;
+        const bool bad = s_bad != 0;
+        // C: each sub-tile's gap sum; a warp stages its next sub-tile while it
+        // sums the current one.
+        uint16_t *pos = s_pos[warp];
+        const uintptr_t blo = (uintptr_t)lo, bhi = (uintptr_t)hi;
+        auto geom = [&](uint32_t j, uint32_t &qb, uint32_t &nq, u64 &start, uint32_t &len) {
+            qb = qb0 + j * kSubQuads;
+            nq = min((uint32_t)kSubQuads, qe - qb);
+            start = d0 + s_off[j];
+            len = s_off[j + 1] - s_off[j];
+            const bool full = nq == (uint32_t)kSubQuads && !(qb + nq == nql && last_nints < 4);
+            return full && len == 4u * kSubQuads;   // every code zero: a byte sum
+        };
+        auto stage = [&](uint32_t j, uint8_t *slot) {
+            if (bad || j >= ns)
+                return;
+            uint32_t qb, nq, len;
+            u64 start;
+            if (geom(j, qb, nq, start, len))
+                return;
+            warp_stage(lo + qb, nq, slot, blo, bhi, keep);
+            warp_stage(data + start, len, slot + kBPrepCtrl, blo, bhi, keep);
+        };
+        stage(warp, s_slot[warp][0]);
+        cp_async_commit();
+        uint32_t k = 0;
+        for (uint32_t j = warp; j < ns; j += kWarps, k++) {
+            stage(j + kWarps, s_slot[warp][(k + 1) & 1]);
+            cp_async_commit();
+            cp_async_wait<1>();   // sub-tile j's copies have landed
+            __syncwarp();
+            uint32_t sum = 0;
+            if (!bad) {
+                uint32_t qb, nq, len;
+                u64 start;
+                if (geom(j, qb, nq, start, len)) {
+#pragma unroll
+                    for (int i = 0; i < 16; i++)
+                        sum += __ldg(data + start + lane + 32 * i);
+                } else {
+                    const uint8_t *slot = s_slot[warp][k & 1];
+                    SubTile t;
+                    t.C = slot + ((uintptr_t)(lo + qb) & 15u);
+                    t.D = slot + kBPrepCtrl;
+                    t.base = (uint32_t)((uintptr_t)(data + start) & 15u);
+                    t.nq = nq;
+                    t.tail = qb + nq == nql ? last_nints : 4u;
+                    const uint32_t w = subtile_ctrl_word(t);
+                    subtile_positions(t, w, pos);
+                    __syncwarp();
+                    uint32_t v[kSubRounds][4];
+                    subtile_gather(t, pos, v);
+#pragma unroll
+                    for (int r = 0; r < kSubRounds; r++)
+                        sum += v[r][0] + v[r][1] + v[r][2] + v[r][3];
+                }
+#pragma unroll
+                for (int d = 16; d >= 1; d >>= 1)
+                    sum += __shfl_xor_sync(0xffffffffu, sum, d);
+            }
+            __syncwarp();  // the slot and pos are read before they are refilled
+            if (lane == 0)
+                s_gap[j] = sum;
+        }
+        cp_async_wait<0>();
+        __syncthreads();
+        // D: the unit's carry-in.
+        if (warp == 0) {
+            uint32_t g = 0;
+            for (uint32_t i = lane; i < ns; i += 32)
+                g += s_gap[i];
+#pragma unroll
+            for (int d = 16; d >= 1; d >>= 1)
+                g += __shfl_xor_sync(0xffffffffu, g, d);
+            TileStatus *me = &recs[U.first + U.seg];
+            u64 c0 = L.prev;
+            bool ok = true;
+            if (U.seg == 0) {
+                if (lane == 0)
+                    publish(&me->val_tag, &me->val_pre, (uint32_t)(L.prev + g), kFlagPrefix, etag);
+            } else {
+                if (lane == 0)
+                    publish(&me->val_tag, &me->val_agg, g, kFlagAgg, etag);
+                c0 = lookback<true>(recs + U.first, U.seg, etag, kPrepSpins, a.hdr, ok);
+                if (lane == 0)
+                    publish(&me->val_tag, &me->val_pre, (uint32_t)(c0 + g), kFlagPrefix, etag);
+            }
+            if (lane == 0) {
+                if (!ok)
+                    raise_error(a.hdr, kErrTimeout);
+                units[u].d0 = d0;
+                units[u].c0 = (uint32_t)c0;
+            }
+        }
+    }
+    // The last CTA readies the claim counters for the decode launch.
+    if (tid == 0) {
+        __threadfence();
+        s_last = atomicAdd(&a.hdr->a_done, 1ull) == (u64)gridDim.x - 1 ? 1u : 0u;
+        if (s_last) {
+            st_relaxed(&a.hdr->a_counter, 0);
+            st_relaxed(&a.hdr->a_done, 0);
+        }
+    }
 }
 
 __global__ void __launch_bounds__(kBBlock, 3) batch_decode_kernel(BatchDecArgs a)
@@ -881,6 +1203,24 @@ int launch_batch_decode(const void *d_plan, const svb_list *d_lists, const uint8
     a.hdr = static_cast<WsHeader *>(ws);
     a.result = result;
     a.delta = delta ? 1u : 0u;
+    // Units of split lists first: their data offsets and carry-ins (a
+    // launch that returns at once when the plan has none).
+    static int pg = 0;
+    if (!pg) {
+        int occ = 0, sms = 0, dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_prep_kernel, kThreads, 0);
+        pg = (sms > 0 ? sms : 148) * (occ > 0 ? occ : 1);
+    }
+    BatchPrepArgs pa;
+    pa.lists = d_lists;
+    pa.plan = a.plan;
+    pa.in = in;
+    pa.hdr = a.hdr;
+    prof_begin("batch_prep_kernel", stream);
+    batch_prep_kernel<<<pg, kThreads, 0, stream>>>(pa);
+    prof_end(stream);
     prof_begin("batch_decode_kernel", stream);
     batch_decode_kernel<<<grid > 0 ? grid : g, kBBlock, sizeof(BPipe), stream>>>(a);
     prof_end(stream);
@@ -909,16 +1249,24 @@ int launch_batch_encode(const void *d_plan, const svb_list *d_lists, const uint3
     return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
 
-size_t batch_plan_bytes(size_t num_lists)
+uint32_t batch_default_seg_tiles()
 {
-    return sizeof(PlanHeader) + 4 * num_lists;
+    return kSegTiles;
 }
 
-int build_batch_plan(const svb_list *h_lists, size_t num_lists, uint32_t threshold, void *d_plan,
-                     cudaStream_t stream)
+size_t batch_plan_bytes(size_t num_lists)
+{
+    const size_t units = num_lists + kExtraUnits;
+    return plan_recs_off(num_lists, units) + sizeof(TileStatus) * units;
+}
+
+int build_batch_plan(const svb_list *h_lists, size_t num_lists, uint32_t threshold,
+                     uint32_t seg_tiles, void *d_plan, cudaStream_t stream)
 {
     if (threshold == 0)
         threshold = kDefaultBigThreshold;
+    if (seg_tiles > kMaxSegTiles)
+        return 1;
     std::vector<uint32_t> big, small;
     for (size_t j = 0; j < num_lists; j++) {
         if (h_lists[j].n == 0)
@@ -931,15 +1279,58 @@ int build_batch_plan(const svb_list *h_lists, size_t num_lists, uint32_t thresho
     };
     std::sort(big.begin(), big.end(), longer);
     std::sort(small.begin(), small.end(), longer);
-    std::vector<uint32_t> buf(4 + big.size() + small.size());
-    buf[0] = (uint32_t)big.size();
-    buf[1] = (uint32_t)small.size();
-    buf[2] = threshold;
-    buf[3] = 0;
-    std::copy(big.begin(), big.end(), buf.begin() + 4);
-    std::copy(small.begin(), small.end(), buf.begin() + 4 + big.size());
+    // Units: a big list longer than a quarter of a CTA's fair share of the
+    // big lists' tiles (and than 2 * seg_tiles tiles) is cut into units of seg_tiles
+    // tiles, while the plan's unit budget lasts: splitting costs a pass over
+    // the list's stream, which pays only when one CTA would otherwise be left
+    // decoding it alone at the end.  The split lists' units come first, then
+    // one unit per other big list.
+    u64 big_tiles = 0;
+    for (uint32_t li : big)
+        big_tiles += (((u64)h_lists[li].n + 3) / 4 + kBQuads - 1) / kBQuads;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const u64 ctas = 3 * (u64)(sms > 0 ? sms : 148);
+    const u64 fair = (big_tiles + ctas - 1) / ctas;
+    std::vector<PlanUnit> split, whole;
+    const size_t budget = num_lists + kExtraUnits;
+    for (uint32_t li : big) {
+        const uint32_t nql = (uint32_t)(((u64)h_lists[li].n + 3) / 4);
+        const uint32_t ntl = (nql + kBQuads - 1) / kBQuads;
+        const uint32_t nseg = seg_tiles ? (ntl + seg_tiles - 1) / seg_tiles : 1u;
+        if (seg_tiles && ntl > 2 * seg_tiles && 4 * (u64)ntl > fair &&
+            split.size() + nseg + (big.size() - 1) <= budget) {
+            const uint32_t first = (uint32_t)split.size();
+            for (uint32_t k = 0; k < nseg; k++)
+                split.push_back(PlanUnit{li, k * seg_tiles, std::min(seg_tiles, ntl - k * seg_tiles),
+                                         k, 0, 0, first});
+        } else {
+            whole.push_back(PlanUnit{li, 0, ntl, 0, 0, 0, 0});
+        }
+    }
+    const size_t ids = big.size() + small.size();
+    const size_t nunits = split.empty() ? 0 : split.size() + whole.size();
+    const size_t bytes = nunits ? plan_recs_off(ids, nunits) + sizeof(TileStatus) * nunits
+                                : sizeof(PlanHeader) + 4 * ids;
+    std::vector<uint8_t> buf(bytes, 0);
+    uint32_t *w = reinterpret_cast<uint32_t *>(buf.data());
+    w[0] = (uint32_t)big.size();
+    w[1] = (uint32_t)small.size();
+    w[2] = threshold;
+    w[3] = (uint32_t)nunits;
+    std::copy(big.begin(), big.end(), w + 4);
+    std::copy(small.begin(), small.end(), w + 4 + big.size());
+    if (nunits) {
+        // Units header (nsplit), the units, then zeroed records: a zero tag
+        // never matches a launch's tag.
+        *reinterpret_cast<uint32_t *>(buf.data() + plan_units_off(ids)) = (uint32_t)split.size();
+        PlanUnit *u = reinterpret_cast<PlanUnit *>(buf.data() + plan_units_off(ids) + 16);
+        std::copy(split.begin(), split.end(), u);
+        std::copy(whole.begin(), whole.end(), u + split.size());
+    }
     // Pageable source: the copy is staged before this call returns.
-    return cudaMemcpyAsync(d_plan, buf.data(), buf.size() * 4, cudaMemcpyHostToDevice, stream) ==
+    return cudaMemcpyAsync(d_plan, buf.data(), buf.size(), cudaMemcpyHostToDevice, stream) ==
                    cudaSuccess
                ? 0
                : 3;

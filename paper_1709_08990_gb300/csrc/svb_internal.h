@@ -72,8 +72,9 @@ int launch_batch_encode(const void *d_plan, const svb_list *d_lists, const uint3
                         uint8_t *out, u64 *sizes, bool delta, void *ws, DeviceResult *result,
                         cudaStream_t stream, int grid);
 size_t batch_plan_bytes(size_t num_lists);
-int build_batch_plan(const svb_list *h_lists, size_t num_lists, uint32_t threshold, void *d_plan,
-                     cudaStream_t stream);
+int build_batch_plan(const svb_list *h_lists, size_t num_lists, uint32_t threshold,
+                     uint32_t seg_tiles, void *d_plan, cudaStream_t stream);
+uint32_t batch_default_seg_tiles();
 
 // Seek / select queries on a pool of lists (svb_query.cu).
 int launch_query(const svb_list *lists, u64 num_lists, const uint8_t *in, bool delta,

@@ -125,4 +125,53 @@ __device__ __forceinline__ void subtile_gather(const SubTile &t, const uint16_t 
     }
 }
 
+// Sum of the 512 one-byte integers at staged positions [base, base + 512) of
+// D (a sub-tile whose control bytes are all zero: Sec. 4, an all-zero control
+// byte covers 4 bytes), a word at a time with the bytes outside masked; the
+// warp's total in every lane.
+__device__ __forceinline__ uint32_t zero_ctrl_sum(const uint8_t *D, uint32_t base)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t *Wd = reinterpret_cast<const uint32_t *>(D);
+    const uint32_t b0 = base >> 2, b1 = (base + 4 * kSubQuads + 3) >> 2;
+    const uint32_t head = base & 3u, tail = (base + 4 * kSubQuads) & 3u;
+    uint32_t t = 0;
+    for (uint32_t i = b0 + lane; i < b1; i += 32) {
+        uint32_t x = Wd[i];
+        if (i == b0)
+            x &= 0xffffffffu << (8 * head);
+        if (i == b1 - 1 && tail)
+            x &= 0xffffffffu >> (8 * (4 - tail));
+        const uint32_t y = (x & 0x00ff00ffu) + ((x >> 8) & 0x00ff00ffu);
+        t += (y & 0xffffu) + (y >> 16);
+    }
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1)
+        t += __shfl_xor_sync(0xffffffffu, t, d);
+    return t;
+}
+
+// Copies the bytes of global [g, g + len) that lie inside [lo, hi) so that
+// byte g + i lands at dst + (g mod 16) + i (dst 16-byte aligned): whole
+// 16-byte chunks by cp.async, a chunk that straddles lo or hi byte by byte
+// (none of its bytes outside [lo, hi) is read).  One whole warp; the caller
+// commits and waits.
+__device__ __forceinline__ void warp_stage(const uint8_t *g, uint32_t len, uint8_t *dst,
+                                           uintptr_t lo, uintptr_t hi, uint64_t policy)
+{
+    const int lane = threadIdx.x & 31;
+    const uintptr_t a0 = (uintptr_t)g & ~(uintptr_t)15;
+    const uint32_t nch = (uint32_t)((((uintptr_t)g + len + 15) & ~(uintptr_t)15) - a0) >> 4;
+    for (uint32_t c = lane; c < nch; c += 32) {
+        const uintptr_t src = a0 + 16 * (uintptr_t)c;
+        if (src >= lo && src + 16 <= hi) {
+            cp_async16(dst + 16 * c, reinterpret_cast<const void *>(src), policy);
+        } else {
+            for (int i = 0; i < 16; i++)
+                if (src + i >= lo && src + i < hi)
+                    dst[16 * c + i] = __ldg(reinterpret_cast<const uint8_t *>(src + i));
+        }
+    }
+}
+
 }  // namespace svb

@@ -72,6 +72,7 @@ def lib() -> ctypes.CDLL:
             "svb_profile_begin": ([], i32),
             "svb_profile_end": ([ctypes.c_char_p, sz], sz),
             "svb_batch_plan": ([vp, sz, u32, vp, sz, vp], i32),
+            "svb_batch_plan_segments": ([vp, sz, u32, u32, vp, sz, vp], i32),
             "svb_batch_workspace_size": ([], sz),
             "svb_batch_decode": ([vp, vp, vp, vp, i32, vp, vp, sz, i32, vp], i32),
             "svb_batch_encode": ([vp, vp, vp, vp, i32, vp, vp, vp, sz, i32, vp], i32),
@@ -222,6 +223,12 @@ def svb_batch_plan(h_lists, num_lists: int, big_threshold: int, d_plan, plan_byt
                    stream=None) -> int:
     return lib().svb_batch_plan(_p(h_lists), num_lists, big_threshold, _p(d_plan), plan_bytes,
                                 _stream(stream))
+
+
+def svb_batch_plan_segments(h_lists, num_lists: int, big_threshold: int, segment_tiles: int,
+                            d_plan, plan_bytes: int, stream=None) -> int:
+    return lib().svb_batch_plan_segments(_p(h_lists), num_lists, big_threshold, segment_tiles,
+                                         _p(d_plan), plan_bytes, _stream(stream))
 
 
 def svb_batch_workspace_size() -> int:

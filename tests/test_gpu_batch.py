@@ -70,10 +70,14 @@ def opos_enc(j, lengths):
     return int(sum(svb.svb_max_compressed_size(int(m)) for m in lengths[:j]))
 
 
-def run_plan(h_lists, threshold):
+def run_plan(h_lists, threshold, segment_tiles=None):
     nbytes = svb.svb_batch_plan_bytes(len(h_lists))
     d_plan = torch.empty(nbytes, dtype=torch.uint8, device=DEV)
-    assert svb.svb_batch_plan(h_lists, len(h_lists), threshold, d_plan, nbytes) == 0
+    if segment_tiles is None:
+        assert svb.svb_batch_plan(h_lists, len(h_lists), threshold, d_plan, nbytes) == 0
+    else:
+        assert svb.svb_batch_plan_segments(h_lists, len(h_lists), threshold, segment_tiles,
+                                           d_plan, nbytes) == 0
     return d_plan
 
 
@@ -84,14 +88,20 @@ def workspace():
     return ws, nb
 
 
-def batch_decode(b: Batch, threshold=0, grid=0):
-    d_plan = run_plan(b.dec_lists, threshold)
-    d_lists = to_dev(b.dec_lists.view(np.uint8))
+def batch_decode(b: Batch, threshold=0, grid=0, segment_tiles=None, repeat=1, in_lens=None):
+    lists = b.dec_lists.copy()
+    if in_lens is not None:
+        lists["in_len"] = in_lens
+    d_plan = run_plan(lists, threshold, segment_tiles)
+    d_lists = to_dev(lists.view(np.uint8))
     d_in = to_dev(b.pool) if b.pool.size else torch.zeros(1, dtype=torch.uint8, device=DEV)
     d_out = torch.full((max(1, b.total_ints),), -7, dtype=torch.int32, device=DEV)
     ws, nb = workspace()
     res = torch.zeros(2, dtype=torch.int64, device=DEV)
-    assert svb.svb_batch_decode(d_plan, d_lists, d_in, d_out, int(b.delta), res, ws, nb, grid) == 0
+    for _ in range(repeat):  # a plan and workspace serve one call after another
+        d_out.fill_(-7)
+        assert svb.svb_batch_decode(d_plan, d_lists, d_in, d_out, int(b.delta), res, ws, nb,
+                                    grid) == 0
     r = res.cpu().numpy()
     return d_out[: b.total_ints].cpu().numpy().view(np.uint32), r
 
@@ -254,3 +264,43 @@ def test_one_call_per_list_matches_the_oracle(delta):
         off = int(b.enc_lists[j]["out_off"])
         assert r[j, 1] == 0 and r[j, 0] == b.streams[j].size
         assert np.array_equal(e[off: off + b.streams[j].size], b.streams[j])
+
+
+# Unscaled long lists (up to the 4,194,304 integers the list workload draws
+# from), so that big lists are cut into units decoded by several CTAs, with
+# lengths at and around the split edges.
+LONG = [4_194_304, 1_500_001, 600_003, 262_145, 131_073, 131_072, 131_071, 65_537, 8193, 77,
+        4096 * 33 + 1, 4096 * 32, 3, 0, 9000]
+
+
+@pytest.mark.parametrize("delta", [False, True])
+@pytest.mark.parametrize("segment_tiles", [None, 0, 1, 3, 32])
+def test_batch_decode_splits_long_lists(delta, segment_tiles):
+    b = Batch(LONG, delta, seed=11, prevs=[(1237 * j) & 0xFFFFFFF for j in range(len(LONG))],
+              gap_bytes=3)
+    got, r = batch_decode(b, 0, 0, segment_tiles, repeat=2)
+    assert r[1] == 0
+    assert r[0] == sum(s.size for s in b.streams)
+    for j, m in enumerate(b.lengths):
+        o = int(b.dec_lists[j]["out_off"])
+        assert np.array_equal(got[o:o + int(m)], b.values[j]), f"list {j} (n={m})"
+
+
+def test_batch_decode_split_list_cut_short_is_reported():
+    b = Batch([600_003, 1000, 262_145], True, seed=12)
+    lens = b.dec_lists["in_len"].copy()
+    lens[0] -= 1          # the split list's stream ends one byte early
+    _, r = batch_decode(b, 0, 0, 2, in_lens=lens)
+    assert r[1] == svb.SVB_ETRUNCATED
+    got, r = batch_decode(b, 0, 0, 2)   # the whole streams still decode
+    assert r[1] == 0 and np.array_equal(got, b.all_values)
+
+
+def test_segmented_plan_rejects_bad_arguments():
+    lists = np.zeros(3, dtype=svb.list_dtype())
+    lists["n"] = 5
+    nb = svb.svb_batch_plan_bytes(3)
+    d = torch.empty(nb + 16, dtype=torch.uint8, device=DEV)
+    assert svb.svb_batch_plan_segments(lists, 3, 0, 33, d, nb) == svb.SVB_EINVAL
+    assert svb.svb_batch_plan_segments(lists, 3, 0, 4, d[1:], nb) == svb.SVB_EINVAL
+    assert svb.svb_batch_plan_segments(lists, 3, 0, 4, d, nb) == svb.SVB_OK
