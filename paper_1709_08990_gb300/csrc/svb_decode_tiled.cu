@@ -660,6 +660,8 @@ struct TiledArgs {
     u64 range_subs;     // kDelta: carries are relative to ranges of this many
                         // sub-tiles, whose carry-ins are st[range].val_pre
                         // (0: the carries are absolute)
+    u64 range_magic;    // ceil(2^64 / (range_subs / kSubs)): a tile's range is
+                        // the high word of tile * range_magic
     u64 tile0, tile1;   // decoding: the tiles [tile0, tile1) to decode
     uint32_t prev;
     uint32_t out_aligned;
@@ -702,8 +704,11 @@ __device__ void produce(const TiledArgs &a, Pipe &P, u64 first, int lane)
             off = a.offs[sb];
             if (kMode == kDelta && lane < kSubs && sb < a.nsubs) {
                 car = (uint32_t)a.carries[sb];
+                // A range is a whole number of tiles; t / (tiles per range)
+                // by one multiply (exact for t < 2^32: the rounding error
+                // of the reciprocal stays below 1 / divisor).
                 if (a.range_subs)
-                    car += (uint32_t)a.st[sb / a.range_subs].val_pre;
+                    car += (uint32_t)a.st[__umul64hi(t, a.range_magic)].val_pre;
             }
         }
     };
@@ -1219,6 +1224,7 @@ static TiledArgs tiled_args(const uint8_t *in, u64 n, uint32_t *out, uint32_t pr
     t.spin_limit = spin_limit;
     t.per_cta = 0;
     t.range_subs = 0;
+    t.range_magic = 0;
     t.tile0 = 0;
     t.tile1 = t.ntiles;
     t.prev = prev;
@@ -1282,6 +1288,8 @@ int launch_decode_tiled(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, uin
         t.range_subs = launch_delta_prep(in, in_len, n, prev, ws, stream, spin_limit);
         if (!t.range_subs)
             return 3;
+        const u64 range_tiles = t.range_subs / kSubs;  // >= 16: ranges are whole groups
+        t.range_magic = ~0ull / range_tiles + 1;
         u64 grid = min((u64)tiled_grid<kDelta>(), ntiles);
         prof_begin("decode_tiled_kernel<delta>", stream);
         decode_tiled_kernel<kDelta><<<(unsigned)grid, kDecBlock, sizeof(Pipe), stream>>>(t);
