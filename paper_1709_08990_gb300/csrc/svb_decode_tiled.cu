@@ -166,12 +166,41 @@ __device__ RangeBytes range_offsets(const OffsetsArgs &a, u64 cta, u64 etag, u64
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t last_nints = (uint32_t)(a.n - 4 * (a.nquads - 1));
 
-    // Each iteration: 64 quads per thread, two threads per sub-tile.
+    // Each iteration: 64 quads per thread, two threads per sub-tile.  On an
+    // aligned stream the next group's four 16-byte loads are issued before
+    // this group is summed, so each group costs a scan and a barrier, not a
+    // round trip to memory as well.
     u64 running = 0;  // this CTA's data bytes so far (every thread)
     int buf = 0;
+    auto whole = [&](u64 q) { return a.in_aligned && q + 64 <= a.nquads; };
+    uint4 nxt[4] = {};
+    if (g0 < g1 && whole(g0 * (u64)kOffGroupQuads + 64u * tid)) {
+        const uint4 *p = reinterpret_cast<const uint4 *>(a.in + g0 * (u64)kOffGroupQuads + 64u * tid);
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+            nxt[i] = __ldg(p + i);
+    }
     for (u64 g = g0; g < g1; g++, buf ^= 1) {
         const u64 q = g * (u64)kOffGroupQuads + 64u * tid;
-        uint32_t sum = sum64(a, q, last_nints);
+        uint4 cur[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+            cur[i] = nxt[i];
+        const u64 qn = q + (u64)kOffGroupQuads;
+        if (g + 1 < g1 && whole(qn)) {
+            const uint4 *p = reinterpret_cast<const uint4 *>(a.in + qn);
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+                nxt[i] = __ldg(p + i);
+        }
+        uint32_t sum = 0;
+        if (whole(q)) {
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+                sum += chunk_bytes(cur[i], q + 16 * i, a.nquads, last_nints);
+        } else {
+            sum = sum64(a, q, last_nints);
+        }
         sum += __shfl_xor_sync(0xffffffffu, sum, 1);   // the sub-tile's bytes
         const uint32_t v = (lane & 1) ? 0u : sum;
         const uint32_t inc = warp_incl_scan(v);
@@ -258,9 +287,22 @@ __device__ RangeBytes range_offsets(const OffsetsArgs &a, u64 cta, u64 etag, u64
     __syncthreads();
     const u64 base = *s_base;
     if (base) {
+        // Eight loads in flight per thread, then the eight stores.
         const u64 s0 = g0 * kOffGroupSubs, s1 = min(g1 * kOffGroupSubs, a.nsubs);
-        for (u64 s = s0 + tid; s < s1; s += kThreads)
-            a.offs[s] += base;
+        for (u64 s = s0 + tid; s < s1; s += 8u * kThreads) {
+            u64 v[8];
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                const u64 si = s + (u64)i * kThreads;
+                v[i] = si < s1 ? a.offs[si] : 0ull;
+            }
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                const u64 si = s + (u64)i * kThreads;
+                if (si < s1)
+                    a.offs[si] = v[i] + base;
+            }
+        }
     }
     __syncthreads();
     return RangeBytes{base, running};
