@@ -702,7 +702,8 @@ def time_lists(svb, W, dev, peaks, count: int):
     pool = ListPool(L, d_vals, delta=True, device=dev)
     total = pool.total
     d_out = torch.empty(total, dtype=torch.int32, device=dev)
-    tuned = autotune.tune_batch(pool, f"lists_{count}", d_out)
+    d_enc = torch.empty_like(pool.pool)
+    tuned = autotune.tune_batch(pool, f"lists_{count}", d_out, enc_out=d_enc)
     stream = torch.cuda.current_stream()
     g = pool.graph(lambda: pool.decode(d_out))
     ms_graph = _time(lambda: g.replay(), 20, stream)

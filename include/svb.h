@@ -245,6 +245,18 @@ int svb_batch_plan_segments(const svb_list *h_lists, size_t num_lists, uint32_t 
  * svb_workspace_init, like the single-stream workspace). */
 size_t svb_batch_workspace_size(void);
 
+/* Staging depth of the batched kernels, for every later svb_batch_decode /
+ * svb_batch_encode of this process: the tiles of compressed bytes (decode)
+ * or values (encode) each CTA keeps in flight in shared memory.  Fewer
+ * stages take less shared memory, so more CTAs fit on an SM; the depths
+ * built are 2, 3 and 4 for decoding and 2 and 3 for encoding (0 restores
+ * the default: 2 and 3).  The tuner (autotune.py) picks them per GPU and
+ * workload.  No paper counterpart: a launch parameter.  Returns SVB_EINVAL
+ * for a depth that is not built, leaving both settings as they were.
+ * svb_batch_get_stages gives the depth in use (encode != 0: the encoder's). */
+int svb_batch_set_stages(int decode_stages, int encode_stages);
+int svb_batch_get_stages(int encode);
+
 /* Decode / encode every list of the plan in one persistent launch enqueued on
  * stream.  d_lists is the DEVICE copy of the list table.  d_result receives
  * the total bytes consumed / written and the status (SVB_ETRUNCATED when

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "svb.h"
@@ -29,7 +30,6 @@
 namespace svb {
 
 constexpr int kBQuads = 1024;                // quads per tile
-constexpr int kBStages = 4;
 constexpr int kBStageData = 16 * kBQuads + 64;
 constexpr int kBStageCtrl = kBQuads + 32;
 constexpr int kBBlock = kThreads + 32;       // 8 consumer warps + 1 producer warp
@@ -78,28 +78,31 @@ struct BatchDecArgs {
 // Control bytes travel ahead of the data: tile g's control bytes sit in ring
 // slot g % kCRing and are fetched kCAhead tiles before its data, so the
 // producer never waits a round trip to learn where a tile's data start.  Slot
-// (g + kCAhead) % kCRing was last used by tile g - kBStages, whose stage the
+// (g + kCAhead) % kCRing was last used by tile g - S, whose stage the
 // producer has seen released before it refills the slot.
 constexpr int kCAhead = 2;
-constexpr int kCRing = kBStages + kCAhead;
 
+// Staging depth S (stages of tile data) is a compile-time parameter of the
+// decode kernel: the autotuner picks among the instantiations.
+template <int S>
 struct BPipe {
-    uint8_t data[kBStages][kBStageData];
+    static constexpr int kCRing = S + kCAhead;
+    uint8_t data[S][kBStageData];
     uint8_t ctrl[kCRing][kBStageCtrl];
-    uint64_t full[kBStages];   // control and data landed (consumers wait)
+    uint64_t full[S];   // control and data landed (consumers wait)
     uint64_t cfull[kCRing];    // control landed (the producer waits)
-    uint64_t empty[kBStages];  // consumers done with the stage
-    uint32_t list[kBStages];   // list id, or kNoList
-    uint32_t tile[kBStages];   // tile index within the list
-    uint32_t skip[kBStages];   // the list is truncated: decode nothing
-    uint32_t hd[kBStages], hc[kBStages];
+    uint64_t empty[S];  // consumers done with the stage
+    uint32_t list[S];   // list id, or kNoList
+    uint32_t tile[S];   // tile index within the list
+    uint32_t skip[S];   // the list is truncated: decode nothing
+    uint32_t hd[S], hc[S];
     uint32_t clist[kCRing], ctile[kCRing], chc[kCRing];   // what each ring slot holds
     uint32_t cfirst[kCRing], cc0[kCRing];   // first tile of a unit; the unit's carry-in
     u64 cd0[kCRing];                        // and its data offset within the list
-    uint32_t soff[kBStages][kBSubs];   // each sub-tile's data offset inside the tile
-    u64 out_off[kBStages];             // the tile's list: where its integers go,
-    uint32_t n[kBStages], prev[kBStages];   // how many, and the unit's carry-in
-    uint32_t first[kBStages];               // the stage holds a unit's first tile
+    uint32_t soff[S][kBSubs];   // each sub-tile's data offset inside the tile
+    u64 out_off[S];             // the tile's list: where its integers go,
+    uint32_t n[S], prev[S];   // how many, and the unit's carry-in
+    uint32_t first[S];               // the stage holds a unit's first tile
 };
 
 __device__ __forceinline__ const uint32_t *plan_big(const PlanHeader *p)
@@ -243,8 +246,10 @@ __device__ __forceinline__ uint32_t tile_data_bytes(const uint8_t *C, uint32_t n
 // copies the data.  Every tile whose control bytes were fetched gets one stage
 // (a skipped one if its list's data are cut short), so stage g always pairs
 // with ring slot g % kCRing.
-__device__ void bdec_produce(const BatchDecArgs &a, BPipe &P, int lane)
+template <int S>
+__device__ void bdec_produce(const BatchDecArgs &a, BPipe<S> &P, int lane)
 {
+    constexpr int kCRing = BPipe<S>::kCRing;
     const PlanHeader *plan = a.plan;
     const uint32_t *big = plan_big(plan);
     uint32_t issued = 0;   // stages posted
@@ -333,9 +338,9 @@ __device__ void bdec_produce(const BatchDecArgs &a, BPipe &P, int lane)
             la_claim();
     };
     auto wait_empty = [&](uint32_t g) -> bool {
-        if (g < (uint32_t)kBStages)
+        if (g < (uint32_t)S)
             return true;
-        bool ok = mbar_wait_bounded(&P.empty[g % kBStages], ((g / kBStages) - 1) & 1u, kBPolls);
+        bool ok = mbar_wait_bounded(&P.empty[g % S], ((g / S) - 1) & 1u, kBPolls);
         return __all_sync(0xffffffffu, ok);
     };
 
@@ -352,7 +357,7 @@ __device__ void bdec_produce(const BatchDecArgs &a, BPipe &P, int lane)
     uint32_t g = 0;
     bool failed = false;
     for (; g < c_issued; g++) {
-        const int slot = g % kCRing, s = g % kBStages;
+        const int slot = g % kCRing, s = g % S;
         if (!mbar_wait_bounded(&P.cfull[slot], (g / kCRing) & 1u, kBPolls)) {
             if (lane == 0)
                 raise_error(a.hdr, kErrTimeout);
@@ -424,7 +429,7 @@ __device__ void bdec_produce(const BatchDecArgs &a, BPipe &P, int lane)
     if (!failed) {
         // No tile left: one stage marked kNoList ends the big-list phase.
         if (wait_empty(g)) {
-            const int s = g % kBStages;
+            const int s = g % S;
             if (lane == 0) {
                 P.list[s] = kNoList;
                 mbar_arrive_expect_tx(&P.full[s], 0);
@@ -438,9 +443,9 @@ __device__ void bdec_produce(const BatchDecArgs &a, BPipe &P, int lane)
     }
     // Let every copy this warp started land before the CTA can exit.
     if (lane == 0) {
-        for (int s = 0; s < kBStages; s++)
+        for (int s = 0; s < S; s++)
             if (issued > (uint32_t)s) {
-                uint32_t fills = (issued - 1 - s) / kBStages + 1;
+                uint32_t fills = (issued - 1 - s) / S + 1;
                 mbar_wait_bounded(&P.full[s], (fills - 1) & 1u, kBPolls);
             }
         for (int r = 0; r < kCRing; r++)
@@ -456,15 +461,17 @@ __device__ void bdec_produce(const BatchDecArgs &a, BPipe &P, int lane)
 // tile on its own (the same sub-tile decode as the single-stream decoder).
 // For differential lists the eight warps trade their sub-tile gap sums once
 // per tile (one barrier), and each keeps the list's running sum itself.
-__device__ void bdec_consume(const BatchDecArgs &a, BPipe &P, uint16_t *s_pos,
+template <int S>
+__device__ void bdec_consume(const BatchDecArgs &a, BPipe<S> &P, uint16_t *s_pos,
                              uint32_t (*s_sum)[kWarps])
 {
+    constexpr int kCRing = BPipe<S>::kCRing;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint16_t *pos = s_pos + warp * kSubQuads;
     uint32_t carry = 0;  // the list's integer before the current tile
     for (uint32_t g = 0;; g++) {
-        const int s = g % kBStages;
-        if (!mbar_wait_bounded(&P.full[s], (g / kBStages) & 1u, kBPolls)) {
+        const int s = g % S;
+        if (!mbar_wait_bounded(&P.full[s], (g / S) & 1u, kBPolls)) {
             raise_error(a.hdr, kErrTimeout);
             break;
         }
@@ -859,16 +866,18 @@ __global__ void __launch_bounds__(kThreads) batch_prep_kernel(BatchPrepArgs a)
     }
 }
 
-__global__ void __launch_bounds__(kBBlock, 3) batch_decode_kernel(BatchDecArgs a)
+template <int S, int kMinCtas>
+__global__ void __launch_bounds__(kBBlock, kMinCtas) batch_decode_kernel(BatchDecArgs a)
 {
+    constexpr int kCRing = BPipe<S>::kCRing;
     extern __shared__ __align__(128) uint8_t dyn_smem[];
-    BPipe &P = *reinterpret_cast<BPipe *>(dyn_smem);
+    BPipe<S> &P = *reinterpret_cast<BPipe<S> *>(dyn_smem);
     __shared__ __align__(16) uint16_t s_pos[kBQuads];   // each warp's quad positions
     __shared__ uint32_t s_sum[2][kWarps];                // sub-tile gap sums, per tile parity
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
-        for (int s = 0; s < kBStages; s++) {
+        for (int s = 0; s < S; s++) {
             mbar_init(&P.full[s], 32);
             mbar_init(&P.empty[s], kWarps);
         }
@@ -878,9 +887,9 @@ __global__ void __launch_bounds__(kBBlock, 3) batch_decode_kernel(BatchDecArgs a
     }
     __syncthreads();
     if (warp == kWarps)
-        bdec_produce(a, P, lane);
+        bdec_produce<S>(a, P, lane);
     else
-        bdec_consume(a, P, s_pos, s_sum);
+        bdec_consume<S>(a, P, s_pos, s_sum);
 
     // Small lists: every warp takes them one by one.
     const uint32_t *small = plan_small(a.plan);
@@ -911,22 +920,25 @@ struct BatchEncArgs {
     uint32_t delta;
 };
 
-constexpr int kEStages = 3;
 constexpr int kEStageBytes = 16 * kBQuads + 16;  // 4096 values + 16-byte phase
 
+// Staging depth S of the encode kernel, a compile-time parameter like the
+// decode kernel's.
+template <int S>
 struct EPipe {
-    uint8_t vals[kEStages][kEStageBytes];
+    uint8_t vals[S][kEStageBytes];
     uint32_t slice[kWarps][kEncSliceWords];   // each warp's data bytes, phased like the output
-    uint64_t full[kEStages];
-    uint64_t empty[kEStages];
-    uint32_t list[kEStages];
-    uint32_t tile[kEStages];
-    uint32_t hv[kEStages];  // phase (mod 16) of the staged values
-    u64 out_off[kEStages];  // the tile's list: where its stream goes,
-    uint32_t n[kEStages], prev[kEStages];   // its integers and start value
+    uint64_t full[S];
+    uint64_t empty[S];
+    uint32_t list[S];
+    uint32_t tile[S];
+    uint32_t hv[S];  // phase (mod 16) of the staged values
+    u64 out_off[S];  // the tile's list: where its stream goes,
+    uint32_t n[S], prev[S];   // its integers and start value
 };
 
-__device__ void benc_produce(const BatchEncArgs &a, EPipe &P, int lane)
+template <int S>
+__device__ void benc_produce(const BatchEncArgs &a, EPipe<S> &P, int lane)
 {
     const PlanHeader *plan = a.plan;
     const uint32_t *big = plan_big(plan);
@@ -947,9 +959,9 @@ __device__ void benc_produce(const BatchEncArgs &a, EPipe &P, int lane)
     };
     bool have = claim();
     for (uint32_t g = 0;; g++) {
-        const int s = g % kEStages;
-        if (g >= (uint32_t)kEStages) {
-            bool ok = mbar_wait_bounded(&P.empty[s], ((g / kEStages) - 1) & 1u, kBPolls);
+        const int s = g % S;
+        if (g >= (uint32_t)S) {
+            bool ok = mbar_wait_bounded(&P.empty[s], ((g / S) - 1) & 1u, kBPolls);
             if (!__all_sync(0xffffffffu, ok)) {
                 if (lane == 0)
                     raise_error(a.hdr, kErrTimeout);
@@ -992,9 +1004,9 @@ __device__ void benc_produce(const BatchEncArgs &a, EPipe &P, int lane)
         issued = g + 1;
     }
     if (lane == 0) {
-        for (int s = 0; s < kEStages; s++)
+        for (int s = 0; s < S; s++)
             if (issued > (uint32_t)s) {
-                uint32_t fills = (issued - 1 - s) / kEStages + 1;
+                uint32_t fills = (issued - 1 - s) / S + 1;
                 mbar_wait_bounded(&P.full[s], (fills - 1) & 1u, kBPolls);
             }
     }
@@ -1006,15 +1018,16 @@ __device__ void benc_produce(const BatchEncArgs &a, EPipe &P, int lane)
 // tiles come in order to one CTA, so its data offset is a running sum: the
 // eight warps trade their sub-tile sizes once per tile (one barrier) and each
 // keeps the running offset and the list's last integer itself.
-__device__ void benc_consume(const BatchEncArgs &a, EPipe &P, uint32_t (*s_size)[kWarps])
+template <int S>
+__device__ void benc_consume(const BatchEncArgs &a, EPipe<S> &P, uint32_t (*s_size)[kWarps])
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t sq0 = warp * kSubQuads;
     u64 run = 0;          // data bytes of the current list written so far
     uint32_t before = 0;  // the list's integer before the current tile (differential)
     for (uint32_t g = 0;; g++) {
-        const int s = g % kEStages;
-        if (!mbar_wait_bounded(&P.full[s], (g / kEStages) & 1u, kBPolls)) {
+        const int s = g % S;
+        if (!mbar_wait_bounded(&P.full[s], (g / S) & 1u, kBPolls)) {
             raise_error(a.hdr, kErrTimeout);
             break;
         }
@@ -1141,15 +1154,16 @@ __device__ void benc_small(const BatchEncArgs &a, uint32_t li, int lane)
     }
 }
 
-__global__ void __launch_bounds__(kBBlock, 3) batch_encode_kernel(BatchEncArgs a)
+template <int S, int kMinCtas>
+__global__ void __launch_bounds__(kBBlock, kMinCtas) batch_encode_kernel(BatchEncArgs a)
 {
     extern __shared__ __align__(128) uint8_t dyn_smem[];
-    EPipe &P = *reinterpret_cast<EPipe *>(dyn_smem);
+    EPipe<S> &P = *reinterpret_cast<EPipe<S> *>(dyn_smem);
     __shared__ uint32_t s_size[2][kWarps];   // sub-tile data bytes, per tile parity
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
-        for (int s = 0; s < kEStages; s++) {
+        for (int s = 0; s < S; s++) {
             mbar_init(&P.full[s], 32);
             mbar_init(&P.empty[s], kWarps);
         }
@@ -1157,9 +1171,9 @@ __global__ void __launch_bounds__(kBBlock, 3) batch_encode_kernel(BatchEncArgs a
     }
     __syncthreads();
     if (warp == kWarps)
-        benc_produce(a, P, lane);
+        benc_produce<S>(a, P, lane);
     else
-        benc_consume(a, P, s_size);
+        benc_consume<S>(a, P, s_size);
 
     const uint32_t *small = plan_small(a.plan);
     const uint32_t nsmall = a.plan->nsmall;
@@ -1188,13 +1202,58 @@ static int persistent_grid(K kernel, size_t smem)
     return (sms > 0 ? sms : 148) * (occ > 0 ? occ : 1);
 }
 
+// Staging depths the batched kernels are built with, and the one each uses
+// (0: the default, set by svb_batch_set_stages).
+static std::atomic<int> g_dec_stages{0}, g_enc_stages{0};
+constexpr int kDecStagesDefault = 2, kEncStagesDefault = 3;
+
+int batch_set_stages(int decode_stages, int encode_stages)
+{
+    const bool dec_ok = decode_stages == 0 || (decode_stages >= 2 && decode_stages <= 4);
+    const bool enc_ok = encode_stages == 0 || encode_stages == 2 || encode_stages == 3;
+    if (!dec_ok || !enc_ok)
+        return 1;
+    g_dec_stages.store(decode_stages, std::memory_order_relaxed);
+    g_enc_stages.store(encode_stages, std::memory_order_relaxed);
+    return 0;
+}
+
+int batch_stages(int encode)
+{
+    const int v = (encode ? g_enc_stages : g_dec_stages).load(std::memory_order_relaxed);
+    return v ? v : (encode ? kEncStagesDefault : kDecStagesDefault);
+}
+
+// One instantiation of the decode kernel: S stages, at least kMinCtas CTAs
+// per SM (the register cap that lets that many fit).
+template <int S, int kMinCtas>
+static void launch_bdec(const BatchDecArgs &a, int grid, cudaStream_t stream)
+{
+    static int g = 0;
+    if (!g)
+        g = persistent_grid(batch_decode_kernel<S, kMinCtas>, sizeof(BPipe<S>));
+    prof_begin("batch_decode_kernel", stream);
+    batch_decode_kernel<S, kMinCtas>
+        <<<grid > 0 ? grid : g, kBBlock, sizeof(BPipe<S>), stream>>>(a);
+    prof_end(stream);
+}
+
+template <int S, int kMinCtas>
+static void launch_benc(const BatchEncArgs &a, int grid, cudaStream_t stream)
+{
+    static int g = 0;
+    if (!g)
+        g = persistent_grid(batch_encode_kernel<S, kMinCtas>, sizeof(EPipe<S>));
+    prof_begin("batch_encode_kernel", stream);
+    batch_encode_kernel<S, kMinCtas>
+        <<<grid > 0 ? grid : g, kBBlock, sizeof(EPipe<S>), stream>>>(a);
+    prof_end(stream);
+}
+
 int launch_batch_decode(const void *d_plan, const svb_list *d_lists, const uint8_t *in,
                         uint32_t *out, bool delta, void *ws, DeviceResult *result,
                         cudaStream_t stream, int grid)
 {
-    static int g = 0;
-    if (!g)
-        g = persistent_grid(batch_decode_kernel, sizeof(BPipe));
     BatchDecArgs a;
     a.lists = d_lists;
     a.plan = static_cast<const PlanHeader *>(d_plan);
@@ -1221,9 +1280,17 @@ int launch_batch_decode(const void *d_plan, const svb_list *d_lists, const uint8
     prof_begin("batch_prep_kernel", stream);
     batch_prep_kernel<<<pg, kThreads, 0, stream>>>(pa);
     prof_end(stream);
-    prof_begin("batch_decode_kernel", stream);
-    batch_decode_kernel<<<grid > 0 ? grid : g, kBBlock, sizeof(BPipe), stream>>>(a);
-    prof_end(stream);
+    switch (batch_stages(0)) {
+    case 4:
+        launch_bdec<4, 3>(a, grid, stream);
+        break;
+    case 3:
+        launch_bdec<3, 4>(a, grid, stream);
+        break;
+    default:
+        launch_bdec<2, 4>(a, grid, stream);
+        break;
+    }
     return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
 
@@ -1231,9 +1298,6 @@ int launch_batch_encode(const void *d_plan, const svb_list *d_lists, const uint3
                         uint8_t *out, u64 *sizes, bool delta, void *ws, DeviceResult *result,
                         cudaStream_t stream, int grid)
 {
-    static int g = 0;
-    if (!g)
-        g = persistent_grid(batch_encode_kernel, sizeof(EPipe));
     BatchEncArgs a;
     a.lists = d_lists;
     a.plan = static_cast<const PlanHeader *>(d_plan);
@@ -1243,9 +1307,10 @@ int launch_batch_encode(const void *d_plan, const svb_list *d_lists, const uint3
     a.hdr = static_cast<WsHeader *>(ws);
     a.result = result;
     a.delta = delta ? 1u : 0u;
-    prof_begin("batch_encode_kernel", stream);
-    batch_encode_kernel<<<grid > 0 ? grid : g, kBBlock, sizeof(EPipe), stream>>>(a);
-    prof_end(stream);
+    if (batch_stages(1) == 2)
+        launch_benc<2, 4>(a, grid, stream);
+    else
+        launch_benc<3, 3>(a, grid, stream);
     return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
 

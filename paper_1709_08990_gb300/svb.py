@@ -74,6 +74,8 @@ def lib() -> ctypes.CDLL:
             "svb_batch_plan": ([vp, sz, u32, vp, sz, vp], i32),
             "svb_batch_plan_segments": ([vp, sz, u32, u32, vp, sz, vp], i32),
             "svb_batch_workspace_size": ([], sz),
+            "svb_batch_set_stages": ([i32, i32], i32),
+            "svb_batch_get_stages": ([i32], i32),
             "svb_batch_decode": ([vp, vp, vp, vp, i32, vp, vp, sz, i32, vp], i32),
             "svb_batch_encode": ([vp, vp, vp, vp, i32, vp, vp, vp, sz, i32, vp], i32),
             "svb_decode_each": ([vp, sz, vp, vp, i32, vp, vp, sz, vp], i32),
@@ -229,6 +231,14 @@ def svb_batch_plan_segments(h_lists, num_lists: int, big_threshold: int, segment
                             d_plan, plan_bytes: int, stream=None) -> int:
     return lib().svb_batch_plan_segments(_p(h_lists), num_lists, big_threshold, segment_tiles,
                                          _p(d_plan), plan_bytes, _stream(stream))
+
+
+def svb_batch_set_stages(decode_stages: int, encode_stages: int) -> int:
+    return lib().svb_batch_set_stages(decode_stages, encode_stages)
+
+
+def svb_batch_get_stages(encode: int) -> int:
+    return lib().svb_batch_get_stages(encode)
 
 
 def svb_batch_workspace_size() -> int:

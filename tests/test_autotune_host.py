@@ -1,7 +1,8 @@
 """The batched codec's autotuner without a GPU: the candidates are timed
-through a stand-in, the fastest (threshold, grid, segment_tiles) is kept,
-written to the JSON cache under the GPU name and workload with the kernel's
-fixed geometry, and reused on the next call."""
+through a stand-in, the fastest (threshold, grid, segment_tiles, staging
+depth, encoder staging depth) is kept, written to the JSON cache under the
+GPU name and workload with the kernels' fixed geometry, and reused, staging
+depths included, on the next call."""
 from __future__ import annotations
 
 import json
@@ -13,11 +14,14 @@ from paper_1709_08990_gb300 import autotune  # noqa: E402
 
 
 class FakePool:
-    """Records replan() calls; decode() is timed by the stand-in below."""
+    """Records replan() calls; decode() and encode() are timed by the
+    stand-in below."""
 
     def __init__(self):
         self.plans = []
         self.current = None
+        self.segments = None
+        self.op = None
 
     def replan(self, threshold, grid, segment_tiles=None):
         self.current = (threshold, grid)
@@ -25,7 +29,10 @@ class FakePool:
         self.plans.append((threshold, grid))
 
     def decode(self, out):
-        pass
+        self.op = "decode"
+
+    def encode(self, out):
+        self.op = "encode"
 
 
 @pytest.fixture
@@ -33,56 +40,94 @@ def tuner(tmp_path, monkeypatch):
     cache = tmp_path / "cache.json"
     monkeypatch.setattr(autotune, "CACHE", str(cache))
     cost = {}
+    stages = {"dec": 0, "enc": 0, "calls": []}
+
+    def fake_set(dec, enc):
+        stages["dec"], stages["enc"] = dec, enc
+        stages["calls"].append((dec, enc))
 
     def fake_time(fn, reps):
         fn()
+        if pool.op == "encode":
+            return cost.get(("enc", stages["enc"]), 4.0)
         c = cost[pool.current]
-        seg = getattr(pool, "segments", None)
-        return c - (0.5 if seg == 16 and (pool.current, "seg16") in cost else 0.0)
+        if pool.segments == 16 and (pool.current, "seg16") in cost:
+            c -= 0.5
+        return c - cost.get(("dec", stages["dec"]), 0.0)
 
     pool = FakePool()
     monkeypatch.setattr(autotune, "_time_ms", fake_time)
-    return pool, cost, cache
+    monkeypatch.setattr(autotune, "_set_stages", fake_set)
+    return pool, cost, cache, stages
 
 
 def test_picks_the_fastest_and_caches_it(tuner):
-    pool, cost, cache = tuner
+    pool, cost, cache, stages = tuner
     for thr in (2048, 8192):
         for grid in (0, 152):
             cost[(thr, grid)] = 5.0
     cost[(8192, 152)] = 1.5
     cost[((8192, 152), "seg16")] = True
+    cost[("dec", 3)] = 0.25   # three stages shave 0.25 ms
+    cost[("enc", 2)] = 3.0    # the encoder is fastest with two
     e = autotune.tune_batch(pool, "lists_test", None, thresholds=(2048, 8192), grids=(0, 152),
-                            segments=(0, 16))
+                            segments=(0, 16), stages=(2, 3, 4), enc_out=object())
     assert (e["threshold"], e["grid"], e["segment_tiles"], e["cached"]) == (8192, 152, 16, False)
-    assert len(e["trials"]) == 6 and pool.current == (8192, 152) and pool.segments == 16
+    assert (e["stages"], e["encode_stages"]) == (3, 2)
+    assert len(e["trials"]) == 9 and len(e["encode_trials"]) == 2
+    assert pool.current == (8192, 152) and pool.segments == 16
+    assert (stages["dec"], stages["enc"]) == (3, 2)   # the library is left at the winner
     d = json.load(open(cache))
     key = autotune._key("batch_decode", "lists_test")
     assert d[key]["threshold"] == 8192 and d[key]["grid"] == 152
-    assert d[key]["segment_tiles"] == 16
-    assert set(d[key]["geometry"]) == {"tile_ints", "warp_ints", "lane_ints", "stages"}
+    assert d[key]["segment_tiles"] == 16 and d[key]["stages"] == 3
+    assert d[key]["encode_stages"] == 2
+    assert set(d[key]["geometry"]) == {"tile_ints", "warp_ints", "lane_ints"}
 
 
 def test_second_call_reuses_the_cache_and_force_retunes(tuner):
-    pool, cost, cache = tuner
-    cost.update({(4096, 0): 2.0, (4096, 76): 3.0})
-    autotune.tune_batch(pool, "w", None, thresholds=(4096,), grids=(0, 76), segments=())
+    pool, cost, cache, stages = tuner
+    cost.update({(4096, 0): 2.0, (4096, 76): 3.0, ("dec", 4): 0.1})
+    autotune.tune_batch(pool, "w", None, thresholds=(4096,), grids=(0, 76), segments=(),
+                        stages=(2, 4))
     pool.plans.clear()
+    stages["calls"].clear()
     cost.update({(4096, 0): 9.0})  # would change the choice if timed again
     e = autotune.tune_batch(pool, "w", None, thresholds=(4096,), grids=(0, 76), segments=())
-    assert e["cached"] and (e["threshold"], e["grid"]) == (4096, 0)
+    assert e["cached"] and (e["threshold"], e["grid"], e["stages"]) == (4096, 0, 4)
     assert pool.plans == [(4096, 0)]  # replanned straight from the cache
+    assert stages["calls"] == [(4, 0)]  # and the cached staging depth set
     e = autotune.tune_batch(pool, "w", None, thresholds=(4096,), grids=(0, 76), segments=(),
-                            force=True)
+                            stages=(2, 4), force=True)
     assert not e["cached"] and e["grid"] == 76
 
 
 def test_entries_of_other_workloads_survive_and_a_bad_cache_reads_as_empty(tuner):
-    pool, cost, cache = tuner
+    pool, cost, cache, stages = tuner
     cost.update({(1, 0): 1.0})
-    autotune.tune_batch(pool, "a", None, thresholds=(1,), grids=(0,), segments=(0,))
-    autotune.tune_batch(pool, "b", None, thresholds=(1,), grids=(0,), segments=(0,))
+    autotune.tune_batch(pool, "a", None, thresholds=(1,), grids=(0,), segments=(0,), stages=(2,))
+    autotune.tune_batch(pool, "b", None, thresholds=(1,), grids=(0,), segments=(0,), stages=(2,))
     d = json.load(open(cache))
     assert autotune._key("batch_decode", "a") in d and autotune._key("batch_decode", "b") in d
     cache.write_text("{not json")
     assert autotune.lookup("batch_decode", "a") is None
+
+
+def test_stage_setter_rejects_depths_that_are_not_built():
+    svb = pytest.importorskip("paper_1709_08990_gb300.svb")
+    try:
+        svb.lib()
+    except RuntimeError:
+        pytest.skip("libsvb.so not built")
+    try:
+        for dec, enc in ((1, 0), (5, 0), (0, 1), (0, 4), (-1, 0)):
+            assert svb.svb_batch_set_stages(dec, enc) == svb.SVB_EINVAL
+        assert svb.svb_batch_get_stages(0) == 2 and svb.svb_batch_get_stages(1) == 3
+        for dec in (2, 3, 4):
+            for enc in (2, 3):
+                assert svb.svb_batch_set_stages(dec, enc) == svb.SVB_OK
+                assert (svb.svb_batch_get_stages(0), svb.svb_batch_get_stages(1)) == (dec, enc)
+        assert svb.svb_batch_set_stages(9, 9) == svb.SVB_EINVAL
+        assert (svb.svb_batch_get_stages(0), svb.svb_batch_get_stages(1)) == (4, 3)
+    finally:
+        svb.svb_batch_set_stages(0, 0)

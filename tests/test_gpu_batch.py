@@ -304,3 +304,39 @@ def test_segmented_plan_rejects_bad_arguments():
     assert svb.svb_batch_plan_segments(lists, 3, 0, 33, d, nb) == svb.SVB_EINVAL
     assert svb.svb_batch_plan_segments(lists, 3, 0, 4, d[1:], nb) == svb.SVB_EINVAL
     assert svb.svb_batch_plan_segments(lists, 3, 0, 4, d, nb) == svb.SVB_OK
+
+
+@pytest.fixture
+def staging():
+    """Sets the batched kernels' staging depths for one test, then restores
+    the defaults."""
+    def set_(dec, enc):
+        assert svb.svb_batch_set_stages(dec, enc) == 0
+    yield set_
+    svb.svb_batch_set_stages(0, 0)
+
+
+@pytest.mark.parametrize("stages", [2, 3, 4])
+@pytest.mark.parametrize("delta", [False, True])
+def test_batch_decode_every_staging_depth(stages, delta, staging):
+    """Each built depth of the decode kernel, whole lists and split ones."""
+    staging(stages, 0)
+    b = Batch(LENGTHS + [70_001, 131_073], delta, seed=11,
+              prevs=[(53 * j) & 0xFFFF for j in range(len(LENGTHS) + 2)], gap_bytes=3)
+    for seg in (None, 0, 2):
+        got, r = batch_decode(b, threshold=16, segment_tiles=seg, repeat=2)
+        assert r[1] == 0 and r[0] == sum(s.size for s in b.streams)
+        assert np.array_equal(got, b.all_values), f"stages {stages}, segment_tiles {seg}"
+
+
+@pytest.mark.parametrize("stages", [2, 3])
+@pytest.mark.parametrize("delta", [False, True])
+def test_batch_encode_every_staging_depth(stages, delta, staging):
+    staging(0, stages)
+    b = Batch(LENGTHS + [70_001], delta, seed=12,
+              prevs=[(29 * j) & 0xFFFF for j in range(len(LENGTHS) + 1)])
+    out, sizes, r = batch_encode(b, threshold=16)
+    assert r[1] == 0 and r[0] == sum(s.size for s in b.streams)
+    for j, s in enumerate(b.streams):
+        off = int(b.enc_lists[j]["out_off"])
+        assert np.array_equal(out[off:off + s.size], s), f"stages {stages}, list {j}"
