@@ -541,10 +541,19 @@ __device__ void bdec_consume(const BatchDecArgs &a, BPipe<S> &P, uint16_t *s_pos
         }
         if (!have)
             continue;
-        uint32_t *op = a.out + out_off + 4 * (u64)(q0 + lane);
+        uint32_t *base = a.out + out_off + 4 * (u64)q0;
+        uint32_t *op = base + 4 * lane;
         const bool aligned = ((uintptr_t)(a.out + out_off) & 15u) == 0;
+        const uint32_t m = (uint32_t)((uintptr_t)base >> 2) & 3u;
 #pragma unroll
         for (int r = 0; r < kSubRounds; r++) {
+            // Most lists start at an integer that is not 16-byte aligned: a
+            // whole round of 32 quads still goes out in 16-byte writes.
+            if (!aligned && subtile_nints(t, 32u * r + 31u) == 4u) {
+                stg_round_realigned(base + 128 * r, make_uint4(v[r][0], v[r][1], v[r][2], v[r][3]),
+                                    m);
+                continue;
+            }
             const uint32_t lq = r * 32 + lane;
             const uint32_t nints = subtile_nints(t, lq);
             if (!nints)
@@ -1048,11 +1057,14 @@ __device__ void benc_consume(const BatchEncArgs &a, EPipe<S> &P, uint32_t (*s_si
         const uint32_t *V = reinterpret_cast<const uint32_t *>(P.vals[s] + P.hv[s]);
         const uint32_t nvq = nq > sq0 ? min(nq - sq0, (uint32_t)kSubQuads) : 0u;
         const uint32_t tail = q0 + nq == nql ? last_nints : 4u;
-        const bool fast = P.hv[s] == 0 && 4 * (sq0 + kSubQuads) <= cnt;
+        const bool fast = 4 * (sq0 + kSubQuads) <= cnt;   // a whole sub-tile
         uint32_t nints[kEncRounds], d[kEncRounds][4], ctrl[kEncRounds], cb[kEncRounds];
         auto prior = [&]() { return before; };
-        if (fast)
+        if (fast && P.hv[s] == 0)
             subenc_load<true>(V, sq0, nq, tail, a.delta != 0, prior, nints, d, ctrl, cb);
+        else if (fast)   // the list's values start 4, 8 or 12 bytes past a 16-byte boundary
+            subenc_load<true, decltype(prior), false, false>(V, sq0, nq, tail, a.delta != 0, prior,
+                                                            nints, d, ctrl, cb);
         else
             subenc_load<false>(V, sq0, nq, tail, a.delta != 0, prior, nints, d, ctrl, cb);
         const uint32_t tile_last = V[cnt - 1];

@@ -145,6 +145,45 @@ __device__ __forceinline__ void stg_stream128(void *p, uint4 v)
                  : "memory");
 }
 
+// One round of a warp's decoded quads (lane l: the four integers of quad l,
+// bound for dst + 4l) stored with 16-byte writes although dst is only 4-byte
+// aligned: m = (dst / 4) mod 4 in {1, 2, 3}.  The aligned chunk that ends
+// with lane l's first 4 - m integers takes its first m from lane l - 1 (one
+// shuffle per integer); lane 0 writes its first 4 - m integers and lane 31
+// its last m one by one, which the neighbouring rounds' chunks leave out.
+// Every lane of the warp must call it, with the same dst and m.
+__device__ __forceinline__ void stg_round_realigned(uint32_t *dst, uint4 v, uint32_t m)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t p1 = __shfl_up_sync(0xffffffffu, v.y, 1);
+    const uint32_t p2 = __shfl_up_sync(0xffffffffu, v.z, 1);
+    const uint32_t p3 = __shfl_up_sync(0xffffffffu, v.w, 1);
+    uint32_t *own = dst + 4 * lane;
+    uint4 c;
+    if (m == 1)
+        c = make_uint4(p3, v.x, v.y, v.z);
+    else if (m == 2)
+        c = make_uint4(p2, p3, v.x, v.y);
+    else
+        c = make_uint4(p1, p2, p3, v.x);
+    if (lane > 0)
+        stg_stream128(own - m, c);
+    if (lane == 0) {
+        own[0] = v.x;
+        if (m < 3)
+            own[1] = v.y;
+        if (m < 2)
+            own[2] = v.z;
+    }
+    if (lane == 31) {
+        own[3] = v.w;
+        if (m > 1)
+            own[2] = v.z;
+        if (m > 2)
+            own[1] = v.y;
+    }
+}
+
 __device__ __forceinline__ void raise_error(WsHeader *h, u64 code)
 {
     atomicCAS(&h->error, 0ull, code);

@@ -47,11 +47,12 @@ __device__ __forceinline__ void shl128(uint32_t &s0, uint32_t &s1, uint32_t &s2,
 // quad nq - 1 (4 unless it ends the stream).  For differential coding,
 // before() gives the integer preceding the tile (called by lane 0 only, when
 // sq0 == 0; otherwise the preceding integer is V[4 * sq0 - 1]).  kFast: all
-// 128 quads hold 4 integers and V is 16-byte aligned.  Out: per round the
+// 128 quads hold 4 integers.  kAligned: V is 16-byte aligned (a quad is one
+// 16-byte load; else four 4-byte loads).  Out: per round the
 // integers of the lane's quad (0 past the end), the coded values (0 past the
 // end), the control byte (left 0 with kSizeOnly, when only sizes are
 // needed) and the quad's data bytes.
-template <bool kFast, class Before>
+template <bool kFast, class Before, bool kAligned = true>
 __device__ __forceinline__ void subenc_values(const uint32_t *V, uint32_t sq0, uint32_t nq,
                                               uint32_t tail, bool delta, Before before,
                                               uint32_t (&nints)[kEncRounds],
@@ -63,7 +64,9 @@ __device__ __forceinline__ void subenc_values(const uint32_t *V, uint32_t sq0, u
         const uint32_t lq = sq0 + 32 * r + lane;
         nints[r] = kFast ? 4u : (lq >= nq ? 0u : (lq == nq - 1 ? tail : 4u));
         if (kFast) {
-            const uint4 v = *reinterpret_cast<const uint4 *>(V + 4 * lq);
+            const uint4 v = kAligned
+                ? *reinterpret_cast<const uint4 *>(V + 4 * lq)
+                : make_uint4(V[4 * lq], V[4 * lq + 1], V[4 * lq + 2], V[4 * lq + 3]);
             d[r][0] = v.x;
             d[r][1] = v.y;
             d[r][2] = v.z;
@@ -116,7 +119,7 @@ __device__ __forceinline__ void subenc_lengths(const uint32_t (&nints)[kEncRound
     }
 }
 
-template <bool kFast, class Before, bool kSizeOnly = false>
+template <bool kFast, class Before, bool kSizeOnly = false, bool kAligned = true>
 __device__ __forceinline__ void subenc_load(const uint32_t *V, uint32_t sq0, uint32_t nq,
                                             uint32_t tail, bool delta, Before before,
                                             uint32_t (&nints)[kEncRounds],
@@ -124,7 +127,7 @@ __device__ __forceinline__ void subenc_load(const uint32_t *V, uint32_t sq0, uin
                                             uint32_t (&ctrl)[kEncRounds],
                                             uint32_t (&cb)[kEncRounds])
 {
-    subenc_values<kFast>(V, sq0, nq, tail, delta, before, nints, d);
+    subenc_values<kFast, Before, kAligned>(V, sq0, nq, tail, delta, before, nints, d);
     subenc_lengths<kSizeOnly>(nints, d, ctrl, cb);
 }
 
