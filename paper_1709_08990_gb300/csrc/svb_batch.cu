@@ -574,8 +574,39 @@ __device__ void bdec_consume(const BatchDecArgs &a, BPipe<S> &P, uint16_t *s_pos
     }
 }
 
-// One small list, decoded by one warp straight from global memory.
-__device__ void bdec_small(const BatchDecArgs &a, uint32_t li, int lane)
+// Data bytes of a sub-tile from its control word w (every lane): four quads
+// per lane (Sec. 4: a control byte covers 4 + the sum of its codes bytes;
+// the pad fields of the last quad cover none).
+__device__ __forceinline__ uint32_t subtile_bytes(const SubTile &t, uint32_t w)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t c = 0;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const uint32_t nints = subtile_nints(t, 4u * lane + j);
+        uint32_t b = (w >> (8 * j)) & 0xffu;
+        if (nints < 4)
+            b &= (1u << (2 * nints)) - 1u;
+        c += nints ? quad_count(b, nints) : 0u;
+    }
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1)
+        c += __shfl_xor_sync(0xffffffffu, c, d);
+    return c;
+}
+
+// Shared memory one warp uses for a small list: a staged sub-tile's data
+// bytes (16-byte phase, 2048 bytes, round-up and read slack) and its quad
+// positions.
+constexpr int kSmallData = 16 * kSubQuads + 48;
+constexpr int kSmallSlot = kSmallData + 2 * kSubQuads;
+
+// One small list, decoded by one warp, 128 quads (512 integers) at a time:
+// the piece's data bytes are staged into the warp's slot by cp.async (bytes
+// of the list's stream only), decoded with the sub-tile code and stored
+// with 16-byte writes (realigned where the list starts off a 16-byte
+// boundary); differential lists keep a running carry.
+__device__ void bdec_small(const BatchDecArgs &a, uint32_t li, int lane, uint8_t *slot)
 {
     const svb_list L = a.lists[li];
     const uint32_t n = L.n, nq = (n + 3) / 4;
@@ -587,54 +618,75 @@ __device__ void bdec_small(const BatchDecArgs &a, uint32_t li, int lane)
     }
     const uint8_t *data = base + nq;
     const u64 dcap = L.in_len - nq;  // data bytes the stream may use
+    const uintptr_t lo = (uintptr_t)base, hi = (uintptr_t)(base + L.in_len);
+    const uint32_t last_nints = n - 4 * (nq - 1);
+    uint32_t *out = a.out + L.out_off;
+    const bool aligned = ((uintptr_t)out & 15u) == 0;
+    const uint32_t m = (uint32_t)((uintptr_t)out >> 2) & 3u;
+    const uint64_t policy = l2_policy_evict_first();
+    uint16_t *pos = reinterpret_cast<uint16_t *>(slot + kSmallData);
     u64 running = 0;
     uint32_t carry = L.prev;
-    for (uint32_t q0 = 0; q0 < nq; q0 += 32) {
-        const uint32_t q = q0 + lane;
-        const bool valid = q < nq;
-        uint32_t c = valid ? __ldg(base + q) : 0u;
-        const uint32_t nints = !valid ? 0u : (q == nq - 1 ? n - 4 * q : 4u);
-        if (nints < 4)
-            c &= (1u << (2 * nints)) - 1u;
-        const uint32_t C = valid ? quad_count(c, nints) : 0u;
-        const uint32_t incl = warp_incl_scan(C);
-        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    for (uint32_t q0 = 0; q0 < nq; q0 += kSubQuads) {
+        SubTile t;
+        t.C = base + q0;   // read in place (global memory)
+        t.D = slot;
+        t.nq = min((uint32_t)kSubQuads, nq - q0);
+        t.tail = q0 + t.nq == nq ? last_nints : 4u;
+        const uint32_t w = subtile_ctrl_word(t);
+        const uint32_t total = subtile_bytes(t, w);
         if (running + total > dcap) {
             if (lane == 0)
                 raise_error(a.hdr, kErrTruncated);
             return;
         }
-        const uint8_t *p = data + running + (incl - C);
-        uint32_t x[4] = {0, 0, 0, 0};
+        const uint8_t *g = data + running;
+        t.base = (uint32_t)((uintptr_t)g & 15u);
+        warp_stage(g, total, slot, lo, hi, policy);
+        cp_async_commit();
+        subtile_positions(t, w, pos);
+        cp_async_wait<0>();
+        __syncwarp();
+        uint32_t v[kSubRounds][4];
+        subtile_gather(t, pos, v);
+        if (a.delta) {
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-            if ((uint32_t)j < nints) {
-                const uint32_t code = (c >> (2 * j)) & 3u;
-                uint32_t val = 0;
+            for (int r = 0; r < kSubRounds; r++) {
+                v[r][1] += v[r][0];
+                v[r][2] += v[r][1];
+                v[r][3] += v[r][2];
+                const uint32_t qs = v[r][3];
+                const uint32_t inc = warp_incl_scan(qs);
+                const uint32_t add = carry + inc - qs;
 #pragma unroll
-                for (uint32_t b = 0; b < 4; b++)
-                    if (b <= code)
-                        val |= (uint32_t)__ldg(p + b) << (8 * b);
-                x[j] = val;
-                p += code + 1;
+                for (int j = 0; j < 4; j++)
+                    v[r][j] += add;
+                carry += __shfl_sync(0xffffffffu, inc, 31);
             }
         }
-        if (a.delta) {
-            x[1] += x[0];
-            x[2] += x[1];
-            x[3] += x[2];
-            const uint32_t qi = warp_incl_scan(x[3]);
-            const uint32_t add = carry + qi - x[3];
+        __syncwarp();  // the slot and pos are read before the next piece is staged
+        uint32_t *op = out + 4 * q0;
 #pragma unroll
-            for (int j = 0; j < 4; j++)
-                x[j] += add;
-            carry += __shfl_sync(0xffffffffu, qi, 31);
+        for (int r = 0; r < kSubRounds; r++) {
+            const bool whole = subtile_nints(t, 32u * r + 31u) == 4u;
+            const uint4 x = make_uint4(v[r][0], v[r][1], v[r][2], v[r][3]);
+            if (whole && aligned) {
+                stg_stream128(op + 128 * r + 4 * lane, x);
+            } else if (whole) {
+                stg_round_realigned(op + 128 * r, x, m);
+            } else {
+                const uint32_t nints = subtile_nints(t, 32u * r + lane);
+                uint32_t *dst = op + 128 * r + 4 * lane;
+                if (nints > 0)
+                    dst[0] = x.x;
+                if (nints > 1)
+                    dst[1] = x.y;
+                if (nints > 2)
+                    dst[2] = x.z;
+                if (nints > 3)
+                    dst[3] = x.w;
+            }
         }
-        uint32_t *dst = a.out + L.out_off + 4 * (u64)q;
-#pragma unroll
-        for (int j = 0; j < 4; j++)
-            if ((uint32_t)j < nints)
-                dst[j] = x[j];
         running += total;
     }
     if (lane == 0)
@@ -900,7 +952,12 @@ __global__ void __launch_bounds__(kBBlock, kMinCtas) batch_decode_kernel(BatchDe
     else
         bdec_consume<S>(a, P, s_pos, s_sum);
 
-    // Small lists: every warp takes them one by one.
+    // Small lists: every warp takes them one by one, staging their pieces in
+    // a slot of its own carved from the data stages, which the big-list
+    // phase no longer uses once every warp is past it.
+    static_assert((kBBlock / 32) * kSmallSlot <= (int)sizeof(P.data), "small-list slots fit");
+    __syncthreads();
+    uint8_t *slot = &P.data[0][0] + warp * kSmallSlot;
     const uint32_t *small = plan_small(a.plan);
     const uint32_t nsmall = a.plan->nsmall;
     for (;;) {
@@ -910,7 +967,7 @@ __global__ void __launch_bounds__(kBBlock, kMinCtas) batch_decode_kernel(BatchDe
         j = __shfl_sync(0xffffffffu, j, 0);
         if (j >= nsmall)
             break;
-        bdec_small(a, small[j], lane);
+        bdec_small(a, small[j], lane, slot);
     }
     finish_launch(a.hdr, a.result);
 }
