@@ -129,9 +129,11 @@ const char *svb_error_string(int status);
 void svb_set_spin_limit(uint64_t iterations);
 
 /* Decoder variant used by every decode call of this process:
- *   SVB_DECODE_AUTO (0)        the default: SVB_DECODE_SINGLE_PASS for plain
- *                              streams of at most 2^20 integers (launch-
- *                              bound), SVB_DECODE_TWO_PASS otherwise;
+ *   SVB_DECODE_AUTO (0)        the default: SVB_DECODE_SMALL for plain
+ *                              streams of at most 2^22 integers whose tiles
+ *                              can all be resident (launch-bound sizes),
+ *                              else SVB_DECODE_SINGLE_PASS up to 2^20
+ *                              integers and SVB_DECODE_TWO_PASS above;
  *   SVB_DECODE_SINGLE_PASS (1) one kernel: each tile sums its control bytes,
  *                              finds its data offset by a decoupled look-back
  *                              over its predecessors, then decodes;
@@ -142,18 +144,30 @@ void svb_set_spin_limit(uint64_t iterations);
  *                              into its carry-in;
  *   SVB_DECODE_SUMS_PASS (3)   as SVB_DECODE_TWO_PASS, but differential
  *                              streams learn their carry-ins from a separate
- *                              pass over the staged tiles (three launches).
+ *                              pass over the staged tiles (three launches);
+ *   SVB_DECODE_SMALL (4)       plain streams: one cooperative launch, one CTA
+ *                              per 4096-integer tile, a grid barrier between
+ *                              the tiles' byte totals and the decode; where
+ *                              the tiles cannot all be resident at once, or
+ *                              the stream is being captured into a graph,
+ *                              the decode runs as SVB_DECODE_AUTO would run
+ *                              it (single pass up to 2^20 integers, else two
+ *                              pass).  Differential streams as
+ *                              SVB_DECODE_TWO_PASS.
  * All give identical results.  Returns SVB_EINVAL for an unknown variant. */
 enum svb_decode_variant {
     SVB_DECODE_AUTO = 0,
     SVB_DECODE_SINGLE_PASS = 1,
     SVB_DECODE_TWO_PASS = 2,
-    SVB_DECODE_SUMS_PASS = 3
+    SVB_DECODE_SUMS_PASS = 3,
+    SVB_DECODE_SMALL = 4
 };
 int svb_set_decode_variant(int variant);
 
 /* Encoder variant used by every encode call of this process:
- *   SVB_ENCODE_AUTO (0)           the default, currently SVB_ENCODE_CHUNKED;
+ *   SVB_ENCODE_AUTO (0)           the default: SVB_ENCODE_SMALL for arrays
+ *                                 of at most 2^22 integers whose tiles can
+ *                                 all be resident, else SVB_ENCODE_CHUNKED;
  *   SVB_ENCODE_TILE_LOOKBACK (1)  one CTA per tile of 4096 integers, which
  *                                 finds its data offset by a look-back over
  *                                 its predecessors' byte totals;
@@ -161,11 +175,19 @@ int svb_set_decode_variant(int variant);
  *                                 integers: a sizing pass, one look-back per
  *                                 chunk, then a writing pass whose second
  *                                 read of the values is served by L2.
- * Both give identical streams.  Returns SVB_EINVAL for an unknown variant. */
+ *   SVB_ENCODE_SMALL (3)          one cooperative launch, one CTA per
+ *                                 4096-integer tile: each sizes its values,
+ *                                 a grid barrier, then each writes them at
+ *                                 the offset the earlier tiles' totals give
+ *                                 (the values read once); where the tiles
+ *                                 cannot all be resident, or the stream is
+ *                                 being captured, SVB_ENCODE_CHUNKED runs.
+ * All give identical streams.  Returns SVB_EINVAL for an unknown variant. */
 enum svb_encode_variant {
     SVB_ENCODE_AUTO = 0,
     SVB_ENCODE_TILE_LOOKBACK = 1,
-    SVB_ENCODE_CHUNKED = 2
+    SVB_ENCODE_CHUNKED = 2,
+    SVB_ENCODE_SMALL = 3
 };
 int svb_set_encode_variant(int variant);
 

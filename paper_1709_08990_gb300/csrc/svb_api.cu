@@ -25,6 +25,7 @@ std::atomic<int> g_encode_variant{SVB_ENCODE_AUTO};
 
 constexpr u64 kDefaultSpinLimit = 1ull << 21;  // ~2 s of polling at most
 constexpr u64 kSmallPlain = 1ull << 20;         // plain streams decoded in one launch
+constexpr u64 kSmallArray = 1ull << 22;         // arrays tried with the one-launch kernels
 
 u64 spin_limit()
 {
@@ -48,8 +49,14 @@ int decode_dispatch(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, uint32_
 {
     const int v = g_decode_variant.load(std::memory_order_relaxed);
     // Small plain streams are launch-bound: one launch beats the offsets pass
-    // plus the tiled decode there (17.5 against 20.3 us at 2^20 integers).
-    if (v == SVB_DECODE_SINGLE_PASS || (v == SVB_DECODE_AUTO && !delta && n <= kSmallPlain))
+    // plus the tiled decode there.  The one-launch small-array decoder comes
+    // first; where it cannot run (too many tiles to be resident at once, or
+    // a stream being captured), the single pass does.
+    if (!delta && n && (v == SVB_DECODE_SMALL || (v == SVB_DECODE_AUTO && n <= kSmallArray)) &&
+        svb::launch_decode_small(in, in_len, n, out, ws, r, s, spin_limit()) == 0)
+        return 0;
+    if (v == SVB_DECODE_SINGLE_PASS ||
+        ((v == SVB_DECODE_AUTO || v == SVB_DECODE_SMALL) && !delta && n <= kSmallPlain))
         return svb::launch_decode(in, in_len, n, out, prev, delta, ws, r, s, spin_limit());
     return svb::launch_decode_tiled(in, in_len, n, out, prev, delta, ws, r, s, spin_limit(),
                                     v == SVB_DECODE_SUMS_PASS);
@@ -58,8 +65,12 @@ int decode_dispatch(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, uint32_
 int encode_dispatch(const uint32_t *in, u64 n, uint8_t *out, uint32_t prev, bool delta,
                     void *ws, svb::DeviceResult *r, cudaStream_t s)
 {
-    if (g_encode_variant.load(std::memory_order_relaxed) == SVB_ENCODE_TILE_LOOKBACK)
+    const int v = g_encode_variant.load(std::memory_order_relaxed);
+    if (v == SVB_ENCODE_TILE_LOOKBACK)
         return svb::launch_encode(in, n, out, prev, delta, ws, r, s, spin_limit());
+    if (n && (v == SVB_ENCODE_SMALL || (v == SVB_ENCODE_AUTO && n <= kSmallArray)) &&
+        svb::launch_encode_small(in, n, out, prev, delta, ws, r, s, spin_limit()) == 0)
+        return 0;
     return svb::launch_encode_tiled(in, n, out, prev, delta, ws, r, s, spin_limit());
 }
 
@@ -491,7 +502,7 @@ const char *svb_error_string(int status)
 
 int svb_set_decode_variant(int variant)
 {
-    if (variant < SVB_DECODE_AUTO || variant > SVB_DECODE_SUMS_PASS)
+    if (variant < SVB_DECODE_AUTO || variant > SVB_DECODE_SMALL)
         return SVB_EINVAL;
     g_decode_variant.store(variant, std::memory_order_relaxed);
     return SVB_OK;
@@ -499,7 +510,7 @@ int svb_set_decode_variant(int variant)
 
 int svb_set_encode_variant(int variant)
 {
-    if (variant < SVB_ENCODE_AUTO || variant > SVB_ENCODE_CHUNKED)
+    if (variant < SVB_ENCODE_AUTO || variant > SVB_ENCODE_SMALL)
         return SVB_EINVAL;
     g_encode_variant.store(variant, std::memory_order_relaxed);
     return SVB_OK;

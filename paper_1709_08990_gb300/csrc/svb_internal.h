@@ -48,6 +48,16 @@ int launch_encode(const uint32_t *in, u64 n, uint8_t *out, uint32_t prev, bool d
                   DeviceResult *result, cudaStream_t stream, u64 spin_limit);
 u64 encode_tiles(u64 n);
 
+// Small arrays in one cooperative launch (svb_small.cu): one CTA per tile
+// of 4096 integers, a grid barrier between sizing and coding.  Return 0, or
+// 3 when the grid cannot be made resident or the stream is being captured
+// (the caller then takes another path; nothing was enqueued).
+int launch_decode_small(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, void *ws,
+                        DeviceResult *result, cudaStream_t stream, u64 spin_limit);
+int launch_encode_small(const uint32_t *in, u64 n, uint8_t *out, uint32_t prev, bool delta,
+                        void *ws, DeviceResult *result, cudaStream_t stream, u64 spin_limit);
+u64 small_tiles(u64 n);
+
 // Chunked single-pass encoder (svb_encode_tiled.cu).  Control bytes go to
 // out; data bytes to out + ceil(n/4), or, when data is given, to
 // data - *data_back (data_back a device pointer, or null for 0).

@@ -174,14 +174,15 @@ def svb_set_spin_limit(iterations: int) -> None:
     lib().svb_set_spin_limit(iterations)
 
 
-SVB_DECODE_AUTO, SVB_DECODE_SINGLE_PASS, SVB_DECODE_TWO_PASS, SVB_DECODE_SUMS_PASS = 0, 1, 2, 3
+(SVB_DECODE_AUTO, SVB_DECODE_SINGLE_PASS, SVB_DECODE_TWO_PASS, SVB_DECODE_SUMS_PASS,
+ SVB_DECODE_SMALL) = 0, 1, 2, 3, 4
 
 
 def svb_set_decode_variant(variant: int) -> int:
     return lib().svb_set_decode_variant(variant)
 
 
-SVB_ENCODE_AUTO, SVB_ENCODE_TILE_LOOKBACK, SVB_ENCODE_CHUNKED = 0, 1, 2
+SVB_ENCODE_AUTO, SVB_ENCODE_TILE_LOOKBACK, SVB_ENCODE_CHUNKED, SVB_ENCODE_SMALL = 0, 1, 2, 3
 
 
 def svb_set_encode_variant(variant: int) -> int:

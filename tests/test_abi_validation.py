@@ -70,14 +70,14 @@ def test_workspace_size_grows_with_n(lib):
 
 
 def test_variants_reject_unknown_values(lib):
-    for v in (-1, 4, 99):
+    for v in (-1, 5, 99):
         assert lib.svb_set_decode_variant(v) == svb.SVB_EINVAL
-    for v in (-1, 3):
+    for v in (-1, 4):
         assert lib.svb_set_encode_variant(v) == svb.SVB_EINVAL
     try:
-        for v in (0, 1, 2, 3):
+        for v in (0, 1, 2, 3, 4):
             assert lib.svb_set_decode_variant(v) == svb.SVB_OK
-        for v in (0, 1, 2):
+        for v in (0, 1, 2, 3):
             assert lib.svb_set_encode_variant(v) == svb.SVB_OK
     finally:
         lib.svb_set_decode_variant(0)

@@ -18,14 +18,21 @@ pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 
 
-@pytest.fixture(params=[1, 2, 3], ids=["single_pass", "two_pass", "sums_pass"])
+ENCODER_WITH = {1: svb.SVB_ENCODE_TILE_LOOKBACK, 2: svb.SVB_ENCODE_CHUNKED,
+                3: svb.SVB_ENCODE_CHUNKED, 4: svb.SVB_ENCODE_SMALL}
+
+
+@pytest.fixture(params=[1, 2, 3, 4], ids=["single_pass", "two_pass", "sums_pass", "small"])
 def variant(request):
     """Run a test under each decoder variant and, alongside, an encoder
     variant (tile look-back with the single-pass decoder, chunked with the
-    others).  The sums-pass variant differs from the two-pass one only for
-    differential streams."""
+    two-pass and sums-pass ones, the one-launch small-array encoder with the
+    small-array decoder).  The sums-pass variant differs from the two-pass
+    one only for differential streams; the small-array decoder only for
+    plain ones (its encoder codes both), and it falls back to the other
+    decoders above the tiles that can be resident at once."""
     assert svb.svb_set_decode_variant(request.param) == 0
-    assert svb.svb_set_encode_variant(min(request.param, 2)) == 0
+    assert svb.svb_set_encode_variant(ENCODER_WITH[request.param]) == 0
     yield request.param
     svb.svb_set_decode_variant(0)
     svb.svb_set_encode_variant(0)
