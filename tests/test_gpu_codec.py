@@ -360,3 +360,45 @@ def test_host_decode_in_pieces():
     h_in2 = torch.from_numpy(ws).pin_memory()
     assert svb.svb_decode_host(h_in2, ws.size, n, h_out, 0, 1, d_in, d_out) == ws.size
     assert np.array_equal(h_out.numpy().view(np.uint32), xs)
+
+
+@pytest.mark.parametrize("n", [100_003, 1 << 20])
+def test_small_arrays_captured_in_a_graph(n):
+    """The default encoder and decoder of a small array launch one
+    cooperative kernel; inside a CUDA graph capture they take the capturable
+    kernels instead.  Both the eager calls and the graph's replays give the
+    oracle's bytes and values."""
+    x = values("uniform", n, 5)
+    xs = values("sorted", n, 6)
+    ws_bytes = svb.svb_workspace_size(n)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=DEV)
+    assert svb.svb_workspace_init(ws, ws_bytes) == 0
+    res = torch.zeros(2, dtype=torch.int64, device=DEV)
+    for vals, delta in ((x, False), (xs, True)):
+        want = oracle.encode(vals, delta=delta, prev=7)
+        d_in = to_dev(vals)
+        d_stream = to_dev(want)
+        enc = torch.zeros(svb.svb_max_compressed_size(n), dtype=torch.uint8, device=DEV)
+        dec = torch.zeros(n, dtype=torch.int32, device=DEV)
+        # eager
+        assert svb.svb_encode_async(d_in, n, enc, 7, delta, res, ws, ws_bytes) == 0
+        assert np.array_equal(enc[: want.size].cpu().numpy(), want)
+        assert svb.svb_decode_async(d_stream, want.size, n, dec, 7, delta, res, ws, ws_bytes) == 0
+        assert np.array_equal(host_u32(dec), vals)
+        # captured
+        enc.zero_()
+        dec.zero_()
+        s = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            st_e = svb.svb_encode_async(d_in, n, enc, 7, delta, res, ws, ws_bytes, s)
+            st_d = svb.svb_decode_async(d_stream, want.size, n, dec, 7, delta, res, ws, ws_bytes, s)
+        assert st_e == 0 and st_d == 0
+        for _ in range(2):
+            g.replay()
+            torch.cuda.synchronize()
+            assert np.array_equal(enc[: want.size].cpu().numpy(), want)
+            assert np.array_equal(host_u32(dec), vals)
+            r = res.cpu().numpy()
+            assert r[1] == 0 and r[0] == want.size
