@@ -778,7 +778,9 @@ def time_lists(svb, W, dev, peaks, count: int):
            "min_len": int(L.min()), "max_len": int(L.max()),
            "not_multiple_of_4": int((L % 4 != 0).sum()), "verified": ok and ok_per_list and ok_enc,
            "tuned": {"threshold": tuned["threshold"], "grid": tuned["grid"],
-                     "cached": tuned["cached"]},
+                     "segment_tiles": tuned.get("segment_tiles"),
+                     "stages": tuned.get("stages"), "tile_ints": tuned.get("tile_ints"),
+                     "encode_stages": tuned.get("encode_stages"), "cached": tuned["cached"]},
            "decode_batched_graph": {"gints_per_s": total / ms_graph / 1e6, "ms": ms_graph,
                                     "frac": alg / (ms_graph / 1e3) / 1e9 / hb},
            "decode_batched_launch": {"gints_per_s": total / ms_batch / 1e6, "ms": ms_batch},

@@ -246,14 +246,15 @@ size_t svb_batch_plan_bytes(size_t num_lists);
  * svb_batch_plan_bytes bytes) on stream.  Lists with n >= big_threshold (0:
  * the default, 8192) are decoded by CTAs tile by tile, longest first;
  * shorter ones by one warp each.  A big list of more than 2 * segment_tiles
- * tiles of 4096 integers, and more than a quarter of a CTA's fair share of
- * all big lists' tiles (a GPU's resident decode CTAs sharing them evenly), is cut into
- * units of segment_tiles tiles decoded by several CTAs at once: each batched
- * decode first finds every such unit's
- * data offset and carry-in within its list (one pass over the split lists'
- * streams with a look-back over each list's units), then decodes.
- * segment_tiles: 0 never splits; at most 32.  svb_batch_plan uses the
- * default of 16.  A plan stays valid for any batch with the same list
+ * decode tiles (4096 integers unless svb_batch_set_tile chose 8192), and
+ * more than a quarter of a CTA's fair share of all big lists' tiles (a GPU's
+ * resident decode CTAs sharing them evenly), is cut into units of
+ * segment_tiles tiles decoded by several CTAs at once: each batched decode
+ * first finds every such unit's data offset and carry-in within its list
+ * (one pass over the split lists' streams with a look-back over each list's
+ * units), then decodes.  segment_tiles: 0 never splits; at most 32 (16 with
+ * tiles of 8192), else SVB_EINVAL.  svb_batch_plan uses the default of 16.
+ * A plan stays valid for any batch with the same list
  * lengths; a plan with split lists holds the state of the call using it, so
  * use it in one call at a time, always with the same workspace.  The batched
  * encoder codes every big list whole, whatever the plan. */
@@ -270,14 +271,33 @@ size_t svb_batch_workspace_size(void);
 /* Staging depth of the batched kernels, for every later svb_batch_decode /
  * svb_batch_encode of this process: the tiles of compressed bytes (decode)
  * or values (encode) each CTA keeps in flight in shared memory.  Fewer
- * stages take less shared memory, so more CTAs fit on an SM; the depths
- * built are 2, 3 and 4 for decoding and 2 and 3 for encoding (0 restores
- * the default: 2 and 3).  The tuner (autotune.py) picks them per GPU and
- * workload.  No paper counterpart: a launch parameter.  Returns SVB_EINVAL
- * for a depth that is not built, leaving both settings as they were.
+ * stages take less shared memory, so more CTAs fit on an SM.  Encoding is
+ * built at depths 2 and 3; decoding at 2, 3 and 4 for tiles of 4096
+ * integers and at 1 and 2 for tiles of 8192 (0 restores the defaults: 2 and
+ * 3).  The tuner (autotune.py) picks them per GPU and workload.  No paper
+ * counterpart: a launch parameter.  Returns SVB_EINVAL for a depth outside
+ * 1..4 (decode) or 2..3 (encode), leaving both settings as they were.
  * svb_batch_get_stages gives the depth in use (encode != 0: the encoder's). */
 int svb_batch_set_stages(int decode_stages, int encode_stages);
 int svb_batch_get_stages(int encode);
+
+/* Decode tile of the batched decoder, in integers, for every later
+ * svb_batch_plan / svb_batch_plan_segments / svb_batch_decode of this
+ * process: 4096 (the default; 0 restores it) or 8192.  A CTA's consumer
+ * warps decode a tile's sub-tiles of 512 integers, one each (4096) or two
+ * each (8192, 32 integers per lane per tile), so larger tiles spread each
+ * tile's fixed costs (a stage hand-off, the control-byte scan, one barrier
+ * per 4096 integers of differential lists) over more integers.  A plan
+ * records the tile it was built for, and its segment_tiles count tiles of
+ * that size (segment_tiles * tile at most 32 * 4096 integers):
+ * svb_batch_decode with a plan built for another tile decodes nothing and
+ * reports SVB_EINVAL in d_result, and svb_batch_decode returns SVB_EINVAL
+ * when the depth in use is not built for the tile in use.  The batched
+ * encoder keeps tiles of 4096.  No paper counterpart: a launch parameter.
+ * Returns SVB_EINVAL for any other size, leaving the setting as it was;
+ * svb_batch_get_tile gives the tile in use. */
+int svb_batch_set_tile(int tile_ints);
+int svb_batch_get_tile(void);
 
 /* Decode / encode every list of the plan in one persistent launch enqueued on
  * stream.  d_lists is the DEVICE copy of the list table.  d_result receives

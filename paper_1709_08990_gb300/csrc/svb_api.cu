@@ -664,6 +664,16 @@ int svb_batch_get_stages(int encode)
     return svb::batch_stages(encode != 0);
 }
 
+int svb_batch_set_tile(int tile_ints)
+{
+    return svb::batch_set_tile(tile_ints) == 0 ? SVB_OK : SVB_EINVAL;
+}
+
+int svb_batch_get_tile(void)
+{
+    return svb::batch_tile();
+}
+
 int svb_batch_decode(const void *d_plan, const svb_list *d_lists, const uint8_t *in_base,
                      uint32_t *out_base, int delta, svb_result *d_result, void *ws,
                      size_t ws_bytes, int grid, svb_stream_t stream)

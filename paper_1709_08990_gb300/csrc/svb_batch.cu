@@ -29,9 +29,7 @@
 
 namespace svb {
 
-constexpr int kBQuads = 1024;                // quads per tile
-constexpr int kBStageData = 16 * kBQuads + 64;
-constexpr int kBStageCtrl = kBQuads + 32;
+constexpr int kBQuads = 1024;                // quads per tile of 4096 integers
 constexpr int kBBlock = kThreads + 32;       // 8 consumer warps + 1 producer warp
 constexpr u64 kBPolls = 1ull << 24;
 constexpr uint32_t kNoList = 0xffffffffu;
@@ -47,8 +45,11 @@ static_assert(kBSubs == kWarps, "one consumer warp per sub-tile");
 // decode first runs batch_prep_kernel over them to find each unit's data
 // offset and carry-in within its list, then decodes units as it would lists.
 // Plans without units (nunits = 0) decode each big list whole.
+// tile_quads is the decode tile (kBQuads times 1 or 2) the plan's units and
+// split decisions were made for; a decode built for another tile refuses it.
 struct PlanHeader {
     uint32_t nbig, nsmall, threshold, nunits;
+    uint32_t tile_quads, pad[3];
 };
 
 struct PlanUnit {
@@ -82,13 +83,16 @@ struct BatchDecArgs {
 // producer has seen released before it refills the slot.
 constexpr int kCAhead = 2;
 
-// Staging depth S (stages of tile data) is a compile-time parameter of the
-// decode kernel: the autotuner picks among the instantiations.
-template <int S>
+// Staging depth S (stages of tile data) and tile size (K * 4096 integers:
+// each consumer warp decodes K sub-tiles of a tile, 16 K integers a lane)
+// are compile-time parameters of the decode kernel: the autotuner picks
+// among the instantiations.
+template <int S, int K>
 struct BPipe {
     static constexpr int kCRing = S + kCAhead;
-    uint8_t data[S][kBStageData];
-    uint8_t ctrl[kCRing][kBStageCtrl];
+    static constexpr int kTQ = K * kBQuads;   // quads per tile
+    uint8_t data[S][16 * kTQ + 64];
+    uint8_t ctrl[kCRing][kTQ + 32];
     uint64_t full[S];   // control and data landed (consumers wait)
     uint64_t cfull[kCRing];    // control landed (the producer waits)
     uint64_t empty[S];  // consumers done with the stage
@@ -99,7 +103,7 @@ struct BPipe {
     uint32_t clist[kCRing], ctile[kCRing], chc[kCRing];   // what each ring slot holds
     uint32_t cfirst[kCRing], cc0[kCRing];   // first tile of a unit; the unit's carry-in
     u64 cd0[kCRing];                        // and its data offset within the list
-    uint32_t soff[S][kBSubs];   // each sub-tile's data offset inside the tile
+    uint32_t soff[S][K * kBSubs];   // each sub-tile's data offset inside the tile
     u64 out_off[S];             // the tile's list: where its integers go,
     uint32_t n[S], prev[S];   // how many, and the unit's carry-in
     uint32_t first[S];               // the stage holds a unit's first tile
@@ -246,10 +250,11 @@ __device__ __forceinline__ uint32_t tile_data_bytes(const uint8_t *C, uint32_t n
 // copies the data.  Every tile whose control bytes were fetched gets one stage
 // (a skipped one if its list's data are cut short), so stage g always pairs
 // with ring slot g % kCRing.
-template <int S>
-__device__ void bdec_produce(const BatchDecArgs &a, BPipe<S> &P, int lane)
+template <int S, int K>
+__device__ void bdec_produce(const BatchDecArgs &a, BPipe<S, K> &P, int lane)
 {
-    constexpr int kCRing = BPipe<S>::kCRing;
+    constexpr int kCRing = BPipe<S, K>::kCRing;
+    constexpr uint32_t kTQ = BPipe<S, K>::kTQ;
     const PlanHeader *plan = a.plan;
     const uint32_t *big = plan_big(plan);
     uint32_t issued = 0;   // stages posted
@@ -293,7 +298,7 @@ __device__ void bdec_produce(const BatchDecArgs &a, BPipe<S> &P, int lane)
                     raise_error(a.hdr, kErrTruncated);
                 continue;
             }
-            const uint32_t ntl = (nql + kBQuads - 1) / kBQuads;
+            const uint32_t ntl = (nql + kTQ - 1) / kTQ;
             la_li = li;
             la_nql = nql;
             la_off = L.in_off;
@@ -314,8 +319,8 @@ __device__ void bdec_produce(const BatchDecArgs &a, BPipe<S> &P, int lane)
             return;
         const int slot = c_issued % kCRing;
         const uint8_t *lo = a.in + la_off;
-        const uint8_t *gc = lo + (u64)la_k * kBQuads;
-        const uint32_t clen = min((uint32_t)kBQuads, la_nql - la_k * kBQuads);
+        const uint8_t *gc = lo + (u64)la_k * kTQ;
+        const uint32_t clen = min(kTQ, la_nql - la_k * kTQ);
         const StagePlan pc = stage_plan(gc, clen, lo, lo + la_len);
         if (pc.edges)
             range_edges(gc, clen, P.ctrl[slot], lane);
@@ -369,7 +374,7 @@ __device__ void bdec_produce(const BatchDecArgs &a, BPipe<S> &P, int lane)
             li = tli;
             L = a.lists[li];
             nql = (L.n + 3) / 4;
-            ntl = (nql + kBQuads - 1) / kBQuads;
+            ntl = (nql + kTQ - 1) / kTQ;
             last_nints = L.n - 4 * (nql - 1);
             running = P.cd0[slot];
             c0 = P.cc0[slot];
@@ -382,11 +387,23 @@ __device__ void bdec_produce(const BatchDecArgs &a, BPipe<S> &P, int lane)
             break;
         }
         const bool last_tile = tk + 1 == ntl;
-        const uint32_t nq = min((uint32_t)kBQuads, nql - tk * kBQuads);
-        uint32_t dsize = 0, soff = 0;
+        const uint32_t nq = min(kTQ, nql - tk * kTQ);
+        uint32_t dsize = 0, soff[K];
         if (!cut) {
-            soff = tile_sub_offsets(P.ctrl[slot], P.chc[slot], nq, last_tile, last_nints, lane,
-                                    dsize);
+            // The tile's 1024-quad pieces in turn: offsets within a piece,
+            // plus the data bytes of the pieces before it.
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                const uint32_t q0 = (uint32_t)k * kBQuads;
+                soff[k] = dsize;
+                if (q0 < nq) {
+                    const uint32_t hq = min((uint32_t)kBQuads, nq - q0);
+                    uint32_t part = 0;
+                    soff[k] += tile_sub_offsets(P.ctrl[slot] + q0, P.chc[slot], hq,
+                                                last_tile && q0 + hq == nq, last_nints, lane, part);
+                    dsize += part;
+                }
+            }
             if (nql + running + dsize > L.in_len) {
                 cut = true;
                 if (lane == 0)
@@ -400,8 +417,10 @@ __device__ void bdec_produce(const BatchDecArgs &a, BPipe<S> &P, int lane)
         const StagePlan pd = stage_plan(gd, dlen, lo, lo + L.in_len);
         if (pd.edges)
             range_edges(gd, dlen, P.data[s], lane);
-        if (lane < kBSubs)
-            P.soff[s][lane] = soff;
+        if (lane < kBSubs && !cut)
+#pragma unroll
+            for (int k = 0; k < K; k++)
+                P.soff[s][k * kBSubs + lane] = soff[k];
         if (lane == 0) {
             P.list[s] = li;
             P.tile[s] = tk;
@@ -457,18 +476,21 @@ __device__ void bdec_produce(const BatchDecArgs &a, BPipe<S> &P, int lane)
     __syncwarp();
 }
 
-// Consumer warps of the big-list phase: warp w decodes sub-tile w of every
-// tile on its own (the same sub-tile decode as the single-stream decoder).
-// For differential lists the eight warps trade their sub-tile gap sums once
-// per tile (one barrier), and each keeps the list's running sum itself.
-template <int S>
-__device__ void bdec_consume(const BatchDecArgs &a, BPipe<S> &P, uint16_t *s_pos,
+// Consumer warps of the big-list phase: warp w decodes sub-tiles w, w + 8,
+// .. of every tile on its own (the same sub-tile decode as the
+// single-stream decoder), one group of eight sub-tiles after another.  For
+// differential lists the eight warps trade their sub-tile gap sums once per
+// group (one barrier), and each keeps the list's running sum itself.
+template <int S, int K>
+__device__ void bdec_consume(const BatchDecArgs &a, BPipe<S, K> &P, uint16_t *s_pos,
                              uint32_t (*s_sum)[kWarps])
 {
-    constexpr int kCRing = BPipe<S>::kCRing;
+    constexpr int kCRing = BPipe<S, K>::kCRing;
+    constexpr uint32_t kTQ = BPipe<S, K>::kTQ;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint16_t *pos = s_pos + warp * kSubQuads;
-    uint32_t carry = 0;  // the list's integer before the current tile
+    uint32_t carry = 0;  // the list's integer before the current group
+    uint32_t ex = 0;     // gap-sum exchanges so far (selects the s_sum buffer)
     for (uint32_t g = 0;; g++) {
         const int s = g % S;
         if (!mbar_wait_bounded(&P.full[s], (g / S) & 1u, kBPolls)) {
@@ -483,92 +505,99 @@ __device__ void bdec_consume(const BatchDecArgs &a, BPipe<S> &P, uint16_t *s_pos
         const uint32_t k = P.tile[s];
         const uint32_t nql = (n + 3) / 4;
         const uint32_t last_nints = n - 4 * (nql - 1);
-        const uint32_t q0 = k * kBQuads + warp * kSubQuads;   // first quad of the sub-tile
         const bool skip = P.skip[s] != 0;
         if (P.first[s])
             carry = P.prev[s];
-        const bool have = !skip && q0 < nql;
-        uint32_t v[kSubRounds][4] = {};
-        SubTile t;
-        t.nq = have ? min((uint32_t)kSubQuads, nql - q0) : 0u;
-        if (have) {
-            t.C = P.ctrl[g % kCRing] + P.hc[s] + warp * kSubQuads;
-            t.D = P.data[s];
-            t.base = P.hd[s] + P.soff[s][warp];
-            t.tail = q0 + t.nq == nql ? last_nints : 4u;
-            const uint32_t w = subtile_ctrl_word(t);
-            subtile_positions(t, w, pos);
-            __syncwarp();
-            subtile_gather(t, pos, v);
-        }
-        fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0)
-            mbar_arrive(&P.empty[s]);
+        const bool aligned = ((uintptr_t)(a.out + out_off) & 15u) == 0;
+#pragma unroll 1
+        for (int j = 0; j < K; j++) {
+            const uint32_t sub = (uint32_t)(j * kBSubs + warp);   // sub-tile within the tile
+            const uint32_t q0 = k * kTQ + sub * kSubQuads;        // its first quad
+            const bool have = !skip && q0 < nql;
+            uint32_t v[kSubRounds][4] = {};
+            SubTile t;
+            t.nq = have ? min((uint32_t)kSubQuads, nql - q0) : 0u;
+            if (have) {
+                t.C = P.ctrl[g % kCRing] + P.hc[s] + sub * kSubQuads;
+                t.D = P.data[s];
+                t.base = P.hd[s] + P.soff[s][sub];
+                t.tail = q0 + t.nq == nql ? last_nints : 4u;
+                const uint32_t w = subtile_ctrl_word(t);
+                __syncwarp();   // the previous group's gather has read pos
+                subtile_positions(t, w, pos);
+                __syncwarp();
+                subtile_gather(t, pos, v);
+            }
+            if (j == K - 1) {   // the stage's last reads are done
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(&P.empty[s]);
+            }
 
-        if (a.delta) {
-            uint32_t run = 0;   // this sub-tile's gaps so far
+            if (a.delta) {
+                uint32_t run = 0;   // this sub-tile's gaps so far
+#pragma unroll
+                for (int r = 0; r < kSubRounds; r++) {
+                    v[r][1] += v[r][0];
+                    v[r][2] += v[r][1];
+                    v[r][3] += v[r][2];
+                    const uint32_t qs = v[r][3];
+                    const uint32_t inc = warp_incl_scan(qs);
+                    const uint32_t add = run + inc - qs;
+#pragma unroll
+                    for (int i = 0; i < 4; i++)
+                        v[r][i] += add;
+                    run += __shfl_sync(0xffffffffu, inc, 31);
+                }
+                uint32_t *sums = s_sum[ex++ & 1];   // double-buffered: the next group's
+                if (lane == 0)                      // barrier orders these reads before
+                    sums[warp] = run;               // the reuse
+                named_sync(1, kThreads);
+                uint32_t before = carry, all = 0;
+#pragma unroll
+                for (int i = 0; i < kWarps; i++) {
+                    const uint32_t x = sums[i];
+                    before += i < warp ? x : 0u;
+                    all += x;
+                }
+                carry += all;
+#pragma unroll
+                for (int r = 0; r < kSubRounds; r++)
+#pragma unroll
+                    for (int i = 0; i < 4; i++)
+                        v[r][i] += before;
+            }
+            if (!have)
+                continue;
+            uint32_t *base = a.out + out_off + 4 * (u64)q0;
+            uint32_t *op = base + 4 * lane;
+            const uint32_t m = (uint32_t)((uintptr_t)base >> 2) & 3u;
 #pragma unroll
             for (int r = 0; r < kSubRounds; r++) {
-                v[r][1] += v[r][0];
-                v[r][2] += v[r][1];
-                v[r][3] += v[r][2];
-                const uint32_t qs = v[r][3];
-                const uint32_t inc = warp_incl_scan(qs);
-                const uint32_t add = run + inc - qs;
-#pragma unroll
-                for (int j = 0; j < 4; j++)
-                    v[r][j] += add;
-                run += __shfl_sync(0xffffffffu, inc, 31);
-            }
-            uint32_t *sums = s_sum[g & 1];   // double-buffered: the next tile's barrier
-            if (lane == 0)                   // orders these reads before the reuse
-                sums[warp] = run;
-            named_sync(1, kThreads);
-            uint32_t before = carry, all = 0;
-#pragma unroll
-            for (int j = 0; j < kWarps; j++) {
-                const uint32_t x = sums[j];
-                before += j < warp ? x : 0u;
-                all += x;
-            }
-            carry += all;
-#pragma unroll
-            for (int r = 0; r < kSubRounds; r++)
-#pragma unroll
-                for (int j = 0; j < 4; j++)
-                    v[r][j] += before;
-        }
-        if (!have)
-            continue;
-        uint32_t *base = a.out + out_off + 4 * (u64)q0;
-        uint32_t *op = base + 4 * lane;
-        const bool aligned = ((uintptr_t)(a.out + out_off) & 15u) == 0;
-        const uint32_t m = (uint32_t)((uintptr_t)base >> 2) & 3u;
-#pragma unroll
-        for (int r = 0; r < kSubRounds; r++) {
-            // Most lists start at an integer that is not 16-byte aligned: a
-            // whole round of 32 quads still goes out in 16-byte writes.
-            if (!aligned && subtile_nints(t, 32u * r + 31u) == 4u) {
-                stg_round_realigned(base + 128 * r, make_uint4(v[r][0], v[r][1], v[r][2], v[r][3]),
-                                    m);
-                continue;
-            }
-            const uint32_t lq = r * 32 + lane;
-            const uint32_t nints = subtile_nints(t, lq);
-            if (!nints)
-                continue;
-            uint32_t *dst = op + 128 * r;
-            if (nints == 4 && aligned) {
-                stg_stream128(dst, make_uint4(v[r][0], v[r][1], v[r][2], v[r][3]));
-            } else {
-                dst[0] = v[r][0];
-                if (nints > 1)
-                    dst[1] = v[r][1];
-                if (nints > 2)
-                    dst[2] = v[r][2];
-                if (nints > 3)
-                    dst[3] = v[r][3];
+                // Most lists start at an integer that is not 16-byte aligned: a
+                // whole round of 32 quads still goes out in 16-byte writes.
+                if (!aligned && subtile_nints(t, 32u * r + 31u) == 4u) {
+                    stg_round_realigned(base + 128 * r,
+                                        make_uint4(v[r][0], v[r][1], v[r][2], v[r][3]), m);
+                    continue;
+                }
+                const uint32_t lq = r * 32 + lane;
+                const uint32_t nints = subtile_nints(t, lq);
+                if (!nints)
+                    continue;
+                uint32_t *dst = op + 128 * r;
+                if (nints == 4 && aligned) {
+                    stg_stream128(dst, make_uint4(v[r][0], v[r][1], v[r][2], v[r][3]));
+                } else {
+                    dst[0] = v[r][0];
+                    if (nints > 1)
+                        dst[1] = v[r][1];
+                    if (nints > 2)
+                        dst[2] = v[r][2];
+                    if (nints > 3)
+                        dst[3] = v[r][3];
+                }
             }
         }
     }
@@ -712,7 +741,7 @@ __device__ void bdec_small(const BatchDecArgs &a, uint32_t li, int lane, uint8_t
 
 constexpr int kBPrepCtrl = 144;                      // 15-byte phase + 128 control bytes
 constexpr int kBPrepData = 16 * kSubQuads + 48;      // phase + 2048 + read slack
-constexpr uint32_t kMaxSegTiles = 32;                // the most tiles a unit may have
+constexpr uint32_t kMaxSegTiles = 32;   // the most 4096-integer tiles a unit may span
 constexpr u64 kPrepSpins = 1ull << 22;
 
 struct BatchPrepArgs {
@@ -738,8 +767,12 @@ __global__ void __launch_bounds__(kThreads) batch_prep_kernel(BatchPrepArgs a)
     const u64 etag = epoch_tag(a.hdr);
     PlanUnit *units = plan_units(a.plan);
     TileStatus *recs = plan_recs(a.plan);
+    const uint32_t tq = a.plan->tile_quads;   // the plan's tile: units count these
+    const bool tq_ok = tq == (uint32_t)kBQuads || tq == 2u * kBQuads;
+    if (!tq_ok && tid == 0)
+        raise_error(a.hdr, kErrInvalid);
     const uint64_t keep = l2_policy_evict_last();
-    for (;;) {
+    while (tq_ok) {
         __syncthreads();
         if (tid == 0)
             s_unit = atomicAdd(&a.hdr->a_counter, 1ull);
@@ -754,8 +787,8 @@ __global__ void __launch_bounds__(kThreads) batch_prep_kernel(BatchPrepArgs a)
         const uint8_t *lo = a.in + L.in_off;
         const uint8_t *hi = lo + L.in_len;
         const uint8_t *data = lo + nql;
-        const uint32_t qb0 = U.t0 * kBQuads;
-        const uint32_t qe = min((U.t0 + U.nt) * kBQuads, nql);
+        const uint32_t qb0 = U.t0 * tq;
+        const uint32_t qe = min((U.t0 + U.nt) * tq, nql);
         const uint32_t ns = (qe - qb0 + kSubQuads - 1) / kSubQuads;
         const bool ctrl_ok = (u64)nql <= L.in_len;
         // A: data bytes of each sub-tile (byte loads, coalesced across the warp).
@@ -927,16 +960,24 @@ __global__ void __launch_bounds__(kThreads) batch_prep_kernel(BatchPrepArgs a)
     }
 }
 
-template <int S, int kMinCtas>
+template <int S, int K, int kMinCtas>
 __global__ void __launch_bounds__(kBBlock, kMinCtas) batch_decode_kernel(BatchDecArgs a)
 {
-    constexpr int kCRing = BPipe<S>::kCRing;
+    constexpr int kCRing = BPipe<S, K>::kCRing;
     extern __shared__ __align__(128) uint8_t dyn_smem[];
-    BPipe<S> &P = *reinterpret_cast<BPipe<S> *>(dyn_smem);
+    BPipe<S, K> &P = *reinterpret_cast<BPipe<S, K> *>(dyn_smem);
     __shared__ __align__(16) uint16_t s_pos[kBQuads];   // each warp's quad positions
     __shared__ uint32_t s_sum[2][kWarps];                // sub-tile gap sums, per tile parity
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // A plan made for another tile size: its units do not match this
+    // kernel's tiles, so nothing is decoded (every CTA sees the same).
+    if (a.plan->tile_quads != (uint32_t)BPipe<S, K>::kTQ) {
+        if (tid == 0)
+            raise_error(a.hdr, kErrInvalid);
+        finish_launch(a.hdr, a.result);
+        return;
+    }
     if (tid == 0) {
         for (int s = 0; s < S; s++) {
             mbar_init(&P.full[s], 32);
@@ -948,9 +989,9 @@ __global__ void __launch_bounds__(kBBlock, kMinCtas) batch_decode_kernel(BatchDe
     }
     __syncthreads();
     if (warp == kWarps)
-        bdec_produce<S>(a, P, lane);
+        bdec_produce<S, K>(a, P, lane);
     else
-        bdec_consume<S>(a, P, s_pos, s_sum);
+        bdec_consume<S, K>(a, P, s_pos, s_sum);
 
     // Small lists: every warp takes them one by one, staging their pieces in
     // a slot of its own carved from the data stages, which the big-list
@@ -1271,14 +1312,17 @@ static int persistent_grid(K kernel, size_t smem)
     return (sms > 0 ? sms : 148) * (occ > 0 ? occ : 1);
 }
 
-// Staging depths the batched kernels are built with, and the one each uses
-// (0: the default, set by svb_batch_set_stages).
-static std::atomic<int> g_dec_stages{0}, g_enc_stages{0};
+// Staging depths and decode tile sizes the batched kernels are built with,
+// and the ones in use (0: the default; set by svb_batch_set_stages and
+// svb_batch_set_tile).  Decoding is built for tiles of 4096 integers at
+// depths 2, 3 and 4, and for tiles of 8192 at depths 1 and 2.
+static std::atomic<int> g_dec_stages{0}, g_enc_stages{0}, g_dec_tile{0};
 constexpr int kDecStagesDefault = 2, kEncStagesDefault = 3;
+constexpr int kTileIntsDefault = 4 * kBQuads;
 
 int batch_set_stages(int decode_stages, int encode_stages)
 {
-    const bool dec_ok = decode_stages == 0 || (decode_stages >= 2 && decode_stages <= 4);
+    const bool dec_ok = decode_stages == 0 || (decode_stages >= 1 && decode_stages <= 4);
     const bool enc_ok = encode_stages == 0 || encode_stages == 2 || encode_stages == 3;
     if (!dec_ok || !enc_ok)
         return 1;
@@ -1293,17 +1337,31 @@ int batch_stages(int encode)
     return v ? v : (encode ? kEncStagesDefault : kDecStagesDefault);
 }
 
+int batch_set_tile(int tile_ints)
+{
+    if (tile_ints != 0 && tile_ints != 4 * kBQuads && tile_ints != 8 * kBQuads)
+        return 1;
+    g_dec_tile.store(tile_ints, std::memory_order_relaxed);
+    return 0;
+}
+
+int batch_tile(void)
+{
+    const int v = g_dec_tile.load(std::memory_order_relaxed);
+    return v ? v : kTileIntsDefault;
+}
+
 // One instantiation of the decode kernel: S stages, at least kMinCtas CTAs
 // per SM (the register cap that lets that many fit).
-template <int S, int kMinCtas>
+template <int S, int K, int kMinCtas>
 static void launch_bdec(const BatchDecArgs &a, int grid, cudaStream_t stream)
 {
     static int g = 0;
     if (!g)
-        g = persistent_grid(batch_decode_kernel<S, kMinCtas>, sizeof(BPipe<S>));
+        g = persistent_grid(batch_decode_kernel<S, K, kMinCtas>, sizeof(BPipe<S, K>));
     prof_begin("batch_decode_kernel", stream);
-    batch_decode_kernel<S, kMinCtas>
-        <<<grid > 0 ? grid : g, kBBlock, sizeof(BPipe<S>), stream>>>(a);
+    batch_decode_kernel<S, K, kMinCtas>
+        <<<grid > 0 ? grid : g, kBBlock, sizeof(BPipe<S, K>), stream>>>(a);
     prof_end(stream);
 }
 
@@ -1323,6 +1381,12 @@ int launch_batch_decode(const void *d_plan, const svb_list *d_lists, const uint8
                         uint32_t *out, bool delta, void *ws, DeviceResult *result,
                         cudaStream_t stream, int grid)
 {
+    // The instantiation for the tile and depth in use; a pair that is not
+    // built is refused before anything is enqueued.
+    const int tile = batch_tile(), stages = batch_stages(0);
+    const bool built = tile == 4 * kBQuads ? stages >= 2 && stages <= 4 : stages <= 2;
+    if (!built)
+        return 1;
     BatchDecArgs a;
     a.lists = d_lists;
     a.plan = static_cast<const PlanHeader *>(d_plan);
@@ -1349,16 +1413,17 @@ int launch_batch_decode(const void *d_plan, const svb_list *d_lists, const uint8
     prof_begin("batch_prep_kernel", stream);
     batch_prep_kernel<<<pg, kThreads, 0, stream>>>(pa);
     prof_end(stream);
-    switch (batch_stages(0)) {
-    case 4:
-        launch_bdec<4, 3>(a, grid, stream);
-        break;
-    case 3:
-        launch_bdec<3, 4>(a, grid, stream);
-        break;
-    default:
-        launch_bdec<2, 4>(a, grid, stream);
-        break;
+    if (tile == 8 * kBQuads) {
+        if (stages == 1)
+            launch_bdec<1, 2, 4>(a, grid, stream);
+        else
+            launch_bdec<2, 2, 2>(a, grid, stream);
+    } else if (stages == 4) {
+        launch_bdec<4, 1, 3>(a, grid, stream);
+    } else if (stages == 3) {
+        launch_bdec<3, 1, 4>(a, grid, stream);
+    } else {
+        launch_bdec<2, 1, 4>(a, grid, stream);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
@@ -1399,7 +1464,10 @@ int build_batch_plan(const svb_list *h_lists, size_t num_lists, uint32_t thresho
 {
     if (threshold == 0)
         threshold = kDefaultBigThreshold;
-    if (seg_tiles > kMaxSegTiles)
+    // The plan is made for the decode tile in use: tq quads, units of
+    // seg_tiles such tiles (at most kMaxSegTiles tiles of 4096 integers).
+    const uint32_t tq = (uint32_t)batch_tile() / 4;
+    if ((u64)seg_tiles * tq > (u64)kMaxSegTiles * kBQuads)
         return 1;
     std::vector<uint32_t> big, small;
     for (size_t j = 0; j < num_lists; j++) {
@@ -1421,7 +1489,7 @@ int build_batch_plan(const svb_list *h_lists, size_t num_lists, uint32_t thresho
     // one unit per other big list.
     u64 big_tiles = 0;
     for (uint32_t li : big)
-        big_tiles += (((u64)h_lists[li].n + 3) / 4 + kBQuads - 1) / kBQuads;
+        big_tiles += (((u64)h_lists[li].n + 3) / 4 + tq - 1) / tq;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1431,7 +1499,7 @@ int build_batch_plan(const svb_list *h_lists, size_t num_lists, uint32_t thresho
     const size_t budget = num_lists + kExtraUnits;
     for (uint32_t li : big) {
         const uint32_t nql = (uint32_t)(((u64)h_lists[li].n + 3) / 4);
-        const uint32_t ntl = (nql + kBQuads - 1) / kBQuads;
+        const uint32_t ntl = (nql + tq - 1) / tq;
         const uint32_t nseg = seg_tiles ? (ntl + seg_tiles - 1) / seg_tiles : 1u;
         if (seg_tiles && ntl > 2 * seg_tiles && 4 * (u64)ntl > fair &&
             split.size() + nseg + (big.size() - 1) <= budget) {
@@ -1448,13 +1516,16 @@ int build_batch_plan(const svb_list *h_lists, size_t num_lists, uint32_t thresho
     const size_t bytes = nunits ? plan_recs_off(ids, nunits) + sizeof(TileStatus) * nunits
                                 : sizeof(PlanHeader) + 4 * ids;
     std::vector<uint8_t> buf(bytes, 0);
-    uint32_t *w = reinterpret_cast<uint32_t *>(buf.data());
-    w[0] = (uint32_t)big.size();
-    w[1] = (uint32_t)small.size();
-    w[2] = threshold;
-    w[3] = (uint32_t)nunits;
-    std::copy(big.begin(), big.end(), w + 4);
-    std::copy(small.begin(), small.end(), w + 4 + big.size());
+    PlanHeader h = {};
+    h.nbig = (uint32_t)big.size();
+    h.nsmall = (uint32_t)small.size();
+    h.threshold = threshold;
+    h.nunits = (uint32_t)nunits;
+    h.tile_quads = tq;
+    std::copy_n(reinterpret_cast<const uint8_t *>(&h), sizeof(h), buf.data());
+    uint32_t *w = reinterpret_cast<uint32_t *>(buf.data() + sizeof(PlanHeader));
+    std::copy(big.begin(), big.end(), w);
+    std::copy(small.begin(), small.end(), w + big.size());
     if (nunits) {
         // Units header (nsplit), the units, then zeroed records: a zero tag
         // never matches a launch's tag.

@@ -79,6 +79,8 @@ int launch_append(uint8_t *ctrl, uint8_t *data, u64 data_len, u64 n, const uint3
 // for the default.  Returns 0, or 1 for a depth that is not built.
 int batch_set_stages(int decode_stages, int encode_stages);
 int batch_stages(int encode);
+int batch_set_tile(int tile_ints);
+int batch_tile(void);
 int launch_batch_decode(const void *d_plan, const svb_list *d_lists, const uint8_t *in,
                         uint32_t *out, bool delta, void *ws, DeviceResult *result,
                         cudaStream_t stream, int grid);

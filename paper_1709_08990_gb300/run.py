@@ -102,6 +102,8 @@ def _lists(op: str, name: str, count: int, reps: int, cap: int = 1 << 30,
         ms = _time(lambda: pool.encode(out), reps, stream)
         ok = bool(torch.equal(out, pool.pool))
     return {"op": op, "workload": name, "lists": count, "n": total,
+            "tile_ints": svb.svb_batch_get_tile(),
+            "stages": svb.svb_batch_get_stages(int(op == "batch_encode")),
             "stream_bytes": pool.pool_bytes, "ms": ms,
             "gints_per_s": total / (ms / 1e3) / 1e9, "verified": ok}
 
@@ -191,6 +193,10 @@ def main(argv=None) -> None:
     ap.add_argument("--segment-tiles", type=int, default=-1,
                     help="batch: tiles per unit of a split list (0: no splitting; "
                          "-1: the library's default)")
+    ap.add_argument("--tile", type=int, default=0,
+                    help="batch_decode: decode tile, 4096 or 8192 integers (0: the default)")
+    ap.add_argument("--stages", type=int, default=0,
+                    help="batch: staging depth of the batched kernel (0: the default)")
     ap.add_argument("--variant", type=int, default=0,
                     help="decoder variant (svb_set_decode_variant), 0 = the default")
     ap.add_argument("--kernels", action="store_true",
@@ -201,6 +207,10 @@ def main(argv=None) -> None:
     if a.kernels:
         svb.svb_profile_begin()
     if a.op.startswith("batch"):
+        enc = a.op == "batch_encode"
+        if (svb.svb_batch_set_tile(a.tile) != 0 or
+                svb.svb_batch_set_stages(0 if enc else a.stages, a.stages if enc else 0) != 0):
+            raise SystemExit(f"tile {a.tile} / staging depth {a.stages} not built")
         r = _lists(a.op, a.workload or "lists_100k", a.lists, a.reps, a.cap,
                    None if a.segment_tiles < 0 else a.segment_tiles)
     elif a.op == "size":

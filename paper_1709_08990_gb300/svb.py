@@ -76,6 +76,8 @@ def lib() -> ctypes.CDLL:
             "svb_batch_workspace_size": ([], sz),
             "svb_batch_set_stages": ([i32, i32], i32),
             "svb_batch_get_stages": ([i32], i32),
+            "svb_batch_set_tile": ([i32], i32),
+            "svb_batch_get_tile": ([], i32),
             "svb_batch_decode": ([vp, vp, vp, vp, i32, vp, vp, sz, i32, vp], i32),
             "svb_batch_encode": ([vp, vp, vp, vp, i32, vp, vp, vp, sz, i32, vp], i32),
             "svb_decode_each": ([vp, sz, vp, vp, i32, vp, vp, sz, vp], i32),
@@ -240,6 +242,14 @@ def svb_batch_set_stages(decode_stages: int, encode_stages: int) -> int:
 
 def svb_batch_get_stages(encode: int) -> int:
     return lib().svb_batch_get_stages(encode)
+
+
+def svb_batch_set_tile(tile_ints: int) -> int:
+    return lib().svb_batch_set_tile(tile_ints)
+
+
+def svb_batch_get_tile() -> int:
+    return lib().svb_batch_get_tile()
 
 
 def svb_batch_workspace_size() -> int:

@@ -340,3 +340,80 @@ def test_batch_encode_every_staging_depth(stages, delta, staging):
     for j, s in enumerate(b.streams):
         off = int(b.enc_lists[j]["out_off"])
         assert np.array_equal(out[off:off + s.size], s), f"stages {stages}, list {j}"
+
+
+@pytest.fixture
+def decode_tile():
+    """Sets the batched decoder's tile and staging depth for one test (plans
+    are built for the tile in use), then restores the defaults."""
+    def set_(tile, stages):
+        assert svb.svb_batch_set_tile(tile) == 0
+        assert svb.svb_batch_set_stages(stages, 0) == 0
+    yield set_
+    svb.svb_batch_set_tile(0)
+    svb.svb_batch_set_stages(0, 0)
+
+
+# Lengths at and around one and two tiles of 8192 integers.
+AROUND_8192 = [16_383, 16_384, 16_385, 24_577, 8191 * 3, 70_001, 131_073]
+
+
+@pytest.mark.parametrize("stages", [1, 2])
+@pytest.mark.parametrize("delta", [False, True])
+def test_batch_decode_tiles_of_8192(stages, delta, decode_tile):
+    """Tiles of 8192 integers (two sub-tiles per consumer warp) at each
+    depth built for them, whole lists and split ones."""
+    decode_tile(8192, stages)
+    lengths = LENGTHS + AROUND_8192
+    b = Batch(lengths, delta, seed=13, prevs=[(71 * j) & 0xFFFF for j in range(len(lengths))],
+              gap_bytes=3)
+    for thr, seg in ((16, None), (16, 0), (16, 1), (16, 2), (0, 16), (1 << 30, None)):
+        got, r = batch_decode(b, threshold=thr, segment_tiles=seg, repeat=2)
+        assert r[1] == 0 and r[0] == sum(s.size for s in b.streams)
+        assert np.array_equal(got, b.all_values), f"stages {stages}, threshold {thr}, seg {seg}"
+
+
+@pytest.mark.parametrize("delta", [False, True])
+def test_batch_decode_tiles_of_8192_split_long_lists(delta, decode_tile):
+    decode_tile(8192, 2)
+    b = Batch(LONG, delta, seed=14, prevs=[(4099 * j) & 0xFFFFFFF for j in range(len(LONG))],
+              gap_bytes=1)
+    for seg in (1, 3, 16):
+        got, r = batch_decode(b, 0, 0, seg, repeat=2)
+        assert r[1] == 0 and r[0] == sum(s.size for s in b.streams)
+        for j, m in enumerate(b.lengths):
+            o = int(b.dec_lists[j]["out_off"])
+            assert np.array_equal(got[o:o + int(m)], b.values[j]), f"seg {seg}, list {j}"
+
+
+def test_plan_of_another_tile_is_refused(decode_tile):
+    """A plan records its tile: decoded with another tile in use it decodes
+    nothing and reports SVB_EINVAL, and the workspace still serves the next
+    call; a depth not built for the tile in use is refused at once."""
+    b = Batch([70_001, 5000, 300, 131_073], True, seed=15)
+    d_plan = run_plan(b.dec_lists, 16, 2)             # tiles of 4096
+    d_lists = to_dev(b.dec_lists.view(np.uint8))
+    d_in = to_dev(b.pool)
+    ws, nb = workspace()
+    res = torch.zeros(2, dtype=torch.int64, device=DEV)
+    d_out = torch.full((b.total_ints,), -7, dtype=torch.int32, device=DEV)
+    decode_tile(8192, 2)
+    assert svb.svb_batch_decode(d_plan, d_lists, d_in, d_out, 1, res, ws, nb) == 0
+    assert res[1].item() == svb.SVB_EINVAL
+    assert bool((d_out == -7).all())
+    assert svb.svb_batch_set_stages(3, 0) == 0      # depth 3 is built for 4096 only
+    assert svb.svb_batch_decode(d_plan, d_lists, d_in, d_out, 1, res, ws, nb) == svb.SVB_EINVAL
+    decode_tile(0, 0)
+    assert svb.svb_batch_decode(d_plan, d_lists, d_in, d_out, 1, res, ws, nb) == 0
+    assert res[1].item() == 0
+    assert np.array_equal(d_out.cpu().numpy().view(np.uint32), b.all_values)
+
+
+def test_segment_limit_follows_the_tile(decode_tile):
+    lists = np.zeros(3, dtype=svb.list_dtype())
+    lists["n"] = 5
+    nb = svb.svb_batch_plan_bytes(3)
+    d = torch.empty(nb, dtype=torch.uint8, device=DEV)
+    decode_tile(8192, 2)
+    assert svb.svb_batch_plan_segments(lists, 3, 0, 17, d, nb) == svb.SVB_EINVAL
+    assert svb.svb_batch_plan_segments(lists, 3, 0, 16, d, nb) == svb.SVB_OK
