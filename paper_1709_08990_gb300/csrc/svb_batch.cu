@@ -34,6 +34,7 @@ constexpr int kBBlock = kThreads + 32;       // 8 consumer warps + 1 producer wa
 constexpr u64 kBPolls = 1ull << 24;
 constexpr uint32_t kNoList = 0xffffffffu;
 constexpr uint32_t kDefaultBigThreshold = 8192;
+constexpr u64 kErrInvalid = 1;   // SVB_EINVAL: a plan made for another decode tile
 constexpr int kBSubs = kBQuads / kSubQuads;   // sub-tiles per tile = consumer warps
 static_assert(kBSubs == kWarps, "one consumer warp per sub-tile");
 

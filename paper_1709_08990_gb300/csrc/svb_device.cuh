@@ -30,7 +30,7 @@ constexpr u64 kFlagNone = 0, kFlagAgg = 1, kFlagPrefix = 2;
 constexpr u64 kTagMark = 1ull << 63;
 
 // Error codes written to the workspace (same values as svb_status).
-constexpr u64 kErrInvalid = 1, kErrTruncated = 2, kErrTimeout = 4;
+constexpr u64 kErrTruncated = 2, kErrTimeout = 4;
 
 // One tile's published values.  Each scan has a tag word and two slots; a
 // reader that has seen a tag reads a slot that is written once per launch
