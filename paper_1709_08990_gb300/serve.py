@@ -34,22 +34,31 @@ def _up(x, a=_ALIGN):
     return (x + a - 1) // a * a
 
 
-def host_plan(n: np.ndarray, threshold: int, out: np.ndarray | None = None) -> np.ndarray:
+# The plan header the batched kernels read (PlanHeader in csrc/svb_batch.cu):
+# nbig, nsmall, threshold, nunits, the decode tile in quads, three pad words.
+PLAN_HEADER_WORDS = 8
+
+
+def host_plan(n: np.ndarray, threshold: int, out: np.ndarray | None = None,
+              tile_quads: int = 1024) -> np.ndarray:
     """The batched kernels' plan: lists with n >= threshold first (longest
     first), then the rest in request order (each takes one warp; their order
-    only shifts which warp starts first).  Written into out (uint32, at least
-    4 + n.size entries) when given."""
+    only shifts which warp starts first), no units, made for decode tiles of
+    tile_quads quads (the library's tile when the plan is decoded).  Written
+    into out (uint32, at least PLAN_HEADER_WORDS + n.size entries) when
+    given."""
     isbig = n >= threshold
     big = np.flatnonzero(isbig).astype(np.uint32)
     small = np.flatnonzero(~isbig).astype(np.uint32)
     if big.size > 1:
         big = big[np.argsort(-n[big].astype(np.int64), kind="stable")]
-    k = 4 + n.size
+    h = PLAN_HEADER_WORDS
+    k = h + n.size
     if out is None:
         out = np.empty(k, dtype=np.uint32)
-    out[:4] = (big.size, small.size, threshold, 0)
-    out[4:4 + big.size] = big
-    out[4 + big.size:k] = small
+    out[:h] = (big.size, small.size, threshold, 0, tile_quads, 0, 0, 0)
+    out[h:h + big.size] = big
+    out[h + big.size:k] = small
     return out[:k]
 
 
@@ -200,6 +209,8 @@ class Server:
                                    np.asarray(pool.sizes, dtype=np.uint64)], axis=1)
         self.max_batch = max_batch
         self.threshold = threshold
+        # Plans are made for the decode tile in use when the graphs are captured.
+        self.tile_quads = svb.svb_batch_get_tile() // 4
         self.scratch = torch.empty(budget, dtype=torch.uint8, device=self.dev)
         self.arena = RingArena(budget)
         self.rec = svb.list_dtype().itemsize
@@ -230,6 +241,10 @@ class Server:
     def _write_empty(self, s: Slot):
         h = s.host.numpy()
         h[:] = 0
+        none = np.zeros(0, dtype=np.uint32)
+        for o in (self.o_dp, self.o_ep):
+            host_plan(none, self.threshold, h[o:o + 4 * PLAN_HEADER_WORDS].view(np.uint32),
+                      self.tile_quads)
         s.dev.copy_(s.host)
 
     def _launch_raw(self, s: Slot):
@@ -299,9 +314,11 @@ class Server:
         et[:ne, 0] >>= np.uint64(2)
         et[:ne, 2] += shift(base + p_eo - int(prep.co[lo]))
         host_plan(prep.ndec[a:b], self.threshold,
-                  h[self.o_dp:self.o_dp + 4 * (4 + nd)].view(np.uint32))
+                  h[self.o_dp:self.o_dp + 4 * (PLAN_HEADER_WORDS + nd)].view(np.uint32),
+                  self.tile_quads)
         host_plan(prep.nenc[c:d], self.threshold,
-                  h[self.o_ep:self.o_ep + 4 * (4 + ne)].view(np.uint32))
+                  h[self.o_ep:self.o_ep + 4 * (PLAN_HEADER_WORDS + ne)].view(np.uint32),
+                  self.tile_quads)
         with torch.cuda.stream(s.stream):
             s.dev.copy_(s.host, non_blocking=True)
             if ne:

@@ -72,3 +72,29 @@ def test_open_loop_arrivals(pool):
     assert np.all(out["done"] >= req.arrival)
     s = summarize(req, out)
     assert s["p99_ms"] >= s["p50_ms"] > 0
+
+
+@pytest.mark.parametrize("tile", [4096, 8192])
+def test_host_plan_matches_the_library_layout(tile):
+    """serve.host_plan writes the plan layout the batched kernels read: its
+    header and big-list order equal the library's plan for the same lists
+    (no units), at either decode tile."""
+    from paper_1709_08990_gb300 import svb
+    from paper_1709_08990_gb300.serve import PLAN_HEADER_WORDS, host_plan
+    n = np.array([5, 70_000, 9000, 8192, 3, 20_000, 20_000, 100, 8191], dtype=np.uint32)
+    lists = np.zeros(n.size, dtype=svb.list_dtype())
+    lists["n"] = n
+    nb = svb.svb_batch_plan_bytes(n.size)
+    d = torch.zeros(nb, dtype=torch.uint8, device="cuda:0")
+    try:
+        assert svb.svb_batch_set_tile(tile) == 0
+        assert svb.svb_batch_plan_segments(lists, n.size, 8192, 0, d, nb) == 0
+        lib = d.cpu().numpy().view(np.uint32)
+        host = host_plan(n, 8192, tile_quads=svb.svb_batch_get_tile() // 4)
+    finally:
+        svb.svb_batch_set_tile(0)
+    h = PLAN_HEADER_WORDS
+    assert np.array_equal(lib[:h], host[:h])
+    nbig = int(host[0])
+    assert np.array_equal(lib[h:h + nbig], host[h:h + nbig])
+    assert sorted(lib[h + nbig:h + n.size].tolist()) == sorted(host[h + nbig:].tolist())

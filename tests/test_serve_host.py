@@ -7,7 +7,8 @@ import numpy as np
 import pytest
 
 pytest.importorskip("torch")
-from paper_1709_08990_gb300.serve import RingArena, Server, host_plan  # noqa: E402
+from paper_1709_08990_gb300.serve import (PLAN_HEADER_WORDS, RingArena, Server,  # noqa: E402
+                                           host_plan)
 
 
 def _live(arena):
@@ -95,18 +96,21 @@ def test_random_traffic_keeps_blocks_disjoint_and_largest_exact(seed):
 def test_plan_orders_big_longest_first_then_small_in_request_order(threshold):
     rng = np.random.default_rng(threshold)
     n = rng.integers(1, 300, 257).astype(np.uint32)
+    h = PLAN_HEADER_WORDS
     p = host_plan(n, threshold)
-    nbig, nsmall, thr, zero = (int(v) for v in p[:4])
-    assert (thr, zero) == (threshold, 0)
-    big, small = p[4:4 + nbig], p[4 + nbig:4 + nbig + nsmall]
-    assert p.size == 4 + n.size
+    nbig, nsmall, thr, units, tile_quads = (int(v) for v in p[:5])
+    assert (thr, units, tile_quads) == (threshold, 0, 1024)   # no units; tiles of 4096
+    assert not p[5:h].any()
+    big, small = p[h:h + nbig], p[h + nbig:h + nbig + nsmall]
+    assert p.size == h + n.size
     assert sorted(np.concatenate([big, small]).tolist()) == list(range(n.size))
     assert np.all(n[big] >= threshold) and np.all(n[small] < threshold)
     assert np.all(np.diff(n[big].astype(np.int64)) <= 0)
     assert np.all(np.diff(small.astype(np.int64)) > 0)
-    out = np.full(4 + n.size + 3, 7, dtype=np.uint32)
+    out = np.full(h + n.size + 3, 7, dtype=np.uint32)
     q = host_plan(n, threshold, out)
-    assert np.array_equal(q, p) and np.all(out[4 + n.size:] == 7)
+    assert np.array_equal(q, p) and np.all(out[h + n.size:] == 7)
+    assert host_plan(n, threshold, tile_quads=2048)[4] == 2048
 
 
 class _Req:
