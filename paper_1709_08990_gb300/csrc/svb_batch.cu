@@ -477,6 +477,77 @@ __device__ void bdec_produce(const BatchDecArgs &a, BPipe<S, K> &P, int lane)
     __syncwarp();
 }
 
+// A full sub-tile's 512 integers (lane l holds quad 32r + l in v[r]) stored
+// to dst, which is 4-byte aligned with M = (dst / 4) mod 4 in {1, 2, 3},
+// with 16-byte writes.  The aligned chunk that ends with the first 4 - M
+// integers of quad Q starts with the last M of quad Q - 1: lane l - 1's of
+// the same round, or, for lane 0, lane 31's of the round before, which the
+// rotated shuffle of that round already delivered to lane 0.  Only the
+// sub-tile's first 4 - M integers and its last M go out one by one.
+template <int M>
+__device__ __forceinline__ void store_full_realigned(uint32_t *dst,
+                                                     const uint32_t (&v)[kSubRounds][4])
+{
+    const int lane = threadIdx.x & 31;
+    const int src = (lane + 31) & 31;
+    uint32_t *chunk = dst + 4 * lane - M;   // 16-byte aligned
+    uint32_t w1 = 0, w2 = 0, w3 = 0;        // lane 0: lane 31's last three of the round before
+#pragma unroll
+    for (int r = 0; r < kSubRounds; r++) {
+        const uint32_t p1 = __shfl_sync(0xffffffffu, v[r][1], src);
+        const uint32_t p2 = __shfl_sync(0xffffffffu, v[r][2], src);
+        const uint32_t p3 = __shfl_sync(0xffffffffu, v[r][3], src);
+        const uint32_t a1 = lane ? p1 : w1, a2 = lane ? p2 : w2, a3 = lane ? p3 : w3;
+        uint4 c;
+        if (M == 1)
+            c = make_uint4(a3, v[r][0], v[r][1], v[r][2]);
+        else if (M == 2)
+            c = make_uint4(a2, a3, v[r][0], v[r][1]);
+        else
+            c = make_uint4(a1, a2, a3, v[r][0]);
+        if (r > 0 || lane > 0)   // the chunk before quad 0 is not the sub-tile's
+            stg_stream128(chunk + 128 * r, c);
+        w1 = p1;
+        w2 = p2;
+        w3 = p3;
+    }
+    if (lane == 0) {
+        dst[0] = v[0][0];
+        if (M < 3)
+            dst[1] = v[0][1];
+        if (M < 2)
+            dst[2] = v[0][2];
+    }
+    if (lane == 31) {
+        uint32_t *q = dst + 4 * (kSubQuads - 1);
+        q[3] = v[kSubRounds - 1][3];
+        if (M > 1)
+            q[2] = v[kSubRounds - 1][2];
+        if (M > 2)
+            q[1] = v[kSubRounds - 1][1];
+    }
+}
+
+// A full sub-tile's integers to dst (4-byte aligned): 16-byte writes,
+// realigned unless dst is 16-byte aligned.
+__device__ __forceinline__ void store_full_subtile(uint32_t *dst,
+                                                   const uint32_t (&v)[kSubRounds][4])
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t m = (uint32_t)((uintptr_t)dst >> 2) & 3u;
+    if (m == 0) {
+#pragma unroll
+        for (int r = 0; r < kSubRounds; r++)
+            stg_stream128(dst + 128 * r + 4 * lane, make_uint4(v[r][0], v[r][1], v[r][2], v[r][3]));
+    } else if (m == 1) {
+        store_full_realigned<1>(dst, v);
+    } else if (m == 2) {
+        store_full_realigned<2>(dst, v);
+    } else {
+        store_full_realigned<3>(dst, v);
+    }
+}
+
 // Consumer warps of the big-list phase: warp w decodes sub-tiles w, w + 8,
 // .. of every tile on its own (the same sub-tile decode as the
 // single-stream decoder), one group of eight sub-tiles after another.  For
@@ -572,6 +643,10 @@ __device__ void bdec_consume(const BatchDecArgs &a, BPipe<S, K> &P, uint16_t *s_
             if (!have)
                 continue;
             uint32_t *base = a.out + out_off + 4 * (u64)q0;
+            if (t.full()) {
+                store_full_subtile(base, v);
+                continue;
+            }
             uint32_t *op = base + 4 * lane;
             const uint32_t m = (uint32_t)((uintptr_t)base >> 2) & 3u;
 #pragma unroll
@@ -696,6 +771,11 @@ __device__ void bdec_small(const BatchDecArgs &a, uint32_t li, int lane, uint8_t
         }
         __syncwarp();  // the slot and pos are read before the next piece is staged
         uint32_t *op = out + 4 * q0;
+        if (t.full()) {
+            store_full_subtile(op, v);
+            running += total;
+            continue;
+        }
 #pragma unroll
         for (int r = 0; r < kSubRounds; r++) {
             const bool whole = subtile_nints(t, 32u * r + 31u) == 4u;
