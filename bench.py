@@ -780,6 +780,7 @@ def time_lists(svb, W, dev, peaks, count: int):
            "tuned": {"threshold": tuned["threshold"], "grid": tuned["grid"],
                      "segment_tiles": tuned.get("segment_tiles"),
                      "stages": tuned.get("stages"), "tile_ints": tuned.get("tile_ints"),
+                     "encode_threshold": tuned.get("encode_threshold"),
                      "encode_stages": tuned.get("encode_stages"), "cached": tuned["cached"]},
            "decode_batched_graph": {"gints_per_s": total / ms_graph / 1e6, "ms": ms_graph,
                                     "frac": alg / (ms_graph / 1e3) / 1e9 / hb},

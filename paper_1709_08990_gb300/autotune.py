@@ -17,7 +17,8 @@ tune_batch() times the batched decode of a ListPool (CUDA events, the
 median of several runs) over threshold x grid, then over segment_tiles at
 the best pair, then over the staging depth, then over the larger tile at
 its depths (with units of the same number of integers), optionally the
-batched encode over its staging depth, and caches the winner in a JSON file
+batched encode over its own threshold and staging depth (its plan is built
+apart from the decode's), and caches the winner in a JSON file
 keyed by GPU name and workload, so later runs reuse it.  A plan is laid out
 in the tile it was built for, so every change of tile replans.  The cache
 path is SVB_AUTOTUNE_CACHE, else autotune_cache.json next to this file.
@@ -110,20 +111,23 @@ def _scaled_segments(seg, tile_ints: int):
 
 
 def tune_batch(pool, workload: str, d_out: torch.Tensor,
-               thresholds=(2048, 4096, 8192, 16384, 65536), grids=None,
+               thresholds=(1024, 2048, 4096, 8192, 16384, 65536, 262144), grids=None,
                segments=(0, 8, 16, 32), stages=(2, 3, 4), reps: int = 5, force: bool = False,
                enc_out: torch.Tensor | None = None, enc_stages=(2, 3),
-               tiles=(4096, 8192)) -> dict:
+               tiles=(4096, 8192), enc_thresholds=None) -> dict:
     """Pick (threshold, grid, segment_tiles, stages, tile) for pool.decode,
-    and the encoder's staging depth when enc_out (pool.encode's output) is
-    given; returns the cache entry and leaves the pool and the library set
-    to it.  threshold, grid, segment_tiles and the depth are searched at the
-    first tile of `tiles`; every other tile is tried at each of its depths."""
+    and the encoder's threshold and staging depth when enc_out
+    (pool.encode's output) is given; returns the cache entry and leaves the
+    pool and the library set to it.  threshold, grid, segment_tiles and the
+    depth are searched at the first tile of `tiles`; every other tile is
+    tried at each of its depths.  The encoder's thresholds default to the
+    decode's."""
     hit = None if force else lookup("batch_decode", workload)
     if hit is not None:
         _set_tile(hit.get("tile_ints", 0))
         _set_stages(hit.get("stages", 0), hit.get("encode_stages", 0))
-        pool.replan(hit["threshold"], hit["grid"], hit.get("segment_tiles"))
+        pool.replan(hit["threshold"], hit["grid"], hit.get("segment_tiles"),
+                    hit.get("encode_threshold"))
         return dict(hit, cached=True)
     if grids is None:
         sms = torch.cuda.get_device_properties(pool.device).multi_processor_count
@@ -161,19 +165,23 @@ def tune_batch(pool, workload: str, d_out: torch.Tensor,
             trial(best["threshold"], best["grid"], seg, st, tile)
     best = min(trials, key=lambda t: t["ms"])
     _set_tile(best["tile_ints"])
-    enc_best, enc_trials = 0, []
+    enc_best, enc_thr, enc_trials = 0, best["threshold"], []
     if enc_out is not None:
-        for st in enc_stages:
-            _set_stages(best["stages"], st)
-            enc_trials.append({"encode_stages": st,
-                               "ms": _time_ms(lambda: pool.encode(enc_out), reps)})
-        enc_best = min(enc_trials, key=lambda t: t["ms"])["encode_stages"]
+        for thr in (thresholds if enc_thresholds is None else enc_thresholds):
+            pool.replan(best["threshold"], best["grid"], best["segment_tiles"], thr)
+            for st in enc_stages:
+                _set_stages(best["stages"], st)
+                enc_trials.append({"encode_threshold": thr, "encode_stages": st,
+                                   "ms": _time_ms(lambda: pool.encode(enc_out), reps)})
+        e = min(enc_trials, key=lambda t: t["ms"])
+        enc_best, enc_thr = e["encode_stages"], e["encode_threshold"]
     entry = {"threshold": best["threshold"], "grid": best["grid"],
              "segment_tiles": best["segment_tiles"], "stages": best["stages"],
-             "tile_ints": best["tile_ints"], "encode_stages": enc_best, "ms": best["ms"],
+             "tile_ints": best["tile_ints"], "encode_threshold": enc_thr,
+             "encode_stages": enc_best, "ms": best["ms"],
              "geometry": geometry(best["tile_ints"]), "trials": trials,
              "encode_trials": enc_trials}
     store("batch_decode", workload, entry)
     _set_stages(best["stages"], enc_best)
-    pool.replan(best["threshold"], best["grid"], best["segment_tiles"])
+    pool.replan(best["threshold"], best["grid"], best["segment_tiles"], enc_thr)
     return dict(entry, cached=False)

@@ -49,6 +49,7 @@ class ListPool:
             self.first[1:] = np.cumsum(self.lengths[:-1], dtype=np.uint64)
         self.total = int(self.lengths.sum(dtype=np.uint64))
         self.threshold = threshold
+        self.enc_threshold = threshold
         self.grid = grid
         self.segment_tiles = segment_tiles   # None: the library's default
         if isinstance(values, torch.Tensor):
@@ -130,12 +131,16 @@ class ListPool:
     def result(self):
         return self.ws.res.cpu().numpy()
 
-    def replan(self, threshold: int, grid: int = 0, segment_tiles: int | None = None):
+    def replan(self, threshold: int, grid: int = 0, segment_tiles: int | None = None,
+               enc_threshold: int | None = None):
+        """New plans: the decode's from threshold and segment_tiles, the
+        encode's from enc_threshold (None: threshold)."""
         self.threshold = threshold
         self.grid = grid
         self.segment_tiles = segment_tiles
+        self.enc_threshold = threshold if enc_threshold is None else enc_threshold
         self.dec_plan = self._plan(self.dec_table, threshold)
-        self.enc_plan = self._plan(self.enc_table, threshold)
+        self.enc_plan = self._plan(self.enc_table, self.enc_threshold)
 
     def graph(self, fn) -> torch.cuda.CUDAGraph:
         """fn() captured once into a CUDA graph (after one eager warm-up run)."""

@@ -25,9 +25,10 @@ class FakePool:
         self.tile = 0            # the library's decode tile (set by the tuner)
         self.planned_tile = None
 
-    def replan(self, threshold, grid, segment_tiles=None):
+    def replan(self, threshold, grid, segment_tiles=None, enc_threshold=None):
         self.current = (threshold, grid)
         self.segments = segment_tiles
+        self.enc_threshold = threshold if enc_threshold is None else enc_threshold
         self.plans.append((threshold, grid))
         self.planned_tile = self.tile   # a plan is laid out in the tile in use
 
@@ -56,7 +57,8 @@ def tuner(tmp_path, monkeypatch):
     def fake_time(fn, reps):
         fn()
         if pool.op == "encode":
-            return cost.get(("enc", stages["enc"]), 4.0)
+            return (cost.get(("enc", stages["enc"]), 4.0)
+                    - cost.get(("enc_thr", pool.enc_threshold), 0.0))
         # A decode runs the plan made last, in the tile it was made for,
         # and must be timed with that tile still in use.
         assert pool.planned_tile == pool.tile
@@ -82,13 +84,17 @@ def test_picks_the_fastest_and_caches_it(tuner):
     cost[((8192, 152), "seg16")] = True
     cost[("dec", 3)] = 0.25   # three stages shave 0.25 ms
     cost[("enc", 2)] = 3.0    # the encoder is fastest with two
+    cost[("enc_thr", 2048)] = 0.5   # and with its own, smaller threshold
     e = autotune.tune_batch(pool, "lists_test", None, thresholds=(2048, 8192), grids=(0, 152),
                             segments=(0, 16), stages=(2, 3, 4), enc_out=object())
     assert (e["threshold"], e["grid"], e["segment_tiles"], e["cached"]) == (8192, 152, 16, False)
     assert (e["stages"], e["encode_stages"], e["tile_ints"]) == (3, 2, 4096)
-    # 4 pairs, 2 segment lengths, 3 depths at 4096, 2 depths at 8192
-    assert len(e["trials"]) == 11 and len(e["encode_trials"]) == 2
+    assert e["encode_threshold"] == 2048
+    # 4 pairs, 2 segment lengths, 3 depths at 4096, 2 depths at 8192;
+    # the encoder: 2 thresholds x 2 depths
+    assert len(e["trials"]) == 11 and len(e["encode_trials"]) == 4
     assert pool.current == (8192, 152) and pool.segments == 16
+    assert pool.enc_threshold == 2048   # the pool's encode plan is the encoder's
     assert (stages["dec"], stages["enc"]) == (3, 2)   # the library is left at the winner
     assert pool.tile == 4096 and pool.planned_tile == 4096
     d = json.load(open(cache))
@@ -96,6 +102,7 @@ def test_picks_the_fastest_and_caches_it(tuner):
     assert d[key]["threshold"] == 8192 and d[key]["grid"] == 152
     assert d[key]["segment_tiles"] == 16 and d[key]["stages"] == 3
     assert d[key]["encode_stages"] == 2 and d[key]["tile_ints"] == 4096
+    assert d[key]["encode_threshold"] == 2048
     assert d[key]["geometry"] == {"tile_ints": 4096, "warp_ints": 512, "subtile_ints": 512,
                                   "lane_ints": 16}
 
