@@ -153,14 +153,23 @@ void svb_set_spin_limit(uint64_t iterations);
  *                              the decode runs as SVB_DECODE_AUTO would run
  *                              it (single pass up to 2^20 integers, else two
  *                              pass).  Differential streams as
- *                              SVB_DECODE_TWO_PASS.
+ *                              SVB_DECODE_TWO_PASS;
+ *   SVB_DECODE_CHUNKED (5)     plain streams: one persistent launch over
+ *                              chunks of 65536 integers; a chunk's data
+ *                              offset comes from a decoupled look-back over
+ *                              the chunks before it, found one chunk ahead of
+ *                              the decode (Sec. 4's offsets without a
+ *                              separate pass).  Differential streams, and
+ *                              streams whose in_len does not cover their
+ *                              control bytes, as SVB_DECODE_TWO_PASS.
  * All give identical results.  Returns SVB_EINVAL for an unknown variant. */
 enum svb_decode_variant {
     SVB_DECODE_AUTO = 0,
     SVB_DECODE_SINGLE_PASS = 1,
     SVB_DECODE_TWO_PASS = 2,
     SVB_DECODE_SUMS_PASS = 3,
-    SVB_DECODE_SMALL = 4
+    SVB_DECODE_SMALL = 4,
+    SVB_DECODE_CHUNKED = 5
 };
 int svb_set_decode_variant(int variant);
 

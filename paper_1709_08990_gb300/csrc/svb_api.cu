@@ -55,6 +55,8 @@ int decode_dispatch(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, uint32_
     if (!delta && n && (v == SVB_DECODE_SMALL || (v == SVB_DECODE_AUTO && n <= kSmallArray)) &&
         svb::launch_decode_small(in, in_len, n, out, ws, r, s, spin_limit()) == 0)
         return 0;
+    if (v == SVB_DECODE_CHUNKED && !delta && in_len >= (n + 3) / 4)
+        return svb::launch_decode_chunked(in, in_len, n, out, ws, r, s, spin_limit());
     if (v == SVB_DECODE_SINGLE_PASS ||
         ((v == SVB_DECODE_AUTO || v == SVB_DECODE_SMALL) && !delta && n <= kSmallPlain))
         return svb::launch_decode(in, in_len, n, out, prev, delta, ws, r, s, spin_limit());
@@ -502,7 +504,7 @@ const char *svb_error_string(int status)
 
 int svb_set_decode_variant(int variant)
 {
-    if (variant < SVB_DECODE_AUTO || variant > SVB_DECODE_SMALL)
+    if (variant < SVB_DECODE_AUTO || variant > SVB_DECODE_CHUNKED)
         return SVB_EINVAL;
     g_decode_variant.store(variant, std::memory_order_relaxed);
     return SVB_OK;

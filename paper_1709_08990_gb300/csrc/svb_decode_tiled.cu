@@ -705,6 +705,7 @@ struct TiledArgs {
     u64 range_magic;    // ceil(2^64 / (range_subs / kSubs)): a tile's range is
                         // the high word of tile * range_magic
     u64 tile0, tile1;   // decoding: the tiles [tile0, tile1) to decode
+    u64 in_len;         // decode_chunked_kernel: stream bytes that may be read
     uint32_t prev;
     uint32_t out_aligned;
 };
@@ -1045,6 +1046,282 @@ __device__ void sums_to_carries(const TiledArgs &a, u64 first, u64 etag)
     range_carries(a.carries, s0, s1, cta, a.prev, a.st, etag, a.spin_limit, a.hdr);
 }
 
+// ---------------------------------------------------------------------------
+// Single pass for plain streams, by chunks: decode_chunked_kernel.
+//
+// Persistent CTAs take chunks of kDcTiles tiles in claim order.  A chunk
+// warp, one chunk ahead of the decode, reads the chunk's control bytes,
+// turns them into each sub-tile's data offset within the chunk (Sec. 4: a
+// control byte covers 4 + the sum of its codes bytes), publishes the chunk's
+// total and finds the chunk's data offset by decoupled look-back over the
+// chunks before it.  The producer warp then stages the chunk's tiles with
+// bulk copies and the consumer warps decode them exactly as in the two-pass
+// decoder, so no separate offsets pass runs.  A chunk's look-back has the
+// decode of the previous chunk to complete in: chunks are claimed about as
+// fast as CTAs finish them, so the predecessors it waits on are a window of
+// recent claims whose totals were published as soon as their control bytes
+// were summed.  The control reads ask L2 to keep the bytes, which the
+// producer stages again shortly after.
+
+constexpr int kDcTiles = 16;                   // tiles per chunk (65536 integers)
+constexpr int kDcSubs = kDcTiles * kSubs;      // sub-tiles per chunk
+constexpr int kDcBlock = kDecBlock + 32;       // consumers, producer, chunk warp
+constexpr int kDcVecs = kDcTiles * kTileQuads / 16;   // 16-byte control vectors per chunk
+constexpr int kDcLaneSubs = kDcSubs / 32;              // sub-tiles each lane scans
+static_assert(kDcSubs % 32 == 0 && kDcVecs % (8 * 32) == 0, "whole batches of vectors");
+
+struct DcChunks {
+    u64 chunk[2];                     // chunk index, or kNoTile once none is left
+    u64 base[2];                      // the chunk's first data byte (from the data start)
+    uint32_t soff[2][kDcSubs + 1];    // sub-tile data offsets in the chunk; [kDcSubs]: its total
+    uint32_t bad[2];                  // cut short or failed: decode nothing
+    uint64_t ready[2];                // chunk warp -> producer
+    uint64_t freed[2];                // producer -> chunk warp
+};
+
+// The chunk warp: sums, look-back and hand-over of one chunk after another,
+// double-buffered; buffer b is claimed again only once the producer freed it.
+__device__ void dc_chunks(const TiledArgs &a, DcChunks &C, uint32_t *s_cnt, u64 etag, int lane)
+{
+    const u64 nchunks = (a.ntiles + kDcTiles - 1) / kDcTiles;
+    const uint32_t last_nints = (uint32_t)(a.n - 4 * (a.nquads - 1));
+    const bool aligned = ((uintptr_t)a.in & 15u) == 0;
+    const uint64_t keep = l2_policy_evict_last();
+    for (uint32_t j = 0;; j++) {
+        const int b = j & 1;
+        if (j >= 2 && !__all_sync(0xffffffffu, mbar_wait_bounded(&C.freed[b], ((j >> 1) - 1) & 1u,
+                                                                  kBarrierPolls))) {
+            if (lane == 0)
+                raise_error(a.hdr, kErrTimeout);
+            return;   // the producer's own wait for this buffer runs out too
+        }
+        u64 c = 0;
+        if (lane == 0)
+            c = atomicAdd(&a.hdr->tile_counter, 1ull);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if (c >= nchunks) {
+            if (lane == 0) {
+                C.chunk[b] = kNoTile;
+                mbar_arrive(&C.ready[b]);
+            }
+            return;
+        }
+        // Data bytes of each sub-tile: vector 32i + lane holds quads
+        // 16 (32i + lane) .. of the chunk, which lie in sub-tile 4i + lane / 8;
+        // the 8 lanes of a sub-tile add up their counts.
+        const u64 q0 = c * (u64)kDcTiles * kTileQuads;
+#pragma unroll
+        for (int h = 0; h < kDcVecs / (8 * 32); h++) {
+            uint4 v[8];
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                const u64 q = q0 + 16 * (u64)((8 * h + i) * 32 + lane);
+                if (q >= a.nquads) {
+                    v[i] = make_uint4(0u, 0u, 0u, 0u);
+                } else if (aligned && q + 16 <= a.nquads) {
+                    v[i] = ld_keep128(a.in + q, keep);
+                } else {
+                    uint32_t w[4] = {0, 0, 0, 0};
+                    for (int k = 0; k < 16; k++)
+                        if (q + k < a.nquads)
+                            w[k >> 2] |= (uint32_t)__ldg(a.in + q + k) << (8 * (k & 3));
+                    v[i] = make_uint4(w[0], w[1], w[2], w[3]);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                const u64 q = q0 + 16 * (u64)((8 * h + i) * 32 + lane);
+                uint32_t cnt = q < a.nquads ? chunk_bytes(v[i], q, a.nquads, last_nints) : 0u;
+                cnt += __shfl_xor_sync(0xffffffffu, cnt, 1);
+                cnt += __shfl_xor_sync(0xffffffffu, cnt, 2);
+                cnt += __shfl_xor_sync(0xffffffffu, cnt, 4);
+                if ((lane & 7) == 0)
+                    s_cnt[4 * (8 * h + i) + (lane >> 3)] = cnt;
+            }
+        }
+        __syncwarp();
+        uint32_t cs[kDcLaneSubs], lt = 0;
+#pragma unroll
+        for (int i = 0; i < kDcLaneSubs; i++) {
+            cs[i] = s_cnt[kDcLaneSubs * lane + i];
+            lt += cs[i];
+        }
+        const uint32_t inc = warp_incl_scan(lt);
+        uint32_t ex = inc - lt;
+#pragma unroll
+        for (int i = 0; i < kDcLaneSubs; i++) {
+            C.soff[b][kDcLaneSubs * lane + i] = ex;
+            ex += cs[i];
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
+        // The chunk's data offset: publish its total, then look back.
+        u64 excl = 0;
+        bool ok = true;
+        if (c == 0) {
+            if (lane == 0)
+                publish(&a.st[0].off_tag, &a.st[0].off_pre, total, kFlagPrefix, etag);
+        } else {
+            if (lane == 0)
+                publish(&a.st[c].off_tag, &a.st[c].off_agg, total, kFlagAgg, etag);
+            excl = lookback<false>(a.st, c, etag, a.spin_limit, a.hdr, ok);
+            if (lane == 0 && ok)
+                publish(&a.st[c].off_tag, &a.st[c].off_pre, excl + total, kFlagPrefix, etag);
+        }
+        const u64 end = a.nquads + excl + total;   // stream bytes up to the chunk's end
+        if (lane == 0) {
+            if (!ok)
+                raise_error(a.hdr, kErrTimeout);
+            else if (end > a.in_len)
+                raise_error(a.hdr, kErrTruncated);
+            if (c == nchunks - 1)
+                st_relaxed(&a.hdr->total, end);
+            C.soff[b][kDcSubs] = total;
+            C.base[b] = excl;
+            C.chunk[b] = c;
+            C.bad[b] = (!ok || end > a.in_len) ? 1u : 0u;
+        }
+        __syncwarp();   // s_cnt and the buffer are written before the hand-over
+        if (lane == 0)
+            mbar_arrive(&C.ready[b]);
+    }
+}
+
+// The producer: each chunk's tiles into the stage ring, with the offsets the
+// chunk warp found.  Reads stay inside the stream: below the chunk's own data
+// end plus the bytes the integers after it must have (the aligned copy of a
+// tile that would pass that bound falls back to its interior plus plain
+// loads of the ragged ends).
+__device__ void dc_produce(const TiledArgs &a, Pipe &P, DcChunks &C, int lane)
+{
+    uint32_t k = 0, issued = 0;   // stage fills
+    const uint8_t *data = a.in + a.nquads;
+    auto wait_empty = [&]() -> bool {
+        if (k < (uint32_t)kStages)
+            return true;
+        const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&P.empty[k % kStages],
+                                                                  ((k / kStages) - 1) & 1u,
+                                                                  kBarrierPolls));
+        if (!ok && lane == 0)
+            raise_error(a.hdr, kErrTimeout);
+        return ok;
+    };
+    for (uint32_t j = 0;; j++) {
+        const int b = j & 1;
+        if (!__all_sync(0xffffffffu,
+                        mbar_wait_bounded(&C.ready[b], (j >> 1) & 1u, kBarrierPolls))) {
+            if (lane == 0)
+                raise_error(a.hdr, kErrTimeout);
+            break;
+        }
+        const u64 c = C.chunk[b];
+        if (c == kNoTile)
+            break;
+        const u64 t0 = c * kDcTiles, t1 = min(t0 + kDcTiles, a.ntiles);
+        const u64 base = C.base[b];
+        // Readable up to the chunk's data end plus as many bytes as the
+        // integers after the chunk surely have (one each), at most 16.
+        const u64 after = a.n - min(a.n, (t1 * kTileQuads) * 4);
+        const uint8_t *hi = data + base + C.soff[b][kDcSubs] + min(after, (u64)16);
+        if (a.in_len != ~0ull && hi > a.in + a.in_len)
+            hi = a.in + a.in_len;
+        bool failed = false;
+        for (u64 t = C.bad[b] ? t1 : t0; t < t1; t++) {
+            if (!wait_empty()) {
+                failed = true;
+                break;
+            }
+            const int s = k % kStages;
+            const uint32_t i = (uint32_t)(t - t0);
+            const uint32_t so = lane <= kSubs ? C.soff[b][i * kSubs + lane] : 0u;
+            const uint32_t s0 = __shfl_sync(0xffffffffu, so, 0);
+            const uint32_t s1 = __shfl_sync(0xffffffffu, so, kSubs);
+            if (lane < kSubs)
+                P.soff[s][lane] = so - s0;
+            const u64 q0 = t * kTileQuads;
+            const uint32_t clen = (uint32_t)min((u64)kTileQuads, a.nquads - q0);
+            const uint8_t *gc = a.in + q0;
+            const uint8_t *gd = data + base + s0;
+            const uint32_t dlen = s1 - s0;
+            const StagePlan pc = stage_plan(gc, clen, a.in, hi);
+            const StagePlan pd = stage_plan(gd, dlen, a.in, hi);
+            if (pc.edges)
+                range_edges(gc, clen, P.ctrl[s], lane);
+            if (pd.edges)
+                range_edges(gd, dlen, P.data[s], lane);
+            if (lane == 0) {
+                P.tile[s] = t;
+                P.hc[s] = (uint32_t)((uintptr_t)gc & 15u);
+                P.hd[s] = (uint32_t)((uintptr_t)gd & 15u);
+                mbar_arrive_expect_tx(&P.full[s], pc.bytes + pd.bytes);
+                if (pc.bytes)
+                    bulk_g2s(P.ctrl[s] + pc.dst_off, pc.src, pc.bytes, &P.full[s]);
+                if (pd.bytes)
+                    bulk_g2s(P.data[s] + pd.dst_off, pd.src, pd.bytes, &P.full[s]);
+            } else {
+                mbar_arrive(&P.full[s]);
+            }
+            issued = ++k;
+        }
+        __syncwarp();   // buffer b is no longer read
+        if (lane == 0)
+            mbar_arrive(&C.freed[b]);
+        if (failed)
+            break;
+    }
+    // No tile left: one stage marked kNoTile ends the consumers' loop.
+    if (wait_empty()) {
+        const int s = k % kStages;
+        if (lane == 0) {
+            P.tile[s] = kNoTile;
+            mbar_arrive_expect_tx(&P.full[s], 0);
+        } else {
+            mbar_arrive(&P.full[s]);
+        }
+        issued = ++k;
+    }
+    // Let every copy this warp started land before the CTA can exit.
+    if (lane == 0) {
+        for (int s = 0; s < kStages; s++)
+            if (issued > (uint32_t)s) {
+                const uint32_t fills = (issued - 1 - s) / kStages + 1;
+                mbar_wait_bounded(&P.full[s], (fills - 1) & 1u, kBarrierPolls);
+            }
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(kDcBlock, 3) decode_chunked_kernel(TiledArgs a)
+{
+    extern __shared__ __align__(128) uint8_t dyn_smem[];
+    Pipe &P = *reinterpret_cast<Pipe *>(dyn_smem);
+    __shared__ __align__(16) uint16_t s_pos[kWarps * kSubQuads];
+    __shared__ DcChunks C;
+    __shared__ uint32_t s_cnt[kDcSubs];
+    __shared__ u64 s_etag;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        for (int s = 0; s < kStages; s++) {
+            mbar_init(&P.full[s], 32);        // the 32 producer lanes arrive
+            mbar_init(&P.empty[s], kWarps);   // one arrival per consumer warp
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&C.ready[b], 1);
+            mbar_init(&C.freed[b], 1);
+        }
+        fence_mbar_init();
+        s_etag = epoch_tag(a.hdr);
+    }
+    __syncthreads();
+    if (warp == kWarps)
+        dc_produce(a, P, C, lane);
+    else if (warp == kWarps + 1)
+        dc_chunks(a, C, s_cnt, s_etag, lane);
+    else
+        consume<kPlain>(a, P, s_pos);
+    finish_launch(a.hdr, a.result);
+}
+
 template <int kMode>
 __global__ void __launch_bounds__(kDecBlock, 3) decode_tiled_kernel(TiledArgs a)
 {
@@ -1271,6 +1548,7 @@ static TiledArgs tiled_args(const uint8_t *in, u64 n, uint32_t *out, uint32_t pr
     t.tile1 = t.ntiles;
     t.prev = prev;
     t.out_aligned = (((uintptr_t)out) & 15u) == 0;
+    t.in_len = ~0ull;
     return t;
 }
 
@@ -1315,6 +1593,30 @@ int launch_decode_range(const uint8_t *in, u64 n, uint32_t *out, void *ws, Devic
     const u64 grid = max((u64)1, min((u64)tiled_grid<kPlain>(), t.tile1 - min(tile0, t.tile1)));
     prof_begin("decode_tiled_kernel<plain>", stream);
     decode_tiled_kernel<kPlain><<<(unsigned)grid, kDecBlock, sizeof(Pipe), stream>>>(t);
+    prof_end(stream);
+    return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+// The chunked single pass over a plain stream (the caller checked that
+// in_len covers the control bytes).
+int launch_decode_chunked(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, void *ws,
+                          DeviceResult *result, cudaStream_t stream, u64 spin_limit)
+{
+    static int g = 0;
+    if (!g) {
+        cudaFuncSetAttribute(decode_chunked_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(Pipe));
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, decode_chunked_kernel, kDcBlock,
+                                                      sizeof(Pipe));
+        g = sm_count() * (occ > 0 ? occ : 1);
+    }
+    TiledArgs t = tiled_args(in, n, out, 0, ws, result, spin_limit);
+    t.in_len = in_len;
+    const u64 nchunks = (t.ntiles + kDcTiles - 1) / kDcTiles;
+    const u64 grid = max((u64)1, min((u64)g, nchunks));
+    prof_begin("decode_chunked_kernel", stream);
+    decode_chunked_kernel<<<(unsigned)grid, kDcBlock, sizeof(Pipe), stream>>>(t);
     prof_end(stream);
     return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }

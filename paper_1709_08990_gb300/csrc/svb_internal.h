@@ -21,6 +21,8 @@ u64 decode_tiles(u64 n);
 // Reduce-then-decode: control-stream offsets pass, then a persistent decode
 // with bulk-copy staging.  Differential streams get their carry-ins in the
 // offsets pass, or, with sums_pass, from a separate pass over staged tiles.
+int launch_decode_chunked(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, void *ws,
+                          DeviceResult *result, cudaStream_t stream, u64 spin_limit);
 int launch_decode_tiled(const uint8_t *in, u64 in_len, u64 n, uint32_t *out, uint32_t prev,
                         bool delta, void *ws, DeviceResult *result, cudaStream_t stream,
                         u64 spin_limit, bool sums_pass = false);

@@ -177,7 +177,7 @@ def svb_set_spin_limit(iterations: int) -> None:
 
 
 (SVB_DECODE_AUTO, SVB_DECODE_SINGLE_PASS, SVB_DECODE_TWO_PASS, SVB_DECODE_SUMS_PASS,
- SVB_DECODE_SMALL) = 0, 1, 2, 3, 4
+ SVB_DECODE_SMALL, SVB_DECODE_CHUNKED) = 0, 1, 2, 3, 4, 5
 
 
 def svb_set_decode_variant(variant: int) -> int:

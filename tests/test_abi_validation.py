@@ -70,12 +70,12 @@ def test_workspace_size_grows_with_n(lib):
 
 
 def test_variants_reject_unknown_values(lib):
-    for v in (-1, 5, 99):
+    for v in (-1, 6, 99):
         assert lib.svb_set_decode_variant(v) == svb.SVB_EINVAL
     for v in (-1, 4):
         assert lib.svb_set_encode_variant(v) == svb.SVB_EINVAL
     try:
-        for v in (0, 1, 2, 3, 4):
+        for v in (0, 1, 2, 3, 4, 5):
             assert lib.svb_set_decode_variant(v) == svb.SVB_OK
         for v in (0, 1, 2, 3):
             assert lib.svb_set_encode_variant(v) == svb.SVB_OK

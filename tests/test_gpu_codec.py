@@ -19,18 +19,20 @@ DEV = "cuda:0"
 
 
 ENCODER_WITH = {1: svb.SVB_ENCODE_TILE_LOOKBACK, 2: svb.SVB_ENCODE_CHUNKED,
-                3: svb.SVB_ENCODE_CHUNKED, 4: svb.SVB_ENCODE_SMALL}
+                3: svb.SVB_ENCODE_CHUNKED, 4: svb.SVB_ENCODE_SMALL, 5: svb.SVB_ENCODE_CHUNKED}
 
 
-@pytest.fixture(params=[1, 2, 3, 4], ids=["single_pass", "two_pass", "sums_pass", "small"])
+@pytest.fixture(params=[1, 2, 3, 4, 5],
+                ids=["single_pass", "two_pass", "sums_pass", "small", "chunked"])
 def variant(request):
     """Run a test under each decoder variant and, alongside, an encoder
     variant (tile look-back with the single-pass decoder, chunked with the
     two-pass and sums-pass ones, the one-launch small-array encoder with the
-    small-array decoder).  The sums-pass variant differs from the two-pass
-    one only for differential streams; the small-array decoder only for
-    plain ones (its encoder codes both), and it falls back to the other
-    decoders above the tiles that can be resident at once."""
+    small-array decoder, chunked with the chunked single-pass decoder).  The
+    sums-pass variant differs from the two-pass one only for differential
+    streams; the small-array and chunked decoders only for plain ones (the
+    small-array encoder codes both), and the small-array decoder falls back
+    to the other decoders above the tiles that can be resident at once."""
     assert svb.svb_set_decode_variant(request.param) == 0
     assert svb.svb_set_encode_variant(ENCODER_WITH[request.param]) == 0
     yield request.param
@@ -39,9 +41,12 @@ def variant(request):
 
 
 def plain_only_repeat(delta: bool, variant: int) -> None:
-    """The sums-pass variant decodes plain streams exactly as the two-pass one."""
+    """The sums-pass variant decodes plain streams exactly as the two-pass
+    one, and the chunked variant differential ones."""
     if variant == 3 and not delta:
         pytest.skip("plain streams: same kernels as the two-pass variant")
+    if variant == 5 and delta:
+        pytest.skip("differential streams: same kernels as the two-pass variant")
 
 
 def to_dev(a: np.ndarray):
