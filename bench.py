@@ -436,6 +436,15 @@ def main():
         sec["decode_single_pass_" + args.workload] = {
             "gints_per_s": n / ms1 / 1e6, "ms": ms1, "frac": alg_bytes / (ms1 / 1e3) / 1e9 /
             peaks["hbm_gbs"], "verified_prefix": bool(ok1)}
+        if not w.delta:   # the chunked single pass decodes plain streams
+            d_out.zero_()
+            svb.svb_set_decode_variant(svb.SVB_DECODE_CHUNKED)
+            ms5 = _time(step, 50, stream)
+            svb.svb_set_decode_variant(svb.SVB_DECODE_AUTO)
+            ok5 = torch.equal(d_out[:n], h_x.to(dev))
+            sec["decode_chunked_" + args.workload] = {
+                "gints_per_s": n / ms5 / 1e6, "ms": ms5,
+                "frac": alg_bytes / (ms5 / 1e3) / 1e9 / peaks["hbm_gbs"], "verified": bool(ok5)}
         del d_out, d_stream
         torch.cuda.empty_cache()
         sec["encode_" + args.workload] = time_encode(svb, W, args.workload, dev, peaks, h_x)
