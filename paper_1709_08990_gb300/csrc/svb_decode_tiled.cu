@@ -559,11 +559,11 @@ __global__ void __launch_bounds__(kThreads, 4) delta_prep_kernel(OffsetsArgs a)
         // Batches of 8 runs: each lane byte-sums its chunk of each run, a
         // reduce-scatter over lane bits 4, 3, 2 and a butterfly over bits
         // 1, 0 leave run u0 + k's total in lanes 4k .. 4k + 3, and lane
-        // u0 + k takes it from lane 4k.
+        // u0 + k takes it from lane 4k.  Each batch's loads are issued as
+        // soon as the batch before has been byte-summed.
         uint32_t sum = 0;  // chunks 0..31 of this lane's run
-#pragma unroll
-        for (int u0 = 0; u0 < 32; u0 += kPrepUnroll) {
-            uint4 v[kPrepUnroll];
+        uint4 v[kPrepUnroll];
+        auto load_batch = [&](int u0) {
 #pragma unroll
             for (int i = 0; i < kPrepUnroll; i++) {
                 const int u = u0 + i;
@@ -575,10 +575,16 @@ __global__ void __launch_bounds__(kThreads, 4) delta_prep_kernel(OffsetsArgs a)
                     v[i] = ld_keep128(run + lane, policy);
                 }
             }
+        };
+        load_batch(0);
+#pragma unroll
+        for (int u0 = 0; u0 < 32; u0 += kPrepUnroll) {
             uint32_t q[kPrepUnroll];
 #pragma unroll
             for (int i = 0; i < kPrepUnroll; i++)
                 q[i] = bytesum4(v[i], 0u);
+            if (u0 + kPrepUnroll < 32)   // the next batch's loads fly during the shuffles
+                load_batch(u0 + kPrepUnroll);
 #pragma unroll
             for (int h = kPrepUnroll / 2, bit = 16; h >= 1; h >>= 1, bit >>= 1) {
                 const bool upper = (lane & bit) != 0;
