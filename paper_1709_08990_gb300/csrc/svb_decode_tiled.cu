@@ -1076,20 +1076,17 @@ constexpr int kDcVecs = kDcTiles * kTileQuads / 16;   // 16-byte control vectors
 constexpr int kDcLaneSubs = kDcSubs / 32;              // sub-tiles each lane scans
 static_assert(kDcSubs % 32 == 0 && kDcVecs % (8 * 32) == 0, "whole batches of vectors");
 
-constexpr int kDcBufs = 2;   // chunk buffers (3 and 4 were no faster)
-
 struct DcChunks {
-    u64 chunk[kDcBufs];                     // chunk index, or kNoTile once none is left
-    u64 base[kDcBufs];                      // the chunk's first data byte (from the data start)
-    uint32_t soff[kDcBufs][kDcSubs + 1];    // sub-tile data offsets; [kDcSubs]: the chunk's total
-    uint32_t bad[kDcBufs];                  // cut short or failed: decode nothing
-    uint64_t ready[kDcBufs];                // chunk warp -> producer
-    uint64_t freed[kDcBufs];                // producer -> chunk warp
+    u64 chunk[2];                     // chunk index, or kNoTile once none is left
+    u64 base[2];                      // the chunk's first data byte (from the data start)
+    uint32_t soff[2][kDcSubs + 1];    // sub-tile data offsets in the chunk; [kDcSubs]: its total
+    uint32_t bad[2];                  // cut short or failed: decode nothing
+    uint64_t ready[2];                // chunk warp -> producer
+    uint64_t freed[2];                // producer -> chunk warp
 };
 
 // The chunk warp: sums, look-back and hand-over of one chunk after another,
-// through a ring of kDcBufs buffers; buffer b is claimed again only once the
-// producer freed it.
+// double-buffered; buffer b is claimed again only once the producer freed it.
 __device__ void dc_chunks(const TiledArgs &a, DcChunks &C, uint32_t *s_cnt, u64 etag, int lane)
 {
     const u64 nchunks = (a.ntiles + kDcTiles - 1) / kDcTiles;
@@ -1097,9 +1094,8 @@ __device__ void dc_chunks(const TiledArgs &a, DcChunks &C, uint32_t *s_cnt, u64 
     const bool aligned = ((uintptr_t)a.in & 15u) == 0;
     const uint64_t keep = l2_policy_evict_last();
     for (uint32_t j = 0;; j++) {
-        const int b = j % kDcBufs;
-        if (j >= (uint32_t)kDcBufs &&
-            !__all_sync(0xffffffffu, mbar_wait_bounded(&C.freed[b], ((j / kDcBufs) - 1) & 1u,
+        const int b = j & 1;
+        if (j >= 2 && !__all_sync(0xffffffffu, mbar_wait_bounded(&C.freed[b], ((j >> 1) - 1) & 1u,
                                                                   kBarrierPolls))) {
             if (lane == 0)
                 raise_error(a.hdr, kErrTimeout);
@@ -1216,9 +1212,9 @@ __device__ void dc_produce(const TiledArgs &a, Pipe &P, DcChunks &C, int lane)
         return ok;
     };
     for (uint32_t j = 0;; j++) {
-        const int b = j % kDcBufs;
+        const int b = j & 1;
         if (!__all_sync(0xffffffffu,
-                        mbar_wait_bounded(&C.ready[b], (j / kDcBufs) & 1u, kBarrierPolls))) {
+                        mbar_wait_bounded(&C.ready[b], (j >> 1) & 1u, kBarrierPolls))) {
             if (lane == 0)
                 raise_error(a.hdr, kErrTimeout);
             break;
@@ -1315,7 +1311,7 @@ __global__ void __launch_bounds__(kDcBlock, 3) decode_chunked_kernel(TiledArgs a
             mbar_init(&P.full[s], 32);        // the 32 producer lanes arrive
             mbar_init(&P.empty[s], kWarps);   // one arrival per consumer warp
         }
-        for (int b = 0; b < kDcBufs; b++) {
+        for (int b = 0; b < 2; b++) {
             mbar_init(&C.ready[b], 1);
             mbar_init(&C.freed[b], 1);
         }
