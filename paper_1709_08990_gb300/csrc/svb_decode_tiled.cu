@@ -1066,8 +1066,9 @@ __device__ void sums_to_carries(const TiledArgs &a, u64 first, u64 etag)
 // decode of the previous chunk to complete in: chunks are claimed about as
 // fast as CTAs finish them, so the predecessors it waits on are a window of
 // recent claims whose totals were published as soon as their control bytes
-// were summed.  The control reads ask L2 to keep the bytes, which the
-// producer stages again shortly after.
+// were summed.  The control reads ask L2 to keep the bytes for the
+// producer, which stages them again one chunk later; at full size most have
+// been evicted by then, so the control stream is read twice.
 
 constexpr int kDcTiles = 16;                   // tiles per chunk (65536 integers)
 constexpr int kDcSubs = kDcTiles * kSubs;      // sub-tiles per chunk
