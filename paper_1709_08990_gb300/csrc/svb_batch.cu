@@ -872,8 +872,12 @@ __global__ void __launch_bounds__(kThreads) batch_prep_kernel(BatchPrepArgs a)
         const uint32_t qe = min((U.t0 + U.nt) * tq, nql);
         const uint32_t ns = (qe - qb0 + kSubQuads - 1) / kSubQuads;
         const bool ctrl_ok = (u64)nql <= L.in_len;
+        // The list's last unit: no later unit reads its totals, so only its
+        // data offset and carry-in (the two look-backs) are found; a stream
+        // cut short inside it is reported by the decode.
+        const bool last = U.t0 + U.nt >= (nql + tq - 1) / tq;
         // A: data bytes of each sub-tile (byte loads, coalesced across the warp).
-        for (uint32_t j = warp; j < ns; j += kWarps) {
+        for (uint32_t j = warp; !last && j < ns; j += kWarps) {
             const uint32_t qb = qb0 + j * kSubQuads;
             uint32_t t = 0;
             if (ctrl_ok) {
@@ -898,7 +902,7 @@ __global__ void __launch_bounds__(kThreads) batch_prep_kernel(BatchPrepArgs a)
         __syncthreads();
         // B: offsets within the unit (warp 0 scans), then the unit's data offset.
         if (warp == 0) {
-            const uint32_t per = (ns + 31) / 32;
+            const uint32_t per = last ? 0u : (ns + 31) / 32;
             const uint32_t b = min(lane * per, ns), e = min(b + per, ns);
             uint32_t tot = 0;
             for (uint32_t i = b; i < e; i++)
@@ -910,20 +914,20 @@ __global__ void __launch_bounds__(kThreads) batch_prep_kernel(BatchPrepArgs a)
                 s_off[i] = c;
                 c += v;
             }
-            const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
+            const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);   // 0 for the last unit
             if (lane == 0)
                 s_off[ns] = total;
             TileStatus *me = &recs[U.first + U.seg];
             u64 d0 = 0;
             bool ok = true;
             if (U.seg == 0) {
-                if (lane == 0)
+                if (lane == 0 && !last)
                     publish(&me->off_tag, &me->off_pre, total, kFlagPrefix, etag);
             } else {
-                if (lane == 0)
+                if (lane == 0 && !last)
                     publish(&me->off_tag, &me->off_agg, total, kFlagAgg, etag);
                 d0 = lookback<false>(recs + U.first, U.seg, etag, kPrepSpins, a.hdr, ok);
-                if (lane == 0)
+                if (lane == 0 && !last)
                     publish(&me->off_tag, &me->off_pre, d0 + total, kFlagPrefix, etag);
             }
             if (lane == 0) {
@@ -949,7 +953,7 @@ __global__ void __launch_bounds__(kThreads) batch_prep_kernel(BatchPrepArgs a)
             return full && len == 4u * kSubQuads;   // every code zero: a byte sum
         };
         auto stage = [&](uint32_t j, uint8_t *slot) {
-            if (bad || j >= ns)
+            if (bad || last || j >= ns)
                 return;
             uint32_t qb, nq, len;
             u64 start;
@@ -961,7 +965,7 @@ __global__ void __launch_bounds__(kThreads) batch_prep_kernel(BatchPrepArgs a)
         stage(warp, s_slot[warp][0]);
         cp_async_commit();
         uint32_t k = 0;
-        for (uint32_t j = warp; j < ns; j += kWarps, k++) {
+        for (uint32_t j = warp; !last && j < ns; j += kWarps, k++) {
             stage(j + kWarps, s_slot[warp][(k + 1) & 1]);
             cp_async_commit();
             cp_async_wait<1>();   // sub-tile j's copies have landed
@@ -1004,7 +1008,7 @@ __global__ void __launch_bounds__(kThreads) batch_prep_kernel(BatchPrepArgs a)
         // D: the unit's carry-in.
         if (warp == 0) {
             uint32_t g = 0;
-            for (uint32_t i = lane; i < ns; i += 32)
+            for (uint32_t i = lane; !last && i < ns; i += 32)
                 g += s_gap[i];
 #pragma unroll
             for (int d = 16; d >= 1; d >>= 1)
@@ -1013,13 +1017,13 @@ __global__ void __launch_bounds__(kThreads) batch_prep_kernel(BatchPrepArgs a)
             u64 c0 = L.prev;
             bool ok = true;
             if (U.seg == 0) {
-                if (lane == 0)
+                if (lane == 0 && !last)
                     publish(&me->val_tag, &me->val_pre, (uint32_t)(L.prev + g), kFlagPrefix, etag);
             } else {
-                if (lane == 0)
+                if (lane == 0 && !last)
                     publish(&me->val_tag, &me->val_agg, g, kFlagAgg, etag);
                 c0 = lookback<true>(recs + U.first, U.seg, etag, kPrepSpins, a.hdr, ok);
-                if (lane == 0)
+                if (lane == 0 && !last)
                     publish(&me->val_tag, &me->val_pre, (uint32_t)(c0 + g), kFlagPrefix, etag);
             }
             if (lane == 0) {
