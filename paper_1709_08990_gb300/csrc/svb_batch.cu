@@ -818,6 +818,8 @@ __device__ void bdec_small(const BatchDecArgs &a, uint32_t li, int lane, uint8_t
 //      coalesced byte loads); any other sub-tile is staged and decoded;
 //   D  c0 = L.prev plus the gaps of L's earlier units, by a second
 //      look-back; d0 and c0 go into the unit for the decode launch.
+// The list's last unit skips A and C and publishes nothing: no later unit
+// reads its totals, so it only looks back for d0 and c0.
 // A list whose stream is cut short publishes zeros (the decode reports it).
 
 constexpr int kBPrepCtrl = 144;                      // 15-byte phase + 128 control bytes
